@@ -1,0 +1,196 @@
+/*
+ * cutqc.h - C ABI of the GB300 reconstruction library for CutQC
+ * (Tang et al., "CutQC: Using Small Quantum Computers for Large Quantum
+ * Circuit Evaluations", arXiv 2012.02333).
+ *
+ * The library rebuilds an uncut circuit's output distribution from the
+ * attributed probability tensors of its subcircuits (Sec. 3.2.3, Sec. 3.3):
+ *
+ *     p(x) = 2^-K  sum_{e in {I,X,Y,Z}^K}  prod_c  T_c[e|c][x|c]
+ *
+ * in full-definition mode (Sec. 4.2: all 2^n entries), in dynamic-definition
+ * mode (Sec. 4.3, Algorithm 1: active qubits binned, merged qubits summed,
+ * zoomed qubits fixed), and as an adjoint that gives dL/dT_c for a loss
+ * L = sum_x G(x) p(x) over the reconstructed distribution.
+ *
+ * Conventions shared by every call
+ *  - Qubit 0 is the most significant bit of every output index (the paper's
+ *    |q_0 ... q_{n-1}> notation, Sec. 3.2).
+ *  - Pauli digits: I=0, X=1, Y=2, Z=3.  A cut assignment e over K cuts is
+ *    the base-4 number whose most significant digit is cut 0.
+ *  - Subcircuit tensor T_c (caller-owned, device memory, row-major):
+ *        [4^k_in][4^k_out][2^n_eff]
+ *    k_in = init slots (rho_c, Eq. 5), k_out = measurement slots (O_c,
+ *    Eq. 6), n_eff = effective output qubits (f_c, Eq. 7).  Row (a, b):
+ *    a = digits of the init slots, b = digits of the measurement slots,
+ *    slot 0 most significant; in_cut[j] / out_cut[j] name the global cut id
+ *    of slot j.  Column x: bit i of x (bit 0 = most significant) is global
+ *    qubit out_qubit[i].  Entry = Tr[(P_x (x) P_b) U (rho_0 (x) P_a) U^+]
+ *    (Eq. 1-3): the Pauli-basis attribution of the subcircuit's variants.
+ *  - Every call is stream-ordered and asynchronous on `stream` (a
+ *    cudaStream_t; NULL = the legacy default stream) unless it says
+ *    otherwise.  Device pointers must be on the current device.  The caller
+ *    keeps inputs alive and unmodified until the stream has passed the call.
+ *  - The library owns a per-device workspace and a plan cache (device tables
+ *    derived from the problem's structure).  Both grow on demand with
+ *    cudaMalloc and persist until cutqc_release().  Calls from several host
+ *    threads are serialised internally.
+ *  - Errors: every entry point returns a cutqc_status.  Argument and shape
+ *    errors are detected on the host before anything is launched; the
+ *    message is available from cutqc_last_error() (thread-local).  No C++
+ *    exception crosses this boundary.  Kernels never trap: a device-side
+ *    check that fails writes a status word that the next synchronising
+ *    call reports as CUTQC_ERR_DEVICE.
+ *  - Limits: n_qubits <= 34 in full definition, #active <= 34 in dynamic
+ *    definition, n_qubits <= 4096 overall, K <= 12, n_sub <= 16.  Outside
+ *    them the call returns CUTQC_ERR_UNSUPPORTED.
+ */
+#ifndef CUTQC_H
+#define CUTQC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CUTQC_API __attribute__((visibility("default")))
+#else
+#define CUTQC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CUTQC_OK = 0,
+  CUTQC_ERR_ARG = -1,          /* null pointer, bad enum, bad count            */
+  CUTQC_ERR_SHAPE = -2,        /* inconsistent subcircuit / cut structure      */
+  CUTQC_ERR_OOM = -3,          /* workspace allocation failed                  */
+  CUTQC_ERR_CUDA = -4,         /* a CUDA runtime call failed                   */
+  CUTQC_ERR_UNSUPPORTED = -5,  /* outside the documented limits                */
+  CUTQC_ERR_TIMEOUT = -6,      /* a bounded device wait ran out                */
+  CUTQC_ERR_DEVICE = -7        /* a device-side check failed                   */
+} cutqc_status;
+
+typedef enum { CUTQC_F64 = 0, CUTQC_F32 = 1 } cutqc_dtype;
+
+/* How the main contraction (the 4^K sum) is computed.
+ *  CUTQC_CC        CUDA-core FMA in the tensors' dtype (FP64 or FP32): the
+ *                  plain baseline.
+ *  CUTQC_TC_BF16X3 tcgen05 tensor cores, each FP32 operand split into
+ *                  bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated
+ *                  in FP32 in tensor memory (FP32 tensors only).
+ *  CUTQC_AUTO      the planner picks (currently: CC for FP64, TC_BF16X3 for
+ *                  FP32 when the contraction is large enough). */
+typedef enum {
+  CUTQC_AUTO = 0,
+  CUTQC_CC = 1,
+  CUTQC_TC_BF16X3 = 2
+} cutqc_algo;
+
+/* One subcircuit (host struct; `tensor` is a device pointer). */
+typedef struct {
+  int32_t k_in, k_out, n_eff;
+  const int32_t* in_cut;     /* host [k_in]  cut id of each init slot        */
+  const int32_t* out_cut;    /* host [k_out] cut id of each measurement slot */
+  const int32_t* out_qubit;  /* host [n_eff] global qubit of each output bit */
+  const void* tensor;        /* device [4^k_in][4^k_out][2^n_eff], dtype     */
+} cutqc_subcircuit;
+
+/* One cut circuit.  Every cut id 0..n_cuts-1 must appear in exactly one
+ * in_cut and one out_cut; the out_qubit lists must partition 0..n_qubits-1. */
+typedef struct {
+  int32_t n_qubits, n_cuts, n_sub;
+  int32_t dtype;                  /* cutqc_dtype, the same for all tensors */
+  const cutqc_subcircuit* sub;    /* host [n_sub] */
+} cutqc_problem;
+
+/* Full definition (Sec. 4.2).  For each of n_problems cut circuits write all
+ * 2^n_qubits probabilities to out[i] (device, the problem's dtype, index =
+ * bit string with qubit 0 most significant).  Kronecker terms whose factor
+ * rows are all zero are skipped (early termination, Sec. 4.2).  sum_p:
+ * device double [n_problems] receiving sum_x p(x) accumulated in FP64, or
+ * NULL.  No host synchronisation. */
+CUTQC_API int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems,
+                         void* const* out, int32_t algo, double* sum_p,
+                         void* stream);
+
+/* Dynamic definition, one recursion (Sec. 4.3, Algorithm 1).
+ * role[q] (host, n_qubits entries): 0 active, 1 merged, 2 zoomed at 0,
+ * 3 zoomed at 1.  Writes the 2^#active bins (device, the problem's dtype;
+ * bin bit 0 = the lowest-numbered active qubit = most significant) = the
+ * probability summed over the merged qubits with the zoomed qubits fixed.
+ * If topk > 0, also returns on the host the topk heaviest bins ranked in FP64
+ * (each candidate re-evaluated from the tensors in FP64; ties to the lower
+ * index) in top_idx / top_val; this synchronises the stream. */
+CUTQC_API int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role,
+                         void* bins, int32_t topk, int64_t* top_idx,
+                         double* top_val, int32_t algo, void* stream);
+
+/* Loss kinds for the adjoint. */
+typedef enum { CUTQC_LOSS_NONE = 0, CUTQC_LOSS_MAXCUT = 1 } cutqc_loss_kind;
+
+typedef struct {
+  int32_t kind;              /* cutqc_loss_kind                                  */
+  int32_t n_edges;           /* MAXCUT: G(x) = number of edges cut by x          */
+  const int32_t* edges;      /* host [2*n_edges] qubit pairs                     */
+} cutqc_loss;
+
+/* Adjoint of the full definition: grad_tensor[c] (device, shape and dtype of
+ * T_c) receives dL/dT_c for L = sum_x G(x) p(x), where G = grad_out (device,
+ * 2^n entries, problem dtype) when loss is NULL or kind NONE, else the loss's
+ * G(x) generated on the fly.  loss_value: device double receiving L in FP64,
+ * or NULL.  No host synchronisation.  (Not in the paper: the gradient of an
+ * expectation value over the reconstructed distribution.) */
+CUTQC_API int cutqc_reconstruct_backward(const cutqc_problem* problem,
+                               const void* grad_out, const cutqc_loss* loss,
+                               void* const* grad_tensor, double* loss_value,
+                               void* stream);
+
+/* ---- input preparation: the GPU subcircuit simulator -------------------- */
+
+typedef enum {
+  CUTQC_GATE_H = 0, CUTQC_GATE_X, CUTQC_GATE_Y, CUTQC_GATE_Z, CUTQC_GATE_S,
+  CUTQC_GATE_SDG, CUTQC_GATE_T, CUTQC_GATE_SX, CUTQC_GATE_SY, CUTQC_GATE_SW,
+  CUTQC_GATE_RX, CUTQC_GATE_RY, CUTQC_GATE_RZ,
+  CUTQC_GATE_CZ, CUTQC_GATE_CX, CUTQC_GATE_CP
+} cutqc_gate_op;
+
+typedef struct {
+  int32_t op;        /* cutqc_gate_op                                         */
+  int32_t q0, q1;    /* local qubits (q1 unused for 1-qubit gates; for CX q0
+                        is the control)                                        */
+  double param;      /* angle for RX/RY/RZ/CP                                 */
+} cutqc_gate;
+
+/* Produce one subcircuit's attributed tensor on the GPU (Fig. 3, Eq. 2-3):
+ * simulates, in complex FP64, every variant (each init slot in |0>, |1>,
+ * |+>, |+i>; each measurement slot measured in the Z, X, Y basis) of a
+ * d-qubit subcircuit whose other qubits start in |0>, attributes the measured
+ * cut qubits' outcomes with +-1 (Eq. 3) and combines the init variants into
+ * Pauli operators (Eq. 2).  Entries below 2^-40 in magnitude become 0.
+ * init_qubit[k_in], meas_qubit[k_out], out_local[n_eff]: host arrays of local
+ * qubits (local qubit 0 = most significant).  tensor: device
+ * [4^k_in][4^k_out][2^n_eff] of `dtype`.  d <= 30.  Synchronises the stream
+ * (it allocates and frees temporary state buffers). */
+CUTQC_API int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates,
+                              int32_t d, const int32_t* init_qubit,
+                              int32_t k_in, const int32_t* meas_qubit,
+                              int32_t k_out, const int32_t* out_local,
+                              int32_t n_eff, int32_t dtype, void* tensor,
+                              void* stream);
+
+/* ---- housekeeping -------------------------------------------------------- */
+
+/* Message for the last non-OK status returned on this thread. */
+CUTQC_API const char* cutqc_last_error(void);
+
+/* Free the workspace and plan cache of every device. */
+CUTQC_API void cutqc_release(void);
+
+/* Number of kernels this library has launched since load (all devices). */
+CUTQC_API int64_t cutqc_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUTQC_H */

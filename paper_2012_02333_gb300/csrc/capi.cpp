@@ -1,0 +1,604 @@
+// The C ABI (include/cutqc.h): validation, the contraction planner, the
+// per-device workspace and plan cache, and the host side of every call.
+//
+// Planner.  A cut circuit with S subcircuits is reduced to one contraction
+// between two groups (Sec. 3.3: the 4^K Kronecker products).  While more than
+// two nodes remain, the pair of connected nodes whose merged tensor is
+// smallest is merged first (the greedy "smallest subcircuits first" order of
+// Sec. 4.2, which keeps the carried-over vectors small); a merge is itself a
+// batched contraction over the cuts internal to the pair, batched over the
+// pair's remaining open cuts, with the output bits concatenated.  The last
+// contraction deposits its (m, n) pairs into the uncut circuit's output index.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <functional>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "internal.h"
+
+namespace cutqc {
+
+// ------------------------------------------------------------------ errors
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+static std::recursive_mutex g_mu;
+
+void fail(int status, const std::string& msg) { throw Error{status, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    const int st = (e == cudaErrorMemoryAllocation) ? CUTQC_ERR_OOM : CUTQC_ERR_CUDA;
+    fail(st, std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+void count_launch(int n) { g_launches += n; }
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(CUTQC_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
+}
+
+template <class F>
+static int guarded(F&& f) {
+  std::lock_guard<std::recursive_mutex> lk(g_mu);
+  try {
+    f();
+    return CUTQC_OK;
+  } catch (const Error& e) {
+    g_last_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return CUTQC_ERR_OOM;
+  } catch (...) {
+    g_last_error = "unexpected internal error";
+    return CUTQC_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------------------- validation
+static constexpr int kMaxCuts = 12;
+static constexpr int kMaxSub = 16;
+static constexpr int kMaxFD = 34;
+static constexpr int kMaxQubits = 4096;
+
+static size_t dtype_size(int dt) { return dt == CUTQC_F64 ? 8 : 4; }
+
+static void validate(const cutqc_problem* p, bool need_tensors) {
+  if (!p) fail(CUTQC_ERR_ARG, "problem is NULL");
+  if (p->dtype != CUTQC_F32 && p->dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "dtype must be CUTQC_F32 or CUTQC_F64");
+  if (p->n_sub < 1 || !p->sub) fail(CUTQC_ERR_ARG, "need n_sub >= 1 subcircuits");
+  if (p->n_sub > kMaxSub) fail(CUTQC_ERR_UNSUPPORTED, "n_sub > 16");
+  if (p->n_qubits < 1) fail(CUTQC_ERR_SHAPE, "n_qubits must be >= 1");
+  if (p->n_qubits > kMaxQubits) fail(CUTQC_ERR_UNSUPPORTED, "n_qubits > 4096");
+  if (p->n_cuts < 0) fail(CUTQC_ERR_SHAPE, "n_cuts must be >= 0");
+  if (p->n_cuts > kMaxCuts) fail(CUTQC_ERR_UNSUPPORTED, "n_cuts > 12");
+  std::vector<int> in_seen(p->n_cuts, -1), out_seen(p->n_cuts, -1), q_seen(p->n_qubits, 0);
+  int total_eff = 0;
+  for (int c = 0; c < p->n_sub; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    if (s.k_in < 0 || s.k_out < 0 || s.n_eff < 0) fail(CUTQC_ERR_SHAPE, "negative slot or output count");
+    if (s.k_in + s.k_out > kMaxCuts) fail(CUTQC_ERR_UNSUPPORTED, "subcircuit has more than 12 cut slots");
+    if (s.n_eff > 40) fail(CUTQC_ERR_UNSUPPORTED, "subcircuit has more than 40 output qubits");
+    if ((s.k_in && !s.in_cut) || (s.k_out && !s.out_cut) || (s.n_eff && !s.out_qubit))
+      fail(CUTQC_ERR_ARG, "NULL slot or output array");
+    if (need_tensors && !s.tensor) fail(CUTQC_ERR_ARG, "NULL tensor pointer");
+    for (int j = 0; j < s.k_in; ++j) {
+      const int k = s.in_cut[j];
+      if (k < 0 || k >= p->n_cuts) fail(CUTQC_ERR_SHAPE, "init slot names a cut id out of range");
+      if (in_seen[k] >= 0) fail(CUTQC_ERR_SHAPE, "cut id appears in two init slots");
+      in_seen[k] = c;
+    }
+    for (int j = 0; j < s.k_out; ++j) {
+      const int k = s.out_cut[j];
+      if (k < 0 || k >= p->n_cuts) fail(CUTQC_ERR_SHAPE, "measurement slot names a cut id out of range");
+      if (out_seen[k] >= 0) fail(CUTQC_ERR_SHAPE, "cut id appears in two measurement slots");
+      out_seen[k] = c;
+    }
+    for (int i = 0; i < s.n_eff; ++i) {
+      const int q = s.out_qubit[i];
+      if (q < 0 || q >= p->n_qubits) fail(CUTQC_ERR_SHAPE, "output qubit out of range");
+      if (q_seen[q]) fail(CUTQC_ERR_SHAPE, "output qubit appears twice");
+      q_seen[q] = 1;
+    }
+    total_eff += s.n_eff;
+  }
+  for (int k = 0; k < p->n_cuts; ++k) {
+    if (in_seen[k] < 0 || out_seen[k] < 0) fail(CUTQC_ERR_SHAPE, "cut id without both an init and a measurement slot");
+    if (in_seen[k] == out_seen[k]) fail(CUTQC_ERR_SHAPE, "cut joins a subcircuit to itself");
+  }
+  if (total_eff != p->n_qubits) fail(CUTQC_ERR_SHAPE, "output qubits do not cover n_qubits");
+}
+
+// ------------------------------------------------------------------ plans
+struct Node {
+  std::vector<int> cuts;    // open cut ids, row digit order (first = most significant)
+  std::vector<int> bits;    // output position of each x bit (x bit 0 = most significant)
+  int orig = -1;            // original subcircuit, or -1 for a merge result
+  int f() const { return (int)bits.size(); }
+  int64_t rows() const { return int64_t(1) << (2 * cuts.size()); }
+};
+
+struct Step {
+  int a = -1, b = -1, result = -1;    // node indices (result -1: final output)
+  int batch = 1, kmax = 1;
+  std::vector<int32_t> rows;          // [batch][2][kmax]
+  std::vector<uint64_t> depA, depB;   // [ceil(f/8)][256]
+  uint64_t out_stride = 0;
+  int vecB = 1;
+  size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
+  size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
+};
+
+struct Plan {
+  int n_out = 0, K = 0, dtype = CUTQC_F32;
+  std::vector<Node> nodes;
+  std::vector<Step> steps;
+  std::vector<size_t> ws_node;    // workspace offset of each merge-result tensor
+  std::vector<size_t> ws_nz;      // workspace offset of each node's row flags
+  size_t ws_bytes = 0;
+  void* dtab = nullptr;
+  size_t dtab_bytes = 0;
+  ~Plan() {
+    if (dtab) cudaFree(dtab);
+  }
+};
+
+struct DeviceState {
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* one = nullptr;            // a device constant 1.0 (f64) / 1.0f (f32)
+  std::unordered_map<std::string, std::unique_ptr<Plan>> plans;
+  std::vector<std::string> order;
+};
+static std::map<int, DeviceState> g_dev;
+
+static DeviceState& device_state() {
+  int dev = 0;
+  CUTQC_CUDA(cudaGetDevice(&dev));
+  return g_dev[dev];
+}
+
+static void* workspace(DeviceState& ds, size_t bytes) {
+  if (bytes > ds.ws_bytes) {
+    if (ds.ws) CUTQC_CUDA(cudaFree(ds.ws));
+    ds.ws = nullptr;
+    ds.ws_bytes = 0;
+    const size_t want = std::max(bytes, size_t(1) << 20);
+    CUTQC_CUDA(cudaMalloc(&ds.ws, want));
+    ds.ws_bytes = want;
+  }
+  return ds.ws;
+}
+
+static size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// deposit tables for one side: entry [byte][v] = sum over set bits j of v of
+// the output bit value of index bit (8*byte + j) (index bit 0 = least
+// significant = the node's last x bit)
+static std::vector<uint64_t> deposit_table(const std::vector<uint64_t>& bitval) {
+  const int f = (int)bitval.size();
+  const int nb = (f + 7) / 8;
+  std::vector<uint64_t> t(std::max(nb, 1) * 256, 0);
+  for (int b = 0; b < nb; ++b)
+    for (int v = 0; v < 256; ++v) {
+      uint64_t g = 0;
+      for (int j = 0; j < 8; ++j)
+        if ((v >> j) & 1) {
+          const int ib = 8 * b + j;
+          if (ib < f) g += bitval[ib];
+        }
+      t[b * 256 + v] = g;
+    }
+  return t;
+}
+
+static int64_t row_index(const Node& nd, const std::vector<int>& digit) {
+  int64_t r = 0;
+  for (int c : nd.cuts) r = 4 * r + digit[c];
+  return r;
+}
+
+// Build the contraction of nodes a and b.  result >= 0: a merge whose output
+// node has open cuts `open` and bits a.bits ++ b.bits; result < 0: the final
+// contraction into n_out output bits.
+static Step make_step(Plan& P, int ia, int ib, int result, const std::vector<int>& open, int ncuts_total) {
+  const Node& A = P.nodes[ia];
+  const Node& B = P.nodes[ib];
+  std::vector<int> inner;
+  for (int c : A.cuts)
+    if (std::find(B.cuts.begin(), B.cuts.end(), c) != B.cuts.end()) inner.push_back(c);
+  std::sort(inner.begin(), inner.end());
+  Step st;
+  st.a = ia;
+  st.b = ib;
+  st.result = result;
+  st.batch = 1 << (2 * open.size());
+  st.kmax = 1 << (2 * inner.size());
+  st.rows.resize((size_t)st.batch * 2 * st.kmax);
+  std::vector<int> digit(std::max(ncuts_total, 1), 0);
+  for (int bt = 0; bt < st.batch; ++bt) {
+    for (size_t j = 0; j < open.size(); ++j) digit[open[j]] = (bt >> (2 * (open.size() - 1 - j))) & 3;
+    for (int k = 0; k < st.kmax; ++k) {
+      for (size_t j = 0; j < inner.size(); ++j) digit[inner[j]] = (k >> (2 * (inner.size() - 1 - j))) & 3;
+      st.rows[(size_t)bt * 2 * st.kmax + k] = (int32_t)row_index(A, digit);
+      st.rows[(size_t)bt * 2 * st.kmax + st.kmax + k] = (int32_t)row_index(B, digit);
+    }
+  }
+  const int fA = A.f(), fB = B.f();
+  std::vector<uint64_t> va(fA), vb(fB);
+  if (result >= 0) {
+    // concatenation: x = (xA, xB), xB in the low bits
+    for (int i = 0; i < fA; ++i) va[i] = uint64_t(1) << (fB + i);
+    for (int i = 0; i < fB; ++i) vb[i] = uint64_t(1) << i;
+    st.out_stride = uint64_t(1) << (fA + fB);
+    st.vecB = 4;
+  } else {
+    // index bit i (from the least significant) of m is x bit f-1-i
+    for (int i = 0; i < fA; ++i) va[i] = uint64_t(1) << (P.n_out - 1 - A.bits[fA - 1 - i]);
+    for (int i = 0; i < fB; ++i) vb[i] = uint64_t(1) << (P.n_out - 1 - B.bits[fB - 1 - i]);
+    st.out_stride = 0;
+    int run = 0;
+    while (run < fB && run < 2 && vb[run] == (uint64_t(1) << run)) ++run;
+    st.vecB = 1 << run;
+  }
+  st.depA = deposit_table(va);
+  st.depB = deposit_table(vb);
+  return st;
+}
+
+// Plan a problem whose nodes are given (original subcircuits, or merged DD
+// tensors) with output positions already in the nodes' bits.
+static void plan_contractions(Plan& P, int ncuts) {
+  std::vector<int> live;
+  for (size_t i = 0; i < P.nodes.size(); ++i) live.push_back((int)i);
+  auto shared = [&](int i, int j) {
+    int s = 0;
+    for (int c : P.nodes[i].cuts)
+      if (std::find(P.nodes[j].cuts.begin(), P.nodes[j].cuts.end(), c) != P.nodes[j].cuts.end()) ++s;
+    return s;
+  };
+  while (live.size() > 2) {
+    // the connected pair with the smallest merged tensor (ties: lowest indices)
+    double best = -1;
+    int bi = -1, bj = -1;
+    bool best_conn = false;
+    for (size_t x = 0; x < live.size(); ++x)
+      for (size_t y = x + 1; y < live.size(); ++y) {
+        const int i = live[x], j = live[y];
+        const int sh = shared(i, j);
+        const int open = (int)(P.nodes[i].cuts.size() + P.nodes[j].cuts.size()) - 2 * sh;
+        const double size = std::ldexp(1.0, 2 * open + P.nodes[i].f() + P.nodes[j].f());
+        const bool conn = sh > 0;
+        if (bi < 0 || (conn && !best_conn) || (conn == best_conn && size < best)) {
+          best = size;
+          bi = i;
+          bj = j;
+          best_conn = conn;
+        }
+      }
+    Node m;
+    for (int c : P.nodes[bi].cuts)
+      if (std::find(P.nodes[bj].cuts.begin(), P.nodes[bj].cuts.end(), c) == P.nodes[bj].cuts.end()) m.cuts.push_back(c);
+    for (int c : P.nodes[bj].cuts)
+      if (std::find(P.nodes[bi].cuts.begin(), P.nodes[bi].cuts.end(), c) == P.nodes[bi].cuts.end()) m.cuts.push_back(c);
+    std::sort(m.cuts.begin(), m.cuts.end());
+    m.bits = P.nodes[bi].bits;
+    m.bits.insert(m.bits.end(), P.nodes[bj].bits.begin(), P.nodes[bj].bits.end());
+    if (m.rows() * (int64_t(1) << m.f()) > (int64_t(1) << 36))
+      fail(CUTQC_ERR_UNSUPPORTED, "an intermediate group tensor would exceed 2^36 entries");
+    P.nodes.push_back(m);
+    const int r = (int)P.nodes.size() - 1;
+    P.steps.push_back(make_step(P, bi, bj, r, m.cuts, ncuts));
+    live.erase(std::find(live.begin(), live.end(), bi));
+    live.erase(std::find(live.begin(), live.end(), bj));
+    live.push_back(r);
+  }
+  if (live.size() == 1) {
+    // no partner: contract with a constant 1 node (f = 0, no cuts)
+    Node one;
+    one.orig = -2;
+    P.nodes.push_back(one);
+    live.push_back((int)P.nodes.size() - 1);
+  }
+  int a = live[0], b = live[1];
+  // the N side (vector stores) is the node holding the lowest output bit
+  auto holds_last = [&](int i) {
+    for (int pos : P.nodes[i].bits)
+      if (pos == P.n_out - 1) return true;
+    return false;
+  };
+  if (holds_last(a) && !holds_last(b)) std::swap(a, b);
+  P.steps.push_back(make_step(P, a, b, -1, {}, ncuts));
+}
+
+static void finalize_plan(Plan& P) {
+  // device tables
+  size_t off = 0;
+  for (Step& st : P.steps) {
+    st.off_rows = off;
+    off = align_up(off + st.rows.size() * 4);
+    st.off_depA = off;
+    off = align_up(off + st.depA.size() * 8);
+    st.off_depB = off;
+    off = align_up(off + st.depB.size() * 8);
+  }
+  P.dtab_bytes = std::max<size_t>(off, 256);
+  CUTQC_CUDA(cudaMalloc(&P.dtab, P.dtab_bytes));
+  std::vector<char> host(P.dtab_bytes, 0);
+  for (Step& st : P.steps) {
+    std::memcpy(host.data() + st.off_rows, st.rows.data(), st.rows.size() * 4);
+    std::memcpy(host.data() + st.off_depA, st.depA.data(), st.depA.size() * 8);
+    std::memcpy(host.data() + st.off_depB, st.depB.data(), st.depB.size() * 8);
+  }
+  CUTQC_CUDA(cudaMemcpy(P.dtab, host.data(), P.dtab_bytes, cudaMemcpyHostToDevice));
+  // workspace layout: merge results, row flags, compacted rows, counts
+  size_t w = 0;
+  const size_t es = dtype_size(P.dtype);
+  P.ws_node.assign(P.nodes.size(), 0);
+  P.ws_nz.assign(P.nodes.size(), 0);
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    if (P.nodes[i].orig == -1) {
+      P.ws_node[i] = w;
+      w = align_up(w + (size_t)P.nodes[i].rows() * ((size_t)1 << P.nodes[i].f()) * es);
+    }
+  }
+  for (size_t i = 0; i < P.nodes.size(); ++i) {
+    P.ws_nz[i] = w;
+    w = align_up(w + (size_t)P.nodes[i].rows() * 4);
+  }
+  for (Step& st : P.steps) {
+    st.ws_crow = w;
+    w = align_up(w + st.rows.size() * 4);
+    st.ws_kcount = w;
+    w = align_up(w + (size_t)st.batch * 4);
+  }
+  P.ws_bytes = w;
+}
+
+static std::string fd_key(const cutqc_problem* p, int mode, const int8_t* role, int algo) {
+  std::ostringstream o;
+  o << mode << ':' << algo << ':' << p->n_qubits << ',' << p->n_cuts << ',' << p->n_sub << ',' << p->dtype << '|';
+  for (int c = 0; c < p->n_sub; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    o << s.k_in << ',' << s.k_out << ',' << s.n_eff << ':';
+    for (int j = 0; j < s.k_in; ++j) o << s.in_cut[j] << ',';
+    o << ';';
+    for (int j = 0; j < s.k_out; ++j) o << s.out_cut[j] << ',';
+    o << ';';
+    for (int j = 0; j < s.n_eff; ++j) o << s.out_qubit[j] << ',';
+    o << '|';
+  }
+  if (role)
+    for (int q = 0; q < p->n_qubits; ++q) o << (int)role[q];
+  return o.str();
+}
+
+static Plan& get_plan(DeviceState& ds, const std::string& key, const std::function<void(Plan&)>& build) {
+  auto it = ds.plans.find(key);
+  if (it != ds.plans.end()) return *it->second;
+  if (ds.plans.size() >= 64) {
+    ds.plans.erase(ds.order.front());
+    ds.order.erase(ds.order.begin());
+  }
+  auto P = std::make_unique<Plan>();
+  build(*P);
+  Plan& ref = *P;
+  ds.plans.emplace(key, std::move(P));
+  ds.order.push_back(key);
+  return ref;
+}
+
+static void build_fd_plan(Plan& P, const cutqc_problem* p) {
+  P.n_out = p->n_qubits;
+  P.K = p->n_cuts;
+  P.dtype = p->dtype;
+  for (int c = 0; c < p->n_sub; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    Node nd;
+    nd.orig = c;
+    for (int j = 0; j < s.k_in; ++j) nd.cuts.push_back(s.in_cut[j]);
+    for (int j = 0; j < s.k_out; ++j) nd.cuts.push_back(s.out_cut[j]);
+    for (int i = 0; i < s.n_eff; ++i) nd.bits.push_back(s.out_qubit[i]);
+    P.nodes.push_back(nd);
+  }
+  plan_contractions(P, p->n_cuts);
+  finalize_plan(P);
+}
+
+// Run a plan.  `tensor(i)` gives the device pointer of original node i.
+static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& orig_tensor, void* out,
+                     double* sum, int algo, cudaStream_t s) {
+  size_t tc_ws = 0;
+  std::vector<Contraction> cs(P.steps.size());
+  char* base = nullptr;
+  // the constant-one node
+  if (!ds.one) {
+    CUTQC_CUDA(cudaMalloc(&ds.one, 16));
+    const double one64 = 1.0;
+    const float one32 = 1.0f;
+    CUTQC_CUDA(cudaMemcpy(ds.one, &one64, 8, cudaMemcpyHostToDevice));
+    CUTQC_CUDA(cudaMemcpy(static_cast<char*>(ds.one) + 8, &one32, 4, cudaMemcpyHostToDevice));
+  }
+  const void* one = P.dtype == CUTQC_F64 ? ds.one : static_cast<char*>(ds.one) + 8;
+  // decide the algorithm of the final step
+  const Step& last = P.steps.back();
+  int final_algo = algo;
+  if (final_algo == CUTQC_AUTO) final_algo = (P.dtype == CUTQC_F32) ? CUTQC_TC_BF16X3 : CUTQC_CC;
+  if (final_algo == CUTQC_TC_BF16X3 && P.dtype != CUTQC_F32)
+    fail(CUTQC_ERR_ARG, "CUTQC_TC_BF16X3 needs FP32 tensors");
+  for (size_t i = 0; i < P.steps.size(); ++i) {
+    Contraction& c = cs[i];
+    const Step& st = P.steps[i];
+    c.fA = P.nodes[st.a].f();
+    c.fB = P.nodes[st.b].f();
+    c.batch = st.batch;
+    c.kmax = st.kmax;
+    c.out_batch_stride = st.out_stride;
+    c.vecB = st.vecB;
+    c.dtype = P.dtype;
+    c.scale = (i + 1 == P.steps.size()) ? std::ldexp(1.0, -P.K) : 1.0;
+    c.rowsA = (int)P.nodes[st.a].rows();
+    c.rowsB = (int)P.nodes[st.b].rows();
+  }
+  size_t need = P.ws_bytes;
+  const bool use_tc_final = (final_algo == CUTQC_TC_BF16X3) && tc_supported(cs.back());
+  if (use_tc_final) {
+    tc_ws = tc_workspace_bytes(cs.back());
+    need = align_up(need) + tc_ws;
+  }
+  base = static_cast<char*>(workspace(ds, need));
+  auto node_ptr = [&](int i) -> const void* {
+    const Node& nd = P.nodes[i];
+    if (nd.orig >= 0) return orig_tensor[nd.orig];
+    if (nd.orig == -2) return one;
+    return base + P.ws_node[i];
+  };
+  auto dtab = static_cast<char*>(P.dtab);
+  // row flags of the original operands
+  std::vector<int> flagged(P.nodes.size(), 0);
+  auto ensure_flags = [&](int i) {
+    if (flagged[i]) return;
+    const Node& nd = P.nodes[i];
+    launch_row_nonzero(node_ptr(i), P.dtype, (int)nd.rows(), nd.f(), reinterpret_cast<int32_t*>(base + P.ws_nz[i]), s);
+    flagged[i] = 1;
+  };
+  if (sum) CUTQC_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
+  for (size_t i = 0; i < P.steps.size(); ++i) {
+    const Step& st = P.steps[i];
+    Contraction& c = cs[i];
+    ensure_flags(st.a);
+    ensure_flags(st.b);
+    c.A = node_ptr(st.a);
+    c.B = node_ptr(st.b);
+    c.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
+    c.depA = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
+    c.depB = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
+    c.crow = reinterpret_cast<int32_t*>(base + st.ws_crow);
+    c.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
+    c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
+    c.nzB = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.b]);
+    const bool final_step = (i + 1 == P.steps.size());
+    c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
+    c.sum = final_step ? sum : nullptr;
+    launch_compact(c, s);
+    if (final_step && use_tc_final)
+      launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s);
+    else
+      launch_cc_gemm(c, s);
+  }
+}
+
+}  // namespace cutqc
+
+using namespace cutqc;
+
+extern "C" {
+
+int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void* const* out, int32_t algo,
+                         double* sum_p, void* stream) {
+  return guarded([&] {
+    if (!problems || n_problems < 1) fail(CUTQC_ERR_ARG, "need n_problems >= 1 problems");
+    if (!out) fail(CUTQC_ERR_ARG, "out is NULL");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X3) fail(CUTQC_ERR_ARG, "unknown algo");
+    for (int i = 0; i < n_problems; ++i) {
+      validate(&problems[i], true);
+      if (problems[i].n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
+      if (!out[i]) fail(CUTQC_ERR_ARG, "out[i] is NULL");
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceState& ds = device_state();
+    for (int i = 0; i < n_problems; ++i) {
+      const cutqc_problem* p = &problems[i];
+      Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
+      std::vector<const void*> t(p->n_sub);
+      for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
+      run_plan(ds, P, t, out[i], sum_p ? sum_p + i : nullptr, algo, s);
+    }
+  });
+}
+
+int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates, int32_t d, const int32_t* init_qubit,
+                              int32_t k_in, const int32_t* meas_qubit, int32_t k_out, const int32_t* out_local,
+                              int32_t n_eff, int32_t dtype, void* tensor, void* stream) {
+  return guarded([&] {
+    if (d < 1 || d > 30) fail(CUTQC_ERR_UNSUPPORTED, "simulator needs 1 <= d <= 30");
+    if (n_gates < 0 || (n_gates && !gates)) fail(CUTQC_ERR_ARG, "bad gate list");
+    if (k_in < 0 || k_out < 0 || n_eff < 0 || k_in + k_out > kMaxCuts) fail(CUTQC_ERR_SHAPE, "bad slot counts");
+    if (k_out + n_eff != d) fail(CUTQC_ERR_SHAPE, "every local qubit must be an output or a measured cut qubit");
+    if ((k_in && !init_qubit) || (k_out && !meas_qubit) || (n_eff && !out_local) || !tensor)
+      fail(CUTQC_ERR_ARG, "NULL array");
+    if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
+    std::vector<int> seen(d, 0);
+    SimPlan sp;
+    sp.d = d;
+    sp.k_in = k_in;
+    sp.k_out = k_out;
+    sp.n_eff = n_eff;
+    for (int j = 0; j < k_in; ++j) {
+      if (init_qubit[j] < 0 || init_qubit[j] >= d) fail(CUTQC_ERR_SHAPE, "init qubit out of range");
+      sp.init_q.push_back(init_qubit[j]);
+    }
+    for (int j = 0; j < k_out; ++j) {
+      if (meas_qubit[j] < 0 || meas_qubit[j] >= d || seen[meas_qubit[j]]++) fail(CUTQC_ERR_SHAPE, "bad measured qubit");
+      sp.meas_q.push_back(meas_qubit[j]);
+    }
+    for (int j = 0; j < n_eff; ++j) {
+      if (out_local[j] < 0 || out_local[j] >= d || seen[out_local[j]]++) fail(CUTQC_ERR_SHAPE, "bad output qubit");
+      sp.out_q.push_back(out_local[j]);
+    }
+    for (int g = 0; g < n_gates; ++g) {
+      const cutqc_gate& gt = gates[g];
+      if (gt.op < CUTQC_GATE_H || gt.op > CUTQC_GATE_CP) fail(CUTQC_ERR_ARG, "unknown gate op");
+      if (gt.q0 < 0 || gt.q0 >= d) fail(CUTQC_ERR_SHAPE, "gate qubit out of range");
+      if (gt.op >= CUTQC_GATE_CZ && (gt.q1 < 0 || gt.q1 >= d || gt.q1 == gt.q0)) fail(CUTQC_ERR_SHAPE, "bad two-qubit gate");
+      sp.gates.push_back(gt);
+    }
+    run_subcircuit_sim(sp, dtype, tensor, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void* bins, int32_t topk,
+                         int64_t* top_idx, double* top_val, int32_t algo, void* stream) {
+  return guarded([&] { fail(CUTQC_ERR_UNSUPPORTED, "dynamic definition is not built yet"); });
+}
+
+int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_out, const cutqc_loss* loss,
+                               void* const* grad_tensor, double* loss_value, void* stream) {
+  return guarded([&] { fail(CUTQC_ERR_UNSUPPORTED, "backward is not built yet"); });
+}
+
+const char* cutqc_last_error(void) { return g_last_error.c_str(); }
+
+void cutqc_release(void) {
+  std::lock_guard<std::recursive_mutex> lk(g_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_dev) {
+    cudaSetDevice(kv.first);
+    kv.second.plans.clear();
+    kv.second.order.clear();
+    if (kv.second.ws) cudaFree(kv.second.ws);
+    if (kv.second.one) cudaFree(kv.second.one);
+    kv.second.ws = nullptr;
+    kv.second.one = nullptr;
+    kv.second.ws_bytes = 0;
+  }
+  g_dev.clear();
+  cudaSetDevice(cur);
+}
+
+int64_t cutqc_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+// Nothing here crosses the C ABI (include/cutqc.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cutqc.h"
+
+namespace cutqc {
+
+// ---------------------------------------------------------------- errors
+// Thrown inside the library only; every entry point converts it to a status.
+struct Error {
+  int status;
+  std::string msg;
+};
+[[noreturn]] void fail(int status, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define CUTQC_CUDA(call) ::cutqc::check_cuda((call), #call)
+
+void count_launch(int n = 1);
+void check_launch(const char* what);
+
+// Device status word values (written by kernels, read at sync points).
+enum DeviceStatus : int { DEV_OK = 0, DEV_BAD_INDEX = 1, DEV_TIMEOUT = 2 };
+
+// ------------------------------------------------------ the contraction
+// One batched contraction (the 4^K sum between two groups of subcircuits):
+//   out[batch][g] = scale * sum_k A[rowA(batch,k)][m] * B[rowB(batch,k)][n]
+// with g = depA(m) + depB(n) (bit deposit into the output index) and
+// m in [0, 2^fA), n in [0, 2^fB).
+struct Contraction {
+  const void* A = nullptr;      // device, [rowsA][2^fA] row-major
+  const void* B = nullptr;      // device, [rowsB][2^fB]
+  int fA = 0, fB = 0;
+  int batch = 1;                // independent outputs (group builds)
+  int kmax = 1;                 // inner extent before compaction
+  const int32_t* rows = nullptr;   // device [batch][2][kmax]: rowA, rowB
+  int32_t* crow = nullptr;         // device [batch][2][kmax]: compacted rows
+  int32_t* kcount = nullptr;       // device [batch]: compacted inner extent
+  const uint64_t* depA = nullptr;  // device [ceil(fA/8)][256]
+  const uint64_t* depB = nullptr;  // device [ceil(fB/8)][256]
+  uint64_t out_batch_stride = 0;   // elements between batch outputs
+  void* out = nullptr;
+  double scale = 1.0;
+  double* sum = nullptr;           // device double or null
+  int vecB = 1;                    // consecutive n -> consecutive g run length (1, 2, 4)
+  int dtype = CUTQC_F32;
+  const int32_t* nzA = nullptr;    // device row non-zero flags of A (or null)
+  const int32_t* nzB = nullptr;
+  int rowsA = 0, rowsB = 0;
+};
+
+// k_cc.cu
+void launch_row_nonzero(const void* T, int dtype, int rows, int f, int32_t* flags, cudaStream_t s);
+void launch_compact(const Contraction& c, cudaStream_t s);
+void launch_cc_gemm(const Contraction& c, cudaStream_t s);
+void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
+
+// k_tc.cu
+bool tc_supported(const Contraction& c);
+void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s);
+size_t tc_workspace_bytes(const Contraction& c);
+
+// k_sim.cu
+struct SimPlan {
+  int d, k_in, k_out, n_eff;
+  std::vector<int32_t> init_q, meas_q, out_q;
+  std::vector<cutqc_gate> gates;
+};
+void run_subcircuit_sim(const SimPlan& p, int dtype, void* tensor, cudaStream_t s);
+
+}  // namespace cutqc

@@ -1,0 +1,332 @@
+// CUDA-core reconstruction: the plain FP32 / FP64 baseline of the 4^K sum.
+//
+// The sum over cut assignments between two groups of subcircuits is a
+// contraction over the Pauli index (Sec. 3.3: 4^K Kronecker products):
+//   P[m][n] = 2^-K sum_e A[e][m] B[e][n],
+// with A, B the groups' tensors addressed through row maps e -> row.  Terms
+// whose A row or B row is all zero are skipped first (early termination,
+// Sec. 4.2) by a stable compaction of the inner index.  The epilogue deposits
+// (m, n) into the output index g = depA(m) + depB(n) (the Kronecker product's
+// bit interleave; qubit 0 = most significant bit) and accumulates sum_x p(x)
+// in FP64.
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace cutqc {
+
+namespace {
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int W = 2; };
+
+__device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, int nbytes, uint64_t v) {
+  uint64_t g = 0;
+  for (int b = 0; b < nbytes; ++b) g += __ldg(tab + b * 256 + ((v >> (8 * b)) & 255));
+  return g;
+}
+
+// ---- row non-zero flags (one block per row) -------------------------------
+template <typename T>
+__global__ void k_row_nonzero(const T* __restrict__ t, int64_t cols, int32_t* __restrict__ flags) {
+  const T* row = t + (int64_t)blockIdx.x * cols;
+  int nz = 0;
+  for (int64_t i = threadIdx.x; i < cols && !nz; i += blockDim.x) nz = (row[i] != T(0));
+  nz = __syncthreads_or(nz);
+  if (threadIdx.x == 0) flags[blockIdx.x] = nz;
+}
+
+// ---- stable compaction of the inner index (one block per batch) ----------
+__global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int32_t* __restrict__ nzA,
+                          const int32_t* __restrict__ nzB, int32_t* __restrict__ crow,
+                          int32_t* __restrict__ kcount) {
+  __shared__ int warp_tot[32];
+  __shared__ int base;
+  const int b = blockIdx.x;
+  const int32_t* ra = rows + (int64_t)b * 2 * kmax;
+  const int32_t* rb = ra + kmax;
+  int32_t* ca = crow + (int64_t)b * 2 * kmax;
+  int32_t* cb = ca + kmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int k0 = 0; k0 < kmax; k0 += blockDim.x) {
+    const int k = k0 + threadIdx.x;
+    int keep = 0, a = 0, bb = 0;
+    if (k < kmax) {
+      a = ra[k];
+      bb = rb[k];
+      keep = (nzA ? nzA[a] : 1) && (nzB ? nzB[bb] : 1);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    const int before = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) off += warp_tot[w];
+      tot += warp_tot[w];
+    }
+    if (keep) {
+      ca[base + off + before] = a;
+      cb[base + off + before] = bb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) kcount[b] = base;
+}
+
+// ---- the CUDA-core contraction ---------------------------------------------
+template <typename T>
+struct CCArgs {
+  const T* A;
+  const T* B;
+  int64_t M, N;           // 2^fA, 2^fB (also the row strides)
+  int kmax;
+  const int32_t* crow;    // [batch][2][kmax]
+  const int32_t* kcount;  // [batch]
+  const uint64_t* depA;
+  const uint64_t* depB;
+  int nbA, nbB;
+  uint64_t out_batch_stride;
+  T* out;
+  T scale;
+  double* sum;
+  int vecB;
+  int64_t tilesN;
+};
+
+// Block tile BM x BN, inner step BK, 256 threads as 16 x 16, each thread a
+// (TM x TN) micro-tile split in two halves per dimension (rows ty*TM/2 + i
+// and BM/2 + ty*TM/2 + i), so shared-memory reads are conflict-free float4s.
+template <typename T, int BM, int BN, int BK>
+__global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
+  constexpr int TM = BM / 16, TN = BN / 16, HM = TM / 2, HN = TN / 2;
+  constexpr int W = Vec<T>::W;
+  using V = typename Vec<T>::type;
+  static_assert(BK * BM / W == 256 && BK * BN / W == 256, "one vector load per thread");
+  __shared__ __align__(16) T As[2][BK][BM];
+  __shared__ __align__(16) T Bs[2][BK][BN];
+  __shared__ double red[8];
+
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int batch = blockIdx.y;
+  const int64_t tile = blockIdx.x;
+  const int64_t m0 = (tile / a.tilesN) * BM, n0 = (tile % a.tilesN) * BN;
+  const int32_t* ra = a.crow + (int64_t)batch * 2 * a.kmax;
+  const int32_t* rb = ra + a.kmax;
+  const int kc = a.kcount[batch];
+
+  // loader coordinates: one W-vector of A and one of B per thread per step
+  const int lka = tid / (BM / W), lma = (tid % (BM / W)) * W;
+  const int lkb = tid / (BN / W), lnb = (tid % (BN / W)) * W;
+  const bool fullM = a.M >= BM, fullN = a.N >= BN;
+
+  auto load_a = [&](int k0, T (&reg)[W]) {
+    const int k = k0 + lka;
+#pragma unroll
+    for (int w = 0; w < W; ++w) reg[w] = T(0);
+    if (k < kc) {
+      const T* p = a.A + (int64_t)ra[k] * a.M + m0 + lma;
+      if (fullM) {
+        V v = *reinterpret_cast<const V*>(p);
+        const T* vp = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int w = 0; w < W; ++w) reg[w] = vp[w];
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+          if (m0 + lma + w < a.M) reg[w] = p[w];
+      }
+    }
+  };
+  auto load_b = [&](int k0, T (&reg)[W]) {
+    const int k = k0 + lkb;
+#pragma unroll
+    for (int w = 0; w < W; ++w) reg[w] = T(0);
+    if (k < kc) {
+      const T* p = a.B + (int64_t)rb[k] * a.N + n0 + lnb;
+      if (fullN) {
+        V v = *reinterpret_cast<const V*>(p);
+        const T* vp = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int w = 0; w < W; ++w) reg[w] = vp[w];
+      } else {
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+          if (n0 + lnb + w < a.N) reg[w] = p[w];
+      }
+    }
+  };
+
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  T ga[W], gb[W];
+  load_a(0, ga);
+  load_b(0, gb);
+  int buf = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    As[0][lka][lma + w] = ga[w];
+    Bs[0][lkb][lnb + w] = gb[w];
+  }
+  __syncthreads();
+  for (int k0 = 0; k0 < kc; k0 += BK) {
+    const bool more = k0 + BK < kc;
+    if (more) {
+      load_a(k0 + BK, ga);
+      load_b(k0 + BK, gb);
+    }
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T ra_[TM], rb_[TN];
+#pragma unroll
+      for (int i = 0; i < HM; ++i) {
+        ra_[i] = As[buf][kk][ty * HM + i];
+        ra_[HM + i] = As[buf][kk][BM / 2 + ty * HM + i];
+      }
+#pragma unroll
+      for (int j = 0; j < HN; ++j) {
+        rb_[j] = Bs[buf][kk][tx * HN + j];
+        rb_[HN + j] = Bs[buf][kk][BN / 2 + tx * HN + j];
+      }
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(ra_[i], rb_[j], acc[i][j]);
+    }
+    if (more) {
+#pragma unroll
+      for (int w = 0; w < W; ++w) {
+        As[buf ^ 1][lka][lma + w] = ga[w];
+        Bs[buf ^ 1][lkb][lnb + w] = gb[w];
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  }
+
+  // epilogue: scale, deposit into the output index, FP64 sum
+  double local = 0.0;
+  T* out = a.out + (uint64_t)batch * a.out_batch_stride;
+  uint64_t gB[TN];
+  bool okB[TN];
+#pragma unroll
+  for (int j = 0; j < TN; ++j) {
+    const int64_t n = n0 + (j < HN ? tx * HN + j : BN / 2 + tx * HN + (j - HN));
+    okB[j] = n < a.N;
+    gB[j] = okB[j] ? deposit(a.depB, a.nbB, (uint64_t)n) : 0;
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int64_t m = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
+    if (m >= a.M) continue;
+    const uint64_t gA = deposit(a.depA, a.nbA, (uint64_t)m);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (a.vecB >= HN && okB[h * HN + HN - 1] && (HN == 2 || HN == 4)) {
+        T v[HN];
+#pragma unroll
+        for (int j = 0; j < HN; ++j) {
+          v[j] = acc[i][h * HN + j] * a.scale;
+          local += (double)v[j];
+        }
+        if constexpr (sizeof(T) == 4 && HN == 4) {
+          *reinterpret_cast<float4*>(out + gA + gB[h * HN]) = make_float4(v[0], v[1], v[2], v[3]);
+        } else if constexpr (HN == 2) {
+          if constexpr (sizeof(T) == 8)
+            *reinterpret_cast<double2*>(out + gA + gB[h * HN]) = make_double2(v[0], v[1]);
+          else
+            *reinterpret_cast<float2*>(out + gA + gB[h * HN]) = make_float2(v[0], v[1]);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < HN; ++j) {
+          if (!okB[h * HN + j]) continue;
+          const T v = acc[i][h * HN + j] * a.scale;
+          out[gA + gB[h * HN + j]] = v;
+          local += (double)v;
+        }
+      }
+    }
+  }
+  if (a.sum) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((tid & 31) == 0) red[tid >> 5] = local;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0;
+      for (int w = 0; w < 8; ++w) s += red[w];
+      atomicAdd(a.sum, s);
+    }
+  }
+}
+
+template <typename T, int BM, int BN, int BK>
+void launch_typed(const Contraction& c, cudaStream_t s) {
+  CCArgs<T> a;
+  a.A = static_cast<const T*>(c.A);
+  a.B = static_cast<const T*>(c.B);
+  a.M = int64_t(1) << c.fA;
+  a.N = int64_t(1) << c.fB;
+  a.kmax = c.kmax;
+  a.crow = c.crow;
+  a.kcount = c.kcount;
+  a.depA = c.depA;
+  a.depB = c.depB;
+  a.nbA = (c.fA + 7) / 8;
+  a.nbB = (c.fB + 7) / 8;
+  a.out_batch_stride = c.out_batch_stride;
+  a.out = static_cast<T*>(c.out);
+  a.scale = T(c.scale);
+  a.sum = c.sum;
+  a.vecB = c.vecB;
+  const int64_t tilesM = (a.M + BM - 1) / BM;
+  a.tilesN = (a.N + BN - 1) / BN;
+  dim3 grid((unsigned)(tilesM * a.tilesN), (unsigned)c.batch);
+  k_cc_gemm<T, BM, BN, BK><<<grid, 256, 0, s>>>(a);
+  count_launch();
+  check_launch("k_cc_gemm");
+}
+
+}  // namespace
+
+void launch_row_nonzero(const void* T_, int dtype, int rows, int f, int32_t* flags, cudaStream_t s) {
+  const int64_t cols = int64_t(1) << f;
+  const int threads = cols >= 256 ? 256 : (cols >= 32 ? (int)cols : 32);
+  if (dtype == CUTQC_F64)
+    k_row_nonzero<double><<<rows, threads, 0, s>>>(static_cast<const double*>(T_), cols, flags);
+  else
+    k_row_nonzero<float><<<rows, threads, 0, s>>>(static_cast<const float*>(T_), cols, flags);
+  count_launch();
+  check_launch("k_row_nonzero");
+}
+
+void launch_compact(const Contraction& c, cudaStream_t s) {
+  int threads = 32;
+  while (threads < c.kmax && threads < 1024) threads *= 2;
+  k_compact<<<c.batch, threads, 0, s>>>(c.rows, c.kmax, c.nzA, c.nzB, c.crow, c.kcount);
+  count_launch();
+  check_launch("k_compact");
+}
+
+void launch_cc_gemm(const Contraction& c, cudaStream_t s) {
+  if (c.dtype == CUTQC_F64)
+    launch_typed<double, 64, 64, 8>(c, s);
+  else
+    launch_typed<float, 128, 128, 8>(c, s);
+}
+
+void launch_fill_zero(void* p, size_t bytes, cudaStream_t s) {
+  CUTQC_CUDA(cudaMemsetAsync(p, 0, bytes, s));
+}
+
+}  // namespace cutqc

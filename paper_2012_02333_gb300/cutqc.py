@@ -1,0 +1,208 @@
+"""Python binding of the C ABI in include/cutqc.h (ctypes, argument
+marshalling only: every step of the reconstruction runs in the library's CUDA
+kernels).  PyTorch provides device memory and streams.
+
+Loading fails loudly when libcutqc.so is missing: there is no CPU fallback.
+Build it with ``python -c "import __graft_entry__ as g; g.build()"``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import circuits
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcutqc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first (paper_2012_02333_gb300.build)")
+_lib = C.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- constants
+CUTQC_OK = 0
+CUTQC_ERR_ARG = -1
+CUTQC_ERR_SHAPE = -2
+CUTQC_ERR_OOM = -3
+CUTQC_ERR_CUDA = -4
+CUTQC_ERR_UNSUPPORTED = -5
+CUTQC_ERR_TIMEOUT = -6
+CUTQC_ERR_DEVICE = -7
+CUTQC_F64 = 0
+CUTQC_F32 = 1
+CUTQC_AUTO = 0
+CUTQC_CC = 1
+CUTQC_TC_BF16X3 = 2
+ALGOS = {"auto": CUTQC_AUTO, "cc": CUTQC_CC, "tc_bf16x3": CUTQC_TC_BF16X3}
+CUTQC_LOSS_NONE = 0
+CUTQC_LOSS_MAXCUT = 1
+
+GATE_OPS = {name: i for i, name in enumerate(
+    ["h", "x", "y", "z", "s", "sdg", "t", "sx", "sy", "sw", "rx", "ry", "rz", "cz", "cx", "cp"])}
+
+
+class cutqc_subcircuit(C.Structure):
+    _fields_ = [("k_in", C.c_int32), ("k_out", C.c_int32), ("n_eff", C.c_int32),
+                ("in_cut", C.POINTER(C.c_int32)), ("out_cut", C.POINTER(C.c_int32)),
+                ("out_qubit", C.POINTER(C.c_int32)), ("tensor", C.c_void_p)]
+
+
+class cutqc_problem(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_cuts", C.c_int32), ("n_sub", C.c_int32),
+                ("dtype", C.c_int32), ("sub", C.POINTER(cutqc_subcircuit))]
+
+
+class cutqc_loss(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_edges", C.c_int32), ("edges", C.POINTER(C.c_int32))]
+
+
+class cutqc_gate(C.Structure):
+    _fields_ = [("op", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32), ("param", C.c_double)]
+
+
+_lib.cutqc_reconstruct_fd.argtypes = [C.POINTER(cutqc_problem), C.c_int32, C.POINTER(C.c_void_p), C.c_int32,
+                                      C.c_void_p, C.c_void_p]
+_lib.cutqc_reconstruct_dd.argtypes = [C.POINTER(cutqc_problem), C.POINTER(C.c_int8), C.c_void_p, C.c_int32,
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_double), C.c_int32, C.c_void_p]
+_lib.cutqc_reconstruct_backward.argtypes = [C.POINTER(cutqc_problem), C.c_void_p, C.POINTER(cutqc_loss),
+                                            C.POINTER(C.c_void_p), C.c_void_p, C.c_void_p]
+_lib.cutqc_simulate_subcircuit.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                           C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
+                                           C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+_lib.cutqc_last_error.restype = C.c_char_p
+_lib.cutqc_launch_count.restype = C.c_int64
+for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
+           "cutqc_simulate_subcircuit"):
+    getattr(_lib, _f).restype = C.c_int
+
+
+class CutQCError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cutqc status {status}: {msg}")
+        self.status = status
+
+
+def _check(status: int) -> None:
+    if status != CUTQC_OK:
+        raise CutQCError(status, _lib.cutqc_last_error().decode())
+
+
+def last_error() -> str:
+    return _lib.cutqc_last_error().decode()
+
+
+def launch_count() -> int:
+    return int(_lib.cutqc_launch_count())
+
+
+def release() -> None:
+    _lib.cutqc_release()
+
+
+def _i32(xs: Sequence[int]):
+    arr = (C.c_int32 * max(len(xs), 1))(*[int(x) for x in xs])
+    return arr
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+# ------------------------------------------------------------------ problems
+
+class Problem:
+    """Marshals one cut circuit (structure from ``circuits.CutCircuit`` or
+    anything with the same fields) and its device tensors into a
+    ``cutqc_problem``.  Keeps every ctypes array alive while it lives."""
+
+    def __init__(self, n_qubits: int, n_cuts: int, subs, tensors: Sequence[torch.Tensor]):
+        if len(subs) != len(tensors):
+            raise ValueError("one tensor per subcircuit")
+        dts = {t.dtype for t in tensors}
+        if len(dts) != 1 or dts.pop() not in (torch.float32, torch.float64):
+            raise ValueError("tensors must all be float32 or all float64")
+        self.dtype = tensors[0].dtype
+        self.tensors = list(tensors)
+        self._keep = []
+        arr = (cutqc_subcircuit * len(subs))()
+        for i, (s, t) in enumerate(zip(subs, tensors)):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("tensors must be contiguous CUDA tensors")
+            want = (4 ** s.k_in) * (4 ** s.k_out) * (2 ** s.n_eff)
+            if t.numel() != want:
+                raise ValueError(f"tensor {i} has {t.numel()} entries, expected {want}")
+            ic, oc, oq = _i32(s.in_cut), _i32(s.out_cut), _i32(s.out_qubit)
+            self._keep += [ic, oc, oq]
+            arr[i] = cutqc_subcircuit(s.k_in, s.k_out, s.n_eff, ic, oc, oq, C.c_void_p(t.data_ptr()))
+        self._subs = arr
+        self.n_qubits, self.n_cuts = n_qubits, n_cuts
+        self.c = cutqc_problem(n_qubits, n_cuts, len(subs),
+                               CUTQC_F64 if self.dtype == torch.float64 else CUTQC_F32, arr)
+
+    @classmethod
+    def from_cut(cls, cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor]) -> "Problem":
+        return cls(cc.n, cc.n_cuts, cc.subs, tensors)
+
+
+# ------------------------------------------------------------------ entry points
+
+def cutqc_reconstruct_fd(problems: Sequence[Problem], outs: Sequence[torch.Tensor], algo: str = "auto",
+                         sum_p: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Binding of cutqc_reconstruct_fd (full definition, Sec. 4.2)."""
+    n = len(problems)
+    parr = (cutqc_problem * n)(*[p.c for p in problems])
+    optr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+    for p, o in zip(problems, outs):
+        if o.dtype != p.dtype or o.numel() != 2 ** p.n_qubits or not o.is_cuda:
+            raise ValueError("out must be a CUDA tensor of 2^n entries in the tensors' dtype")
+    sp = None
+    if sum_p is not None:
+        if sum_p.dtype != torch.float64 or sum_p.numel() < n or not sum_p.is_cuda:
+            raise ValueError("sum_p must be a CUDA float64 tensor of n_problems entries")
+        sp = sum_p.data_ptr()
+    _check(_lib.cutqc_reconstruct_fd(parr, n, optr, ALGOS[algo], sp, _stream_ptr(stream)))
+
+
+def reconstruct_fd(cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor], algo: str = "auto",
+                   out: Optional[torch.Tensor] = None, with_sum: bool = True, stream=None,
+                   device: Optional[torch.device] = None):
+    """Full-definition reconstruction of one cut circuit.  Tensors on the host
+    are copied to the device first (pinned, on `stream`).  Returns
+    (probabilities on the device, FP64 sum on the device or None)."""
+    dev = device or (tensors[0].device if tensors[0].is_cuda else torch.device("cuda", torch.cuda.current_device()))
+    s = stream or torch.cuda.current_stream(dev)
+    with torch.cuda.stream(s):
+        dts = [t if t.is_cuda else t.to(dev, non_blocking=True) for t in tensors]
+        if out is None:
+            out = torch.empty(2 ** cc.n, dtype=dts[0].dtype, device=dev)
+        sp = torch.empty(1, dtype=torch.float64, device=dev) if with_sum else None
+    p = Problem.from_cut(cc, dts)
+    cutqc_reconstruct_fd([p], [out], algo, sp, s)
+    return out, sp
+
+
+def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, device=None, stream=None) -> torch.Tensor:
+    """Binding of cutqc_simulate_subcircuit: the attributed tensor of one
+    subcircuit, simulated on the GPU (input preparation)."""
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    gates = (cutqc_gate * max(len(sub.gates), 1))()
+    for i, g in enumerate(sub.gates):
+        q1 = g.qubits[1] if len(g.qubits) > 1 else -1
+        gates[i] = cutqc_gate(GATE_OPS[g.name], g.qubits[0], q1, g.params[0] if g.params else 0.0)
+    out = torch.empty((4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff), dtype=dtype, device=dev)
+    s = stream or torch.cuda.current_stream(dev)
+    _check(_lib.cutqc_simulate_subcircuit(
+        gates, len(sub.gates), sub.d, _i32([q for q, _ in sub.in_slots]), sub.k_in,
+        _i32([q for q, _ in sub.out_slots]), sub.k_out, _i32([q for q, _ in sub.outputs]), sub.n_eff,
+        CUTQC_F64 if dtype == torch.float64 else CUTQC_F32, C.c_void_p(out.data_ptr()), s.cuda_stream))
+    return out
+
+
+def simulate_tensors(cc: circuits.CutCircuit, dtype=torch.float32, device=None) -> List[torch.Tensor]:
+    """GPU-simulated tensors of every subcircuit of a cut circuit."""
+    return [cutqc_simulate_subcircuit(s, dtype, device) for s in cc.subs]

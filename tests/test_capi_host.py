@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, it exports every function include/cutqc.h declares, and argument /
+shape errors come back as statuses before anything is launched."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2012_02333_gb300", "libcutqc.so")
+
+
+@pytest.fixture(scope="module")
+def capi():
+    if not os.path.exists(LIB):
+        from paper_2012_02333_gb300 import build
+        build.build()
+    from paper_2012_02333_gb300 import cutqc
+    return cutqc
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cutqc.h")).read()
+    return sorted(set(re.findall(r"CUTQC_API\s+[\w\s\*]+?\b(cutqc_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_entry_points():
+    fns = declared_functions()
+    for want in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
+                 "cutqc_last_error", "cutqc_release", "cutqc_simulate_subcircuit"):
+        assert want in fns
+
+
+def test_library_exports_every_declared_symbol(capi):
+    lib = C.CDLL(LIB)
+    for fn in declared_functions():
+        assert hasattr(lib, fn), fn
+
+
+def _problem(capi, subs_spec, n_qubits, n_cuts, dtype=1):
+    keep = []
+    arr = (capi.cutqc_subcircuit * len(subs_spec))()
+    for i, (kin, kout, neff, ic, oc, oq) in enumerate(subs_spec):
+        a, b, c = capi._i32(ic), capi._i32(oc), capi._i32(oq)
+        keep += [a, b, c]
+        # a non-null placeholder that is never dereferenced: every call below
+        # fails validation on the host before any device work
+        arr[i] = capi.cutqc_subcircuit(kin, kout, neff, a, b, c, C.c_void_p(0x1000))
+    p = capi.cutqc_problem(n_qubits, n_cuts, len(subs_spec), dtype, arr)
+    return p, keep, arr
+
+
+def _fd(capi, p):
+    out = (C.c_void_p * 1)(C.c_void_p(0x2000))
+    return capi._lib.cutqc_reconstruct_fd(C.byref(p), 1, out, 0, None, None)
+
+
+GOOD = [(0, 1, 5, [], [0], [0, 1, 2, 3, 4]), (1, 0, 5, [0], [], [5, 6, 7, 8, 9])]
+
+
+@pytest.mark.parametrize("mutate,status", [
+    (lambda s: s.__setitem__(1, (1, 0, 5, [1], [], [5, 6, 7, 8, 9])), "CUTQC_ERR_SHAPE"),    # cut id out of range
+    (lambda s: s.__setitem__(1, (1, 0, 5, [0], [], [4, 6, 7, 8, 9])), "CUTQC_ERR_SHAPE"),    # qubit twice
+    (lambda s: s.__setitem__(1, (1, 0, 4, [0], [], [5, 6, 7, 8])), "CUTQC_ERR_SHAPE"),       # qubit missing
+    (lambda s: s.__setitem__(0, (0, 0, 5, [], [], [0, 1, 2, 3, 4])), "CUTQC_ERR_SHAPE"),     # cut without upstream
+])
+def test_shape_errors(capi, mutate, status):
+    spec = list(GOOD)
+    mutate(spec)
+    p, keep, arr = _problem(capi, spec, 10, 1)
+    st = _fd(capi, p)
+    assert st == getattr(capi, status), capi.last_error()
+    assert capi.last_error()
+
+
+def test_limits_and_arguments(capi):
+    p, keep, arr = _problem(capi, GOOD, 10, 13)
+    assert _fd(capi, p) == capi.CUTQC_ERR_UNSUPPORTED          # K > 12
+    p, keep, arr = _problem(capi, GOOD, 10, 1, dtype=7)
+    assert _fd(capi, p) == capi.CUTQC_ERR_ARG                  # bad dtype
+    assert capi._lib.cutqc_reconstruct_fd(None, 1, None, 0, None, None) == capi.CUTQC_ERR_ARG
+    big = [(0, 1, 20, [], [0], list(range(20))), (1, 0, 20, [0], [], list(range(20, 40)))]
+    p, keep, arr = _problem(capi, big, 40, 1)
+    assert _fd(capi, p) == capi.CUTQC_ERR_UNSUPPORTED          # FD beyond 2^34
+    p, keep, arr = _problem(capi, GOOD, 10, 1)
+    out = (C.c_void_p * 1)(C.c_void_p(0x2000))
+    assert capi._lib.cutqc_reconstruct_fd(C.byref(p), 1, out, 9, None, None) == capi.CUTQC_ERR_ARG  # algo
+
+
+def test_simulator_argument_errors(capi):
+    g = (capi.cutqc_gate * 1)(capi.cutqc_gate(13, 0, 0, 0.0))   # CZ on one qubit twice
+    t = C.c_void_p(0x3000)
+    st = capi._lib.cutqc_simulate_subcircuit(g, 1, 2, None, 0, None, 0, capi._i32([0, 1]), 2, 1, t, None)
+    assert st == capi.CUTQC_ERR_SHAPE
+    st = capi._lib.cutqc_simulate_subcircuit(g, 1, 40, None, 0, None, 0, capi._i32([0]), 1, 1, t, None)
+    assert st == capi.CUTQC_ERR_UNSUPPORTED

@@ -1,0 +1,152 @@
+"""GPU parity of the full-definition reconstruction and of the GPU subcircuit
+simulator against the FP64 oracle, through the C ABI.
+
+Tolerances: the FP64 CUDA-core path must agree with the oracle to 1e-12 (only
+rounding order differs); every FP32 path must agree to 1e-6 max abs error
+(the target stated for this reconstruction) with the oracle run on the same
+FP32-rounded tensors promoted to FP64, which isolates reconstruction error."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(__file__))
+import cases  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-6
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if not os.path.exists(os.path.join(root, "paper_2012_02333_gb300", "libcutqc.so")):
+        from paper_2012_02333_gb300 import build
+        build.build()
+    from paper_2012_02333_gb300 import cutqc
+    return torch, cutqc
+
+
+_cache = {}
+
+
+def oracle_case(name, make):
+    if name not in _cache:
+        from oracle import attribution as at
+        cc = make()
+        _cache[name] = (cc, at.tensors(cc))
+    return _cache[name]
+
+
+def to_dev(torch, Ts, dtype):
+    return [torch.tensor(np.ascontiguousarray(T).reshape(-1), dtype=dtype, device="cuda") for T in Ts]
+
+
+@pytest.mark.parametrize("name", list(cases.SMALL))
+def test_fd_cc_fp64(env, name):
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    cc, Ts = oracle_case(name, cases.SMALL[name])
+    ref = rc.fd_full(cc.subs, Ts, cc.n, cc.n_cuts)
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, Ts, torch.float64), algo="cc")
+    got = out.cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL64
+    assert float(sp.item()) == pytest.approx(ref.sum(), abs=1e-12)
+
+
+@pytest.mark.parametrize("algo", ["cc", "auto"])
+@pytest.mark.parametrize("name", list(cases.SMALL))
+def test_fd_fp32(env, name, algo):
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    cc, Ts = oracle_case(name, cases.SMALL[name])
+    T32 = [T.astype(np.float32) for T in Ts]
+    ref = rc.fd_full(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts)
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
+    got = out.double().cpu().numpy()
+    err = np.abs(got - ref).max()
+    assert err <= TOL32, f"max abs err {err:.3e}"
+    assert float(sp.item()) == pytest.approx(ref.sum(), abs=TOL32)
+
+
+@pytest.mark.parametrize("name", ["hwea10_k1", "qaoa8_k4", "grid4x4_s4", "aqft8_k4", "bv6_k1"])
+def test_gpu_simulator_matches_oracle(env, name):
+    torch, cutqc = env
+    cc, Ts = oracle_case(name, cases.SMALL[name])
+    for sub, T in zip(cc.subs, Ts):
+        g = cutqc.cutqc_simulate_subcircuit(sub, torch.float64).cpu().numpy()
+        assert np.abs(g - T.reshape(-1)).max() < 1e-12
+        g32 = cutqc.cutqc_simulate_subcircuit(sub, torch.float32).cpu().numpy()
+        assert np.abs(g32 - T.reshape(-1).astype(np.float32)).max() <= 2 * np.finfo(np.float32).eps * max(1.0, np.abs(T).max())
+
+
+def test_repeated_calls_reuse_plan_and_agree(env):
+    torch, cutqc = env
+    cc, Ts = oracle_case("grid4x4_s4", cases.SMALL["grid4x4_s4"])
+    ts = to_dev(torch, [T.astype(np.float32) for T in Ts], torch.float32)
+    a, _ = cutqc.reconstruct_fd(cc, ts, algo="cc")
+    b, _ = cutqc.reconstruct_fd(cc, ts, algo="cc")
+    assert torch.equal(a, b)        # deterministic: stable compaction, fixed order
+
+
+def test_host_tensors_end_to_end(env):
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    cc, Ts = oracle_case("grid3x4_k3", cases.SMALL["grid3x4_k3"])
+    host = [torch.tensor(T.reshape(-1).astype(np.float32)).pin_memory() for T in Ts]
+    out, sp = cutqc.reconstruct_fd(cc, host)
+    ref = rc.fd_full(cc.subs, [T.astype(np.float32).astype(np.float64) for T in Ts], cc.n, cc.n_cuts)
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= TOL32
+
+
+@pytest.fixture(scope="module")
+def sup(env):
+    """The 24-qubit 4x6 supremacy workload at full size: oracle tensors (FP64
+    CPU simulation), rounded to FP32 for both sides."""
+    cc, Ts = oracle_case("sup4x6", cases.supremacy_4x6)
+    return cc, [T.astype(np.float32) for T in Ts]
+
+
+@pytest.mark.parametrize("algo", ["cc", "auto"])
+def test_supremacy_4x6_full_size_sampled(env, sup, algo):
+    """Full size (2^24 outputs, the launch configuration the benchmark times):
+    4096 sampled outputs, each recomputed by the oracle's plain sum, plus the
+    FP64 sum against the closed form over the FP32 tensors."""
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    cc, T32 = sup
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
+    got = out.double().cpu().numpy()
+    rng = np.random.default_rng(11)
+    xs = sorted(set(int(x) for x in rng.integers(0, 2 ** cc.n, 4096)) | {0, 2 ** cc.n - 1})
+    want = rc.fd_entries(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts, xs)
+    err = np.abs(got[xs] - want).max()
+    assert err <= TOL32, f"max abs err {err:.3e}"
+    # closed form: sum_x p(x) = 2^-K sum_e prod_c sum_x T_c[e|c][x]
+    sums = [T.astype(np.float64).reshape(T.shape[0] * T.shape[1], -1).sum(axis=1) for T in T32]
+    total = 0.0
+    for e in range(4 ** cc.n_cuts):
+        dg = [(e >> (2 * (cc.n_cuts - 1 - k))) & 3 for k in range(cc.n_cuts)]
+        prod = 1.0
+        for s, v in zip(cc.subs, sums):
+            prod *= v[rc.row_of(s, dg)]
+        total += prod
+    total *= 2.0 ** -cc.n_cuts
+    assert float(sp.item()) == pytest.approx(total, abs=TOL32)
+    assert got.sum() == pytest.approx(total, abs=TOL32)
+
+
+def test_supremacy_gpu_simulated_inputs(env, sup):
+    """The benchmark's own input preparation (GPU simulator) reproduces the
+    oracle's FP32 tensors of the full-size workload."""
+    torch, cutqc = env
+    cc, T32 = sup
+    for s, T in zip(cc.subs, T32):
+        g = cutqc.cutqc_simulate_subcircuit(s, torch.float32).cpu().numpy()
+        assert np.abs(g - T.reshape(-1)).max() <= 1e-6
