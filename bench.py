@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark: full-definition reconstruction of a 24-qubit supremacy circuit.
+
+Workload: a 4x6 supremacy-style grid circuit of depth 8 (seed 0), cut into
+its left and right halves for a 15-qubit device (two subcircuits of 15 and
+13 qubits, K = 4 wire cuts, 4^4 = 256 Kronecker terms, 2^12 outputs each):
+the paper's Figure 12 setting.  Subcircuit tensors are FP32, produced by the
+library's GPU subcircuit simulator before timing.  One step = one call of the
+C ABI's cutqc_reconstruct_fd over the whole path (early-termination row
+checks, compaction, operand preparation, the contraction into all 2^24
+probabilities, the FP64 sum).
+
+Metric: reconstructed probabilities per second (whole job, all ranks).  The
+L2 is flushed (256 MiB write) between timed steps; each step is timed with
+CUDA events on its stream; the max over ranks is reported.  With --gpus N
+under torchrun every rank reconstructs its own replica (weak scaling, no
+collective on the data path).
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the paper's Sec. 5.2 method: a subset of the Kronecker terms,
+scaled by the term count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reconstructed probs/sec & % roofline at ≤1e-6 max abs err vs FP64 oracle"
+UNIT = "probs/s"
+WORKLOAD = "supremacy_4x6_depth8_K4_fd_fp32"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+def workload():
+    from paper_2012_02333_gb300 import circuits
+    return circuits.supremacy_4x6(0)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed
+    region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def oracle_sample_rate(cc, n_terms: int, T64=None):
+    """Oracle FP64 plain sum over `n_terms` of the 4^K Kronecker terms for all
+    2^n outputs, scaled by the term count (the paper's Sec. 5.2 method).
+    Returns (probs/s, seconds of the sample, the sample description)."""
+    from oracle import attribution as at
+    from oracle import reconstruct as rc
+    if T64 is None:
+        T64 = [T.astype("float32").astype("float64") for T in at.tensors(cc)]
+    total = 4 ** cc.n_cuts
+    terms = list(range(0, total, max(1, total // n_terms)))[:n_terms]
+    t0 = time.perf_counter()
+    rc.fd_full(cc.subs, T64, cc.n, cc.n_cuts, terms=terms)
+    dt = time.perf_counter() - t0
+    scaled = dt * total / len(terms)
+    return 2 ** cc.n / scaled, dt, (f"{len(terms)} of {total} Kronecker terms over all 2^{cc.n} outputs, "
+                                    f"FP64 numpy oracle, time scaled by {total}/{len(terms)}"), T64
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cc = workload()
+    W, K = args.warmup, args.steps
+    T64 = None
+    times = []
+    desc = ""
+    for i in range(W + K):
+        rate, dt, desc, T64 = oracle_sample_rate(cc, 4, T64)
+        if i >= W:
+            times.append(2 ** cc.n / rate)
+    ms = 1e3 * statistics.mean(times)
+    value = 2 ** cc.n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": cc.n, "n_cuts": cc.n_cuts},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2012_02333_gb300 import cutqc
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cc = workload()
+    n_out = 2 ** cc.n
+    # input preparation (untimed): GPU-simulated FP32 subcircuit tensors
+    tensors = cutqc.simulate_tensors(cc, torch.float32, dev)
+    host = [t.cpu().pin_memory() for t in tensors]
+    # algorithmic work: Kronecker terms whose factor rows are all non-zero
+    rows_nz = []
+    for s, t in zip(cc.subs, host):
+        v = t.numpy().reshape(4 ** s.k_in * 4 ** s.k_out, -1)
+        rows_nz.append(np.any(v != 0, axis=1))
+    from itertools import product
+    k_eff = 0
+    for dg in product(range(4), repeat=cc.n_cuts):
+        ok = True
+        for s, nz in zip(cc.subs, rows_nz):
+            a = 0
+            for c in s.in_cut:
+                a = 4 * a + dg[c]
+            b = 0
+            for c in s.out_cut:
+                b = 4 * b + dg[c]
+            ok &= bool(nz[a * 4 ** s.k_out + b])
+        k_eff += ok
+    out = torch.empty(n_out, dtype=torch.float32, device=dev)
+    sum_p = torch.empty(1, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    stream = torch.cuda.current_stream(dev)
+    problem = cutqc.Problem.from_cut(cc, tensors)
+
+    def step():
+        cutqc.cutqc_reconstruct_fd([problem], [out], args.algo, sum_p, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    cutqc.profile_read()        # discard
+    cutqc.profile(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clk = Clocks(dev.index)
+    barrier(world)
+    torch.cuda.synchronize()
+    clk.start()
+    l0 = cutqc.launch_count()
+    for a, b in evs:
+        flush.zero_()
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    launches = cutqc.launch_count() - l0
+    barrier(world)
+    clocks = clk.stop()
+    cutqc.profile(False)
+    n_main, main_ms = cutqc.profile_read()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    ms = max_over_ranks(ms, world)
+    value = world * n_out / (ms / 1e3)
+    kern_ms = main_ms / max(n_main, 1)
+
+    # end to end through the public API: pinned host tensors in, probabilities out
+    out_host = torch.empty(n_out, dtype=torch.float32).pin_memory()
+    sum_host = torch.empty(1, dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        o, sp = cutqc.reconstruct_fd(cc, host, algo=args.algo, stream=stream, device=dev)
+        out_host.copy_(o, non_blocking=True)
+        sum_host.copy_(sp, non_blocking=True)
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(a.elapsed_time(b))
+    e2e = max_over_ranks(statistics.mean(e2e_ms), world)
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    d2h = n_out * 4 + 8
+
+    pk, pk_src = peaks()
+    used_tc = cutqc.last_algo() == cutqc.CUTQC_TC_BF16X3
+    flops1 = 2.0 * k_eff * n_out
+    if used_tc:
+        s = 3
+        achieved = s * flops1 / (kern_ms / 1e3) / 1e12
+        peak = pk["bf16_tflops"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": f"{pk_src} bf16 burst",
+                "flops_per_launch": s * flops1, "split_products": s,
+                "frac_single_product": flops1 / (kern_ms / 1e3) / 1e12 / peak}
+        dtype = "bf16x3-f32acc"
+    else:
+        achieved = flops1 / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_ALU_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_ALU_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "flops_per_launch": flops1}
+        dtype = "f32"
+    bytes_alg = n_out * 4 + sum(t.numel() * 4 for t in tensors)
+    roof["hbm"] = {"bytes_per_launch": bytes_alg, "achieved_gbs": bytes_alg / (kern_ms / 1e3) / 1e9,
+                   "peak_gbs": pk["hbm_gbs"], "frac": bytes_alg / (kern_ms / 1e3) / 1e9 / pk["hbm_gbs"]}
+    roof["kernel_ms"] = kern_ms
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_qubits": cc.n, "n_cuts": cc.n_cuts,
+                       "kronecker_terms": 4 ** cc.n_cuts, "nonzero_terms": k_eff,
+                       "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
+                       "algo": args.algo, "inputs": "FP32 tensors from the GPU subcircuit simulator, seed 0",
+                       "l2": "flushed by a 256 MiB write between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "e2e": {"value": world * n_out / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": e2e},
+            "gpu_launches": launches, "clocks": clocks}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, dt, desc, _ = oracle_sample_rate(cc, 96)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
+                                "sample_seconds": dt, "host_cpus": os.cpu_count()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

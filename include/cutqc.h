@@ -76,15 +76,24 @@ typedef enum { CUTQC_F64 = 0, CUTQC_F32 = 1 } cutqc_dtype;
 /* How the main contraction (the 4^K sum) is computed.
  *  CUTQC_CC        CUDA-core FMA in the tensors' dtype (FP64 or FP32): the
  *                  plain baseline.
- *  CUTQC_TC_BF16X3 tcgen05 tensor cores, each FP32 operand split into
- *                  bf16 hi + lo, products hi*hi + hi*lo + lo*hi accumulated
- *                  in FP32 in tensor memory (FP32 tensors only).
- *  CUTQC_AUTO      the planner picks (currently: CC for FP64, TC_BF16X3 for
- *                  FP32 when the contraction is large enough). */
+ *  CUTQC_TC_BF16X3 tcgen05 tensor cores, FP32 tensors only: each operand x
+ *                  split into h = bf16(x), m = bf16(x - h); the products
+ *                  h*h + h*m + m*h accumulate in FP32 in tensor memory.
+ *                  Error per product <= ~3 * 2^-18 |a||b|.
+ *  CUTQC_TC_BF16X6 as above with a third piece l = bf16(x - h - m) and the
+ *                  six products hh, hm, mh, hl, lh, mm: FP32-level accuracy
+ *                  at twice the tensor work.
+ *  CUTQC_AUTO      FP64 tensors: CUTQC_CC.  FP32 tensors: the tensor-core
+ *                  path when the shape allows it (else CUTQC_CC), with the
+ *                  number of products chosen on the device per call from
+ *                  the a-priori bound S = 2^-K sum_e max|A_e| max|B_e|:
+ *                  x3 when 3 * 2^-18 * S <= 2.5e-7, otherwise x6, so the
+ *                  split error stays within a quarter of 1e-6 absolute. */
 typedef enum {
   CUTQC_AUTO = 0,
   CUTQC_CC = 1,
-  CUTQC_TC_BF16X3 = 2
+  CUTQC_TC_BF16X3 = 2,
+  CUTQC_TC_BF16X6 = 3
 } cutqc_algo;
 
 /* One subcircuit (host struct; `tensor` is a device pointer). */
@@ -189,6 +198,22 @@ CUTQC_API void cutqc_release(void);
 
 /* Number of kernels this library has launched since load (all devices). */
 CUTQC_API int64_t cutqc_launch_count(void);
+
+/* The cutqc_algo that computed the final contraction of the most recent
+ * full-definition call on this thread: CUTQC_CC, or CUTQC_TC_BF16X3 for the
+ * tensor-core path under CUTQC_AUTO (whose x3 / x6 choice is made on the
+ * device), or the tensor-core form that was forced. */
+CUTQC_API int32_t cutqc_last_algo(void);
+
+/* Kernel timing for roofline measurement.  While enabled, every launch of
+ * the main contraction kernel of a full-definition call (the 4^K sum of the
+ * final step) is bracketed by CUDA events recorded on the stream it is
+ * launched on.  cutqc_profile_read() waits for the recorded events, returns
+ * the number of bracketed launches and their summed duration in
+ * milliseconds, and clears the record.  Not thread-safe against concurrent
+ * calls on other threads. */
+CUTQC_API int cutqc_profile(int32_t enable);
+CUTQC_API int cutqc_profile_read(int64_t* launches, double* total_ms);
 
 #ifdef __cplusplus
 }

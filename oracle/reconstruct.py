@@ -59,13 +59,15 @@ def _place(vecs, subs, positions, n_out):
     return prod.transpose(order).reshape(-1) if n_out else prod.reshape(-1)
 
 
-def fd_full(subs, tensors, n_qubits: int, n_cuts: int) -> np.ndarray:
-    """Every one of the 2^n probabilities by the plain sum (Sec. 3.2.3, 3.3)."""
+def fd_full(subs, tensors, n_qubits: int, n_cuts: int, terms=None) -> np.ndarray:
+    """Every one of the 2^n probabilities by the plain sum (Sec. 3.2.3, 3.3).
+    `terms` restricts the sum to a subset of the cut assignments e (used only
+    to time a sample of the terms, the runtime-scaling method of Sec. 5.2)."""
     K = n_cuts
     Ts = [_flat(T, s) for T, s in zip(tensors, subs)]
     positions = [list(s.out_qubit) for s in subs]
     out = np.zeros(2 ** n_qubits)
-    for e in range(4 ** K):
+    for e in (range(4 ** K) if terms is None else terms):
         dg = _digits(e, K)
         vecs = [T[row_of(s, dg)] for T, s in zip(Ts, subs)]
         out += _place(vecs, subs, positions, n_qubits)

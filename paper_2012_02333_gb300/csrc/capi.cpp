@@ -30,6 +30,7 @@ namespace cutqc {
 
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
+static thread_local int g_last_algo = CUTQC_CC;
 static std::atomic<int64_t> g_launches{0};
 static std::recursive_mutex g_mu;
 
@@ -139,6 +140,7 @@ struct Step {
   int vecB = 1;
   size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
   size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
+  size_t ws_bound = 0, ws_nseg = 0;
 };
 
 struct Plan {
@@ -147,6 +149,7 @@ struct Plan {
   std::vector<Step> steps;
   std::vector<size_t> ws_node;    // workspace offset of each merge-result tensor
   std::vector<size_t> ws_nz;      // workspace offset of each node's row flags
+  std::vector<size_t> ws_rmax;    // workspace offset of each node's row max |.|
   size_t ws_bytes = 0;
   void* dtab = nullptr;
   size_t dtab_bytes = 0;
@@ -163,6 +166,24 @@ struct DeviceState {
   std::vector<std::string> order;
 };
 static std::map<int, DeviceState> g_dev;
+
+// main-kernel timing (cutqc_profile)
+static bool g_profile = false;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
+
+static void prof_begin(cudaStream_t s, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!g_profile) return;
+  CUTQC_CUDA(cudaEventCreate(a));
+  CUTQC_CUDA(cudaEventRecord(*a, s));
+}
+static void prof_end(cudaStream_t s, cudaEvent_t a) {
+  if (!a) return;
+  cudaEvent_t b;
+  CUTQC_CUDA(cudaEventCreate(&b));
+  CUTQC_CUDA(cudaEventRecord(b, s));
+  g_prof_events.emplace_back(a, b);
+}
 
 static DeviceState& device_state() {
   int dev = 0;
@@ -354,8 +375,11 @@ static void finalize_plan(Plan& P) {
       w = align_up(w + (size_t)P.nodes[i].rows() * ((size_t)1 << P.nodes[i].f()) * es);
     }
   }
+  P.ws_rmax.assign(P.nodes.size(), 0);
   for (size_t i = 0; i < P.nodes.size(); ++i) {
     P.ws_nz[i] = w;
+    w = align_up(w + (size_t)P.nodes[i].rows() * 4);
+    P.ws_rmax[i] = w;
     w = align_up(w + (size_t)P.nodes[i].rows() * 4);
   }
   for (Step& st : P.steps) {
@@ -363,6 +387,10 @@ static void finalize_plan(Plan& P) {
     w = align_up(w + st.rows.size() * 4);
     st.ws_kcount = w;
     w = align_up(w + (size_t)st.batch * 4);
+    st.ws_bound = w;
+    w = align_up(w + 8);
+    st.ws_nseg = w;
+    w = align_up(w + 4);
   }
   P.ws_bytes = w;
 }
@@ -433,11 +461,10 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
   }
   const void* one = P.dtype == CUTQC_F64 ? ds.one : static_cast<char*>(ds.one) + 8;
   // decide the algorithm of the final step
-  const Step& last = P.steps.back();
   int final_algo = algo;
   if (final_algo == CUTQC_AUTO) final_algo = (P.dtype == CUTQC_F32) ? CUTQC_TC_BF16X3 : CUTQC_CC;
-  if (final_algo == CUTQC_TC_BF16X3 && P.dtype != CUTQC_F32)
-    fail(CUTQC_ERR_ARG, "CUTQC_TC_BF16X3 needs FP32 tensors");
+  const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6;
+  if (tc_algo && P.dtype != CUTQC_F32) fail(CUTQC_ERR_ARG, "the tensor-core forms need FP32 tensors");
   for (size_t i = 0; i < P.steps.size(); ++i) {
     Contraction& c = cs[i];
     const Step& st = P.steps[i];
@@ -453,7 +480,7 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     c.rowsB = (int)P.nodes[st.b].rows();
   }
   size_t need = P.ws_bytes;
-  const bool use_tc_final = (final_algo == CUTQC_TC_BF16X3) && tc_supported(cs.back());
+  const bool use_tc_final = tc_algo && tc_supported(cs.back());
   if (use_tc_final) {
     tc_ws = tc_workspace_bytes(cs.back());
     need = align_up(need) + tc_ws;
@@ -471,7 +498,8 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
   auto ensure_flags = [&](int i) {
     if (flagged[i]) return;
     const Node& nd = P.nodes[i];
-    launch_row_nonzero(node_ptr(i), P.dtype, (int)nd.rows(), nd.f(), reinterpret_cast<int32_t*>(base + P.ws_nz[i]), s);
+    launch_row_stats(node_ptr(i), P.dtype, (int)nd.rows(), nd.f(), reinterpret_cast<int32_t*>(base + P.ws_nz[i]),
+                     reinterpret_cast<float*>(base + P.ws_rmax[i]), s);
     flagged[i] = 1;
   };
   if (sum) CUTQC_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
@@ -490,13 +518,24 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
     c.nzB = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.b]);
     const bool final_step = (i + 1 == P.steps.size());
+    if (final_step && use_tc_final) {
+      c.rmaxA = reinterpret_cast<const float*>(base + P.ws_rmax[st.a]);
+      c.rmaxB = reinterpret_cast<const float*>(base + P.ws_rmax[st.b]);
+      c.bound = reinterpret_cast<double*>(base + st.ws_bound);
+      c.nseg = reinterpret_cast<int32_t*>(base + st.ws_nseg);
+      c.nseg_fixed = algo == CUTQC_TC_BF16X3 ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+    }
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
     c.sum = final_step ? sum : nullptr;
     launch_compact(c, s);
+    cudaEvent_t ev = nullptr;
+    if (final_step) prof_begin(s, &ev);
     if (final_step && use_tc_final)
       launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s);
     else
       launch_cc_gemm(c, s);
+    if (final_step) g_last_algo = use_tc_final ? (algo == CUTQC_AUTO ? CUTQC_TC_BF16X3 : algo) : CUTQC_CC;
+    if (final_step) prof_end(s, ev);
   }
 }
 
@@ -511,7 +550,7 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
   return guarded([&] {
     if (!problems || n_problems < 1) fail(CUTQC_ERR_ARG, "need n_problems >= 1 problems");
     if (!out) fail(CUTQC_ERR_ARG, "out is NULL");
-    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X3) fail(CUTQC_ERR_ARG, "unknown algo");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X6) fail(CUTQC_ERR_ARG, "unknown algo");
     for (int i = 0; i < n_problems; ++i) {
       validate(&problems[i], true);
       if (problems[i].n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
@@ -600,5 +639,29 @@ void cutqc_release(void) {
 }
 
 int64_t cutqc_launch_count(void) { return g_launches.load(); }
+
+int32_t cutqc_last_algo(void) { return g_last_algo; }
+
+int cutqc_profile(int32_t enable) {
+  return guarded([&] { g_profile = enable != 0; });
+}
+
+int cutqc_profile_read(int64_t* launches, double* total_ms) {
+  return guarded([&] {
+    if (!launches || !total_ms) fail(CUTQC_ERR_ARG, "NULL output");
+    double ms = 0.0;
+    for (auto& ab : g_prof_events) {
+      CUTQC_CUDA(cudaEventSynchronize(ab.second));
+      float t = 0.f;
+      CUTQC_CUDA(cudaEventElapsedTime(&t, ab.first, ab.second));
+      ms += t;
+      cudaEventDestroy(ab.first);
+      cudaEventDestroy(ab.second);
+    }
+    *launches = (int64_t)g_prof_events.size();
+    *total_ms = ms;
+    g_prof_events.clear();
+  });
+}
 
 }  // extern "C"

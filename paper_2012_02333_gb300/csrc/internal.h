@@ -52,11 +52,21 @@ struct Contraction {
   int dtype = CUTQC_F32;
   const int32_t* nzA = nullptr;    // device row non-zero flags of A (or null)
   const int32_t* nzB = nullptr;
+  const float* rmaxA = nullptr;    // device row max |.| of A (or null)
+  const float* rmaxB = nullptr;
   int rowsA = 0, rowsB = 0;
+  // split-precision control (tensor-core path): the compaction also computes
+  // the a-priori magnitude S = scale * sum_kept max|A_row| max|B_row| into
+  // *bound, and writes the number of split products to *nseg: `nseg_fixed`
+  // if non-zero, else 3 when split_err3 * S <= split_tol, otherwise 6.
+  double* bound = nullptr;
+  int32_t* nseg = nullptr;
+  int nseg_fixed = 0;
+  double split_tol = 2.5e-7;
 };
 
 // k_cc.cu
-void launch_row_nonzero(const void* T, int dtype, int rows, int f, int32_t* flags, cudaStream_t s);
+void launch_row_stats(const void* T, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s);
 void launch_compact(const Contraction& c, cudaStream_t s);
 void launch_cc_gemm(const Contraction& c, cudaStream_t s);
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);

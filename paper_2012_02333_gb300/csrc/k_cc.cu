@@ -27,22 +27,40 @@ __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, in
   return g;
 }
 
-// ---- row non-zero flags (one block per row) -------------------------------
+// ---- row statistics (one block per row): non-zero flag and max |entry| ----
 template <typename T>
-__global__ void k_row_nonzero(const T* __restrict__ t, int64_t cols, int32_t* __restrict__ flags) {
+__global__ void k_row_stats(const T* __restrict__ t, int64_t cols, int32_t* __restrict__ flags,
+                            float* __restrict__ rmax) {
+  __shared__ float red[32];
   const T* row = t + (int64_t)blockIdx.x * cols;
+  float m = 0.0f;
   int nz = 0;
-  for (int64_t i = threadIdx.x; i < cols && !nz; i += blockDim.x) nz = (row[i] != T(0));
+  for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) {
+    const T v = row[i];
+    nz |= (v != T(0));
+    m = fmaxf(m, (float)fabs((double)v));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
   nz = __syncthreads_or(nz);
-  if (threadIdx.x == 0) flags[blockIdx.x] = nz;
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    flags[blockIdx.x] = nz;
+    rmax[blockIdx.x] = m;
+  }
 }
 
 // ---- stable compaction of the inner index (one block per batch) ----------
 __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int32_t* __restrict__ nzA,
                           const int32_t* __restrict__ nzB, int32_t* __restrict__ crow,
-                          int32_t* __restrict__ kcount) {
+                          int32_t* __restrict__ kcount, const float* __restrict__ rmaxA,
+                          const float* __restrict__ rmaxB, double scale, double* __restrict__ bound,
+                          int32_t* __restrict__ nseg, int nseg_fixed, double split_tol) {
   __shared__ int warp_tot[32];
+  __shared__ double warp_s[32];
   __shared__ int base;
+  double s_acc = 0.0;
   const int b = blockIdx.x;
   const int32_t* ra = rows + (int64_t)b * 2 * kmax;
   const int32_t* rb = ra + kmax;
@@ -71,12 +89,30 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
     if (keep) {
       ca[base + off + before] = a;
       cb[base + off + before] = bb;
+      if (bound) s_acc += (double)rmaxA[a] * (double)rmaxB[bb];
     }
     __syncthreads();
     if (threadIdx.x == 0) base += tot;
     __syncthreads();
   }
-  if (threadIdx.x == 0) kcount[b] = base;
+  if (bound) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s_acc += __shfl_xor_sync(0xffffffffu, s_acc, o);
+    if (lane == 0) warp_s[warp] = s_acc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    kcount[b] = base;
+    if (bound) {
+      double S = 0.0;
+      for (int w = 0; w < nw; ++w) S += warp_s[w];
+      S *= scale;
+      bound[b] = S;
+      // BF16 x3 drops terms of at most ~3 * 2^-18 relative to |a||b| per product
+      const double err3 = 3.0 * 3.814697265625e-06 * S;
+      *nseg = nseg_fixed ? nseg_fixed : (err3 <= split_tol ? 3 : 6);
+    }
+  }
 }
 
 // ---- the CUDA-core contraction ---------------------------------------------
@@ -299,21 +335,23 @@ void launch_typed(const Contraction& c, cudaStream_t s) {
 
 }  // namespace
 
-void launch_row_nonzero(const void* T_, int dtype, int rows, int f, int32_t* flags, cudaStream_t s) {
+void launch_row_stats(const void* T_, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s) {
   const int64_t cols = int64_t(1) << f;
-  const int threads = cols >= 256 ? 256 : (cols >= 32 ? (int)cols : 32);
+  const int threads = cols >= 256 ? 256 : 32;
   if (dtype == CUTQC_F64)
-    k_row_nonzero<double><<<rows, threads, 0, s>>>(static_cast<const double*>(T_), cols, flags);
+    k_row_stats<double><<<rows, threads, 0, s>>>(static_cast<const double*>(T_), cols, flags, rmax);
   else
-    k_row_nonzero<float><<<rows, threads, 0, s>>>(static_cast<const float*>(T_), cols, flags);
+    k_row_stats<float><<<rows, threads, 0, s>>>(static_cast<const float*>(T_), cols, flags, rmax);
   count_launch();
-  check_launch("k_row_nonzero");
+  check_launch("k_row_stats");
 }
 
 void launch_compact(const Contraction& c, cudaStream_t s) {
   int threads = 32;
   while (threads < c.kmax && threads < 1024) threads *= 2;
-  k_compact<<<c.batch, threads, 0, s>>>(c.rows, c.kmax, c.nzA, c.nzB, c.crow, c.kcount);
+  if (c.bound && c.batch != 1) fail(CUTQC_ERR_UNSUPPORTED, "split-precision bound needs batch 1");
+  k_compact<<<c.batch, threads, 0, s>>>(c.rows, c.kmax, c.nzA, c.nzB, c.crow, c.kcount, c.rmaxA, c.rmaxB,
+                                        c.scale, c.bound, c.nseg, c.nseg_fixed, c.split_tol);
   count_launch();
   check_launch("k_compact");
 }

@@ -36,7 +36,8 @@ CUTQC_F32 = 1
 CUTQC_AUTO = 0
 CUTQC_CC = 1
 CUTQC_TC_BF16X3 = 2
-ALGOS = {"auto": CUTQC_AUTO, "cc": CUTQC_CC, "tc_bf16x3": CUTQC_TC_BF16X3}
+CUTQC_TC_BF16X6 = 3
+ALGOS = {"auto": CUTQC_AUTO, "cc": CUTQC_CC, "tc_bf16x3": CUTQC_TC_BF16X3, "tc_bf16x6": CUTQC_TC_BF16X6}
 CUTQC_LOSS_NONE = 0
 CUTQC_LOSS_MAXCUT = 1
 
@@ -72,10 +73,13 @@ _lib.cutqc_reconstruct_backward.argtypes = [C.POINTER(cutqc_problem), C.c_void_p
 _lib.cutqc_simulate_subcircuit.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+_lib.cutqc_profile.argtypes = [C.c_int32]
+_lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
+_lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
-           "cutqc_simulate_subcircuit"):
+           "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -98,8 +102,26 @@ def launch_count() -> int:
     return int(_lib.cutqc_launch_count())
 
 
+def last_algo() -> int:
+    """cutqc_algo of the last full-definition call's final contraction."""
+    return int(_lib.cutqc_last_algo())
+
+
 def release() -> None:
     _lib.cutqc_release()
+
+
+def profile(enable: bool) -> None:
+    """Bracket every main-contraction launch with CUDA events (cutqc_profile)."""
+    _check(_lib.cutqc_profile(1 if enable else 0))
+
+
+def profile_read():
+    """(launches, total milliseconds) of the bracketed main-kernel launches."""
+    n = C.c_int64()
+    ms = C.c_double()
+    _check(_lib.cutqc_profile_read(C.byref(n), C.byref(ms)))
+    return int(n.value), float(ms.value)
 
 
 def _i32(xs: Sequence[int]):
