@@ -205,6 +205,13 @@ CUTQC_API int64_t cutqc_launch_count(void);
  * device), or the tensor-core form that was forced. */
 CUTQC_API int32_t cutqc_last_algo(void);
 
+/* Diagnostics of the most recent tensor-core final contraction on this
+ * thread: the number of split products the device chose (3 or 6) and the
+ * a-priori magnitude S = 2^-K sum_e max|A_e| max|B_e| it was chosen from.
+ * Synchronises the stream of that call.  Returns CUTQC_ERR_ARG if no
+ * tensor-core contraction has run on this thread. */
+CUTQC_API int cutqc_last_split(int32_t* nseg, double* bound);
+
 /* Kernel timing for roofline measurement.  While enabled, every launch of
  * the main contraction kernel of a full-definition call (the 4^K sum of the
  * final step) is bracketed by CUDA events recorded on the stream it is

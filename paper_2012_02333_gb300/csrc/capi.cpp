@@ -31,6 +31,9 @@ namespace cutqc {
 // ------------------------------------------------------------------ errors
 static thread_local std::string g_last_error;
 static thread_local int g_last_algo = CUTQC_CC;
+static thread_local const int32_t* g_last_nseg = nullptr;     // device
+static thread_local const double* g_last_bound = nullptr;     // device
+static thread_local cudaStream_t g_last_stream = nullptr;
 static std::atomic<int64_t> g_launches{0};
 static std::recursive_mutex g_mu;
 
@@ -138,7 +141,8 @@ struct Step {
   std::vector<uint64_t> depA, depB;   // [ceil(f/8)][256]
   uint64_t out_stride = 0;
   int vecB = 1;
-  size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
+  std::vector<uint8_t> epi;           // tensor-core epilogue table (final step)
+  size_t off_rows = 0, off_depA = 0, off_depB = 0, off_epi = 0;   // in the plan's device block
   size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
   size_t ws_bound = 0, ws_nseg = 0;
 };
@@ -273,6 +277,7 @@ static Step make_step(Plan& P, int ia, int ib, int result, const std::vector<int
     int run = 0;
     while (run < fB && run < 2 && vb[run] == (uint64_t(1) << run)) ++run;
     st.vecB = 1 << run;
+    st.epi = tc_epilogue_table(va, vb);
   }
   st.depA = deposit_table(va);
   st.depB = deposit_table(vb);
@@ -354,6 +359,8 @@ static void finalize_plan(Plan& P) {
     off = align_up(off + st.depA.size() * 8);
     st.off_depB = off;
     off = align_up(off + st.depB.size() * 8);
+    st.off_epi = off;
+    off = align_up(off + st.epi.size());
   }
   P.dtab_bytes = std::max<size_t>(off, 256);
   CUTQC_CUDA(cudaMalloc(&P.dtab, P.dtab_bytes));
@@ -362,6 +369,7 @@ static void finalize_plan(Plan& P) {
     std::memcpy(host.data() + st.off_rows, st.rows.data(), st.rows.size() * 4);
     std::memcpy(host.data() + st.off_depA, st.depA.data(), st.depA.size() * 8);
     std::memcpy(host.data() + st.off_depB, st.depB.data(), st.depB.size() * 8);
+    if (!st.epi.empty()) std::memcpy(host.data() + st.off_epi, st.epi.data(), st.epi.size());
   }
   CUTQC_CUDA(cudaMemcpy(P.dtab, host.data(), P.dtab_bytes, cudaMemcpyHostToDevice));
   // workspace layout: merge results, row flags, compacted rows, counts
@@ -478,6 +486,7 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     c.scale = (i + 1 == P.steps.size()) ? std::ldexp(1.0, -P.K) : 1.0;
     c.rowsA = (int)P.nodes[st.a].rows();
     c.rowsB = (int)P.nodes[st.b].rows();
+    c.epi_tab = st.epi.empty() ? nullptr : static_cast<const void*>(static_cast<char*>(P.dtab) + st.off_epi);
   }
   size_t need = P.ws_bytes;
   const bool use_tc_final = tc_algo && tc_supported(cs.back());
@@ -513,6 +522,7 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     c.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
     c.depA = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
     c.depB = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
+    c.epi_tab = st.epi.empty() ? nullptr : static_cast<const void*>(dtab + st.off_epi);
     c.crow = reinterpret_cast<int32_t*>(base + st.ws_crow);
     c.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
     c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
@@ -524,6 +534,9 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
       c.bound = reinterpret_cast<double*>(base + st.ws_bound);
       c.nseg = reinterpret_cast<int32_t*>(base + st.ws_nseg);
       c.nseg_fixed = algo == CUTQC_TC_BF16X3 ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+      g_last_nseg = c.nseg;
+      g_last_bound = c.bound;
+      g_last_stream = s;
     }
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
     c.sum = final_step ? sum : nullptr;
@@ -641,6 +654,16 @@ void cutqc_release(void) {
 int64_t cutqc_launch_count(void) { return g_launches.load(); }
 
 int32_t cutqc_last_algo(void) { return g_last_algo; }
+
+int cutqc_last_split(int32_t* nseg, double* bound) {
+  return guarded([&] {
+    if (!nseg || !bound) fail(CUTQC_ERR_ARG, "NULL output");
+    if (!g_last_nseg || g_last_algo == CUTQC_CC) fail(CUTQC_ERR_ARG, "no tensor-core contraction has run");
+    CUTQC_CUDA(cudaStreamSynchronize(g_last_stream));
+    CUTQC_CUDA(cudaMemcpy(nseg, g_last_nseg, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    CUTQC_CUDA(cudaMemcpy(bound, g_last_bound, sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
 
 int cutqc_profile(int32_t enable) {
   return guarded([&] { g_profile = enable != 0; });

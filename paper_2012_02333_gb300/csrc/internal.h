@@ -61,6 +61,7 @@ struct Contraction {
   // if non-zero, else 3 when split_err3 * S <= split_tol, otherwise 6.
   double* bound = nullptr;
   int32_t* nseg = nullptr;
+  const void* epi_tab = nullptr;   // device tensor-core epilogue table (final step)
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
 };
@@ -75,6 +76,10 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 bool tc_supported(const Contraction& c);
 void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t tc_workspace_bytes(const Contraction& c);
+// Epilogue table of the tensor-core path for a final step whose index bits
+// map to output bit values va (M side) and vb (N side), least significant
+// index bit first.  Empty when the shape cannot use it.
+std::vector<uint8_t> tc_epilogue_table(const std::vector<uint64_t>& va, const std::vector<uint64_t>& vb);
 
 // k_sim.cu
 struct SimPlan {

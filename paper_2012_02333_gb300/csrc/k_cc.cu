@@ -249,7 +249,8 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
     buf ^= 1;
   }
 
-  // epilogue: scale, deposit into the output index, FP64 sum
+  // epilogue: scale, deposit into the output index; the sum accumulates each
+  // row's TN values pairwise in T, then in FP64 (the FP64 pipe is narrow)
   double local = 0.0;
   T* out = a.out + (uint64_t)batch * a.out_batch_stride;
   uint64_t gB[TN];
@@ -265,15 +266,20 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
     const int64_t m = m0 + (i < HM ? ty * HM + i : BM / 2 + ty * HM + (i - HM));
     if (m >= a.M) continue;
     const uint64_t gA = deposit(a.depA, a.nbA, (uint64_t)m);
+    T rowv[TN];
+#pragma unroll
+    for (int j = 0; j < TN; ++j) rowv[j] = okB[j] ? acc[i][j] * a.scale : T(0);
+#pragma unroll
+    for (int w = TN / 2; w > 0; w >>= 1)
+#pragma unroll
+      for (int j = 0; j < w; ++j) rowv[j] += rowv[j + w];
+    local += (double)rowv[0];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (a.vecB >= HN && okB[h * HN + HN - 1] && (HN == 2 || HN == 4)) {
         T v[HN];
 #pragma unroll
-        for (int j = 0; j < HN; ++j) {
-          v[j] = acc[i][h * HN + j] * a.scale;
-          local += (double)v[j];
-        }
+        for (int j = 0; j < HN; ++j) v[j] = acc[i][h * HN + j] * a.scale;
         if constexpr (sizeof(T) == 4 && HN == 4) {
           *reinterpret_cast<float4*>(out + gA + gB[h * HN]) = make_float4(v[0], v[1], v[2], v[3]);
         } else if constexpr (HN == 2) {
@@ -286,9 +292,7 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
 #pragma unroll
         for (int j = 0; j < HN; ++j) {
           if (!okB[h * HN + j]) continue;
-          const T v = acc[i][h * HN + j] * a.scale;
-          out[gA + gB[h * HN + j]] = v;
-          local += (double)v;
+          out[gA + gB[h * HN + j]] = acc[i][h * HN + j] * a.scale;
         }
       }
     }

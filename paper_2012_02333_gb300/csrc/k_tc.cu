@@ -31,7 +31,10 @@
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
+#include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 
@@ -46,7 +49,24 @@ constexpr int B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;
 constexpr int THREADS = 192;
-constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+constexpr int EPI_PITCH = 33;                 // padded row pitch of the epilogue staging buffer
+constexpr int EPI_WARP_BYTES = 32 * EPI_PITCH * 4;
+constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 4 * EPI_WARP_BYTES + 1024 + 256;
+
+// Epilogue staging.  An epilogue warp holds a 32 x 32 chunk (lane = low 5 bits
+// of m, register = low 5 bits of n).  Those 10 index bits land on 10 output
+// bit positions; ordering them by position gives each chunk element a "slot"
+// whose order is the output address order.  The warp writes the chunk to
+// shared memory row by row ([lane][col], pitch 33: conflict-free), then reads
+// it back slot by slot and stores to global memory in address order: runs of
+// 2^contig consecutive floats become coalesced 16-byte stores.  All maps are
+// additive over disjoint bits, so each is a sum of a low and a high table.
+struct EpiTab {
+  int32_t slo[32], shi[32];      // staging offset (floats) of slot bits 0-4 / 5-9
+  uint64_t glo[32], ghi[32];     // output offset of slot bits 0-4 / 5-9
+  int32_t contig;                // slots 0..2^contig-1 are consecutive in memory
+  int32_t pad[3];
+};
 constexpr uint64_t WAIT_NS = 2000000000ull;
 
 // ------------------------------------------------------------ operand prep
@@ -205,6 +225,7 @@ struct TcArgs {
   float scale;
   double* sum;
   int vecB;
+  const void* epi;
   int* status;
 };
 
@@ -214,7 +235,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);   // 256 bytes of barriers
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + 2;
@@ -309,14 +330,34 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp >= 2) {
     // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. +31
     const int q = warp & 3;
+    float* stage_buf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * (32 * EPI_PITCH);
+    const EpiTab* et = static_cast<const EpiTab*>(a.epi);
     double local = 0.0;
+    // per-thread constants of the read-back: slots 4*lane + t (t < 4) of each
+    // 128-slot pass it (< 8): staging offset slo[(4l+t)&31] + shi[4it + l/8]
+    int32_t rs_lo[4];
+    uint64_t rg_lo[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      rs_lo[t] = et->slo[(4 * lane + t) & 31];
+      rg_lo[t] = et->glo[(4 * lane + t) & 31];
+    }
+    int32_t rs_hi[8];
+    uint64_t rg_hi[8], dcol[8];
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      rs_hi[it] = et->shi[4 * it + (lane >> 3)];
+      rg_hi[it] = et->ghi[4 * it + (lane >> 3)];
+      dcol[it] = deposit(a.depB, 1, (uint64_t)(32 * it));   // chunk column base, n bits 5-7
+    }
+    const bool vec = et->contig >= 2;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int tm = tile % a.tilesM, tn = tile / a.tilesM;
-      const uint64_t m = (uint64_t)tm * BM + 32 * q + lane;
-      const uint64_t gA = deposit(a.depA, a.nbA, m);
-      const uint64_t n0 = (uint64_t)tn * BN;
+      // chunk base: rows tm*128 + 32q (m bits >= 5), columns tn*256 (n bits >= 8)
+      const uint64_t gT = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) +
+                          deposit(a.depB, a.nbB, (uint64_t)tn * BN);
       if (nkb > 0) {
         const bool ok = mbar_wait(&tfull[acc], acc_phase, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -331,19 +372,38 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int j = 0; j < 32; ++j) r[j] = 0u;
         }
+        // sum of this 32-column row piece: pairwise in FP32 (error <= 5 * 2^-24 *
+        // sum |v|), then one FP64 add (the FP64 pipe is narrow on this part)
+        float t16[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const uint64_t n = n0 + 32 * c + 4 * j;
-          const float v0 = __uint_as_float(r[4 * j]) * a.scale, v1 = __uint_as_float(r[4 * j + 1]) * a.scale;
-          const float v2 = __uint_as_float(r[4 * j + 2]) * a.scale, v3 = __uint_as_float(r[4 * j + 3]) * a.scale;
-          local += ((double)v0 + (double)v1) + ((double)v2 + (double)v3);
-          if (a.vecB >= 4) {
-            __stcs(reinterpret_cast<float4*>(a.out + gA + deposit(a.depB, a.nbB, n)), make_float4(v0, v1, v2, v3));
+        for (int j = 0; j < 16; ++j)
+          t16[j] = __uint_as_float(r[2 * j]) * a.scale + __uint_as_float(r[2 * j + 1]) * a.scale;
+#pragma unroll
+        for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+          for (int j = 0; j < w; ++j) t16[j] += t16[j + w];
+        local += (double)t16[0];
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) stage_buf[lane * EPI_PITCH + j] = __uint_as_float(r[j]) * a.scale;
+        __syncwarp();
+        uint64_t dc = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
+        float* obase = a.out + gT + dc;
+#pragma unroll
+        for (int it = 0; it < 8; ++it) {
+          const int32_t sh = rs_hi[it];
+          const uint64_t gh = rg_hi[it];
+          const float v0 = stage_buf[rs_lo[0] + sh], v1 = stage_buf[rs_lo[1] + sh];
+          const float v2 = stage_buf[rs_lo[2] + sh], v3 = stage_buf[rs_lo[3] + sh];
+          if (vec) {
+            __stcs(reinterpret_cast<float4*>(obase + gh + rg_lo[0]), make_float4(v0, v1, v2, v3));
           } else {
-            a.out[gA + deposit(a.depB, a.nbB, n)] = v0;
-            a.out[gA + deposit(a.depB, a.nbB, n + 1)] = v1;
-            a.out[gA + deposit(a.depB, a.nbB, n + 2)] = v2;
-            a.out[gA + deposit(a.depB, a.nbB, n + 3)] = v3;
+            obase[gh + rg_lo[0]] = v0;
+            obase[gh + rg_lo[1]] = v1;
+            obase[gh + rg_lo[2]] = v2;
+            obase[gh + rg_lo[3]] = v3;
           }
         }
       }
@@ -417,7 +477,38 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 bool tc_supported(const Contraction& c) {
-  return c.dtype == CUTQC_F32 && c.batch == 1 && c.fA >= 7 && c.fB >= 8 && c.kmax >= 1;
+  return c.dtype == CUTQC_F32 && c.batch == 1 && c.fA >= 7 && c.fB >= 8 && c.kmax >= 1 && c.epi_tab;
+}
+
+std::vector<uint8_t> tc_epilogue_table(const std::vector<uint64_t>& va, const std::vector<uint64_t>& vb) {
+  std::vector<uint8_t> bytes;
+  if (va.size() < 5 || vb.size() < 5) return bytes;
+  // the 10 chunk index bits: lane bits (m bits 0-4) and column bits (n bits 0-4)
+  struct Bit {
+    uint64_t value;
+    int32_t stage;
+  };
+  std::vector<Bit> bits;
+  for (int b = 0; b < 5; ++b) bits.push_back({va[b], (int32_t)(EPI_PITCH << b)});
+  for (int b = 0; b < 5; ++b) bits.push_back({vb[b], (int32_t)(1 << b)});
+  std::sort(bits.begin(), bits.end(), [](const Bit& x, const Bit& y) { return x.value < y.value; });
+  EpiTab t{};
+  for (int i = 0; i < 32; ++i) {
+    for (int k = 0; k < 5; ++k) {
+      if ((i >> k) & 1) {
+        t.slo[i] += bits[k].stage;
+        t.shi[i] += bits[5 + k].stage;
+        t.glo[i] += bits[k].value;
+        t.ghi[i] += bits[5 + k].value;
+      }
+    }
+  }
+  int j = 0;
+  while (j < 10 && bits[j].value == (uint64_t(1) << j)) ++j;
+  t.contig = j;
+  bytes.resize(sizeof(EpiTab));
+  std::memcpy(bytes.data(), &t, sizeof(EpiTab));
+  return bytes;
 }
 
 size_t tc_workspace_bytes(const Contraction& c) {
@@ -461,6 +552,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   a.scale = (float)c.scale;
   a.sum = c.sum;
   a.vecB = c.vecB;
+  a.epi = c.epi_tab;
   a.status = status;
   static int sms = 0;
   static bool attr = false;

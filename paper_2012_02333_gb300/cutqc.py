@@ -74,12 +74,13 @@ _lib.cutqc_simulate_subcircuit.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c
                                            C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
 _lib.cutqc_profile.argtypes = [C.c_int32]
+_lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
-           "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read"):
+           "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -105,6 +106,15 @@ def launch_count() -> int:
 def last_algo() -> int:
     """cutqc_algo of the last full-definition call's final contraction."""
     return int(_lib.cutqc_last_algo())
+
+
+def last_split():
+    """(split products 3 or 6, a-priori magnitude S) of the last tensor-core
+    contraction on this thread (synchronises its stream)."""
+    n = C.c_int32()
+    b = C.c_double()
+    _check(_lib.cutqc_last_split(C.byref(n), C.byref(b)))
+    return int(n.value), float(b.value)
 
 
 def release() -> None:
