@@ -147,8 +147,22 @@ struct Step {
   size_t ws_bound = 0, ws_nseg = 0;
 };
 
+struct DdSubPlan {
+  int64_t rows = 1;
+  int f = 0, a = 0, mg = 0;
+  uint64_t zoom = 0;                   // x index bits fixed by zoomed qubits
+  std::vector<uint64_t> depAct, depMrg;
+  size_t off_act = 0, off_mrg = 0;     // in the plan's DD table block
+  std::vector<int> act_rank;           // bin rank of each active output (x-bit order)
+  std::vector<int> cuts;
+  size_t ws_merged = 0;                // offset of the merged tensor in the front region
+};
+
 struct Plan {
   int n_out = 0, K = 0, dtype = CUTQC_F32;
+  std::vector<DdSubPlan> dd;           // dynamic definition only
+  size_t dd_front = 0;
+  void* ddtab = nullptr;
   std::vector<Node> nodes;
   std::vector<Step> steps;
   std::vector<size_t> ws_node;    // workspace offset of each merge-result tensor
@@ -159,6 +173,7 @@ struct Plan {
   size_t dtab_bytes = 0;
   ~Plan() {
     if (dtab) cudaFree(dtab);
+    if (ddtab) cudaFree(ddtab);
   }
 };
 
@@ -454,8 +469,80 @@ static void build_fd_plan(Plan& P, const cutqc_problem* p) {
 }
 
 // Run a plan.  `tensor(i)` gives the device pointer of original node i.
-static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& orig_tensor, void* out,
-                     double* sum, int algo, cudaStream_t s) {
+// Dynamic-definition plan: one node per subcircuit holding its merged tensor
+// (rows x 2^#active outputs of the subcircuit), output positions = the bin
+// ranks of the active qubits (lowest-numbered active qubit = most significant).
+static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
+  std::vector<int> rank(p->n_qubits, -1);
+  int na = 0;
+  for (int q = 0; q < p->n_qubits; ++q)
+    if (role[q] == 0) rank[q] = na++;
+  P.n_out = na;
+  P.K = p->n_cuts;
+  P.dtype = p->dtype;
+  const size_t es = dtype_size(p->dtype);
+  size_t front = 0;
+  for (int c = 0; c < p->n_sub; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    DdSubPlan d;
+    d.f = s.n_eff;
+    d.rows = int64_t(1) << (2 * (s.k_in + s.k_out));
+    std::vector<uint64_t> act_val, mrg_val;
+    Node nd;
+    nd.orig = c;
+    for (int j = 0; j < s.k_in; ++j) nd.cuts.push_back(s.in_cut[j]);
+    for (int j = 0; j < s.k_out; ++j) nd.cuts.push_back(s.out_cut[j]);
+    for (int j = 0; j < s.n_eff; ++j) {
+      const int q = s.out_qubit[j];
+      const uint64_t xbit = uint64_t(1) << (s.n_eff - 1 - j);
+      if (role[q] == 0) {
+        act_val.push_back(xbit);
+        d.act_rank.push_back(rank[q]);
+        nd.bits.push_back(rank[q]);
+      } else if (role[q] == 1) {
+        mrg_val.push_back(xbit);
+      } else if (role[q] == 3) {
+        d.zoom |= xbit;
+      }
+    }
+    d.a = (int)act_val.size();
+    d.mg = (int)mrg_val.size();
+    // index bit i (least significant first) of xa / xm is the (count-1-i)-th listed output
+    std::reverse(act_val.begin(), act_val.end());
+    std::reverse(mrg_val.begin(), mrg_val.end());
+    d.depAct = deposit_table(act_val);
+    d.depMrg = deposit_table(mrg_val);
+    d.cuts = nd.cuts;
+    d.ws_merged = front;
+    front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * es);
+    P.dd.push_back(d);
+    P.nodes.push_back(nd);
+  }
+  P.dd_front = front;
+  plan_contractions(P, p->n_cuts);
+  finalize_plan(P);
+  size_t off = 0;
+  for (DdSubPlan& d : P.dd) {
+    d.off_act = off;
+    off = align_up(off + d.depAct.size() * 8);
+    d.off_mrg = off;
+    off = align_up(off + d.depMrg.size() * 8);
+  }
+  CUTQC_CUDA(cudaMalloc(&P.ddtab, std::max<size_t>(off, 256)));
+  std::vector<char> host(std::max<size_t>(off, 256), 0);
+  for (DdSubPlan& d : P.dd) {
+    std::memcpy(host.data() + d.off_act, d.depAct.data(), d.depAct.size() * 8);
+    std::memcpy(host.data() + d.off_mrg, d.depMrg.data(), d.depMrg.size() * 8);
+  }
+  CUTQC_CUDA(cudaMemcpy(P.ddtab, host.data(), host.size(), cudaMemcpyHostToDevice));
+}
+
+// Run a plan.  The workspace holds [front | the plan's own buffers | back];
+// `pre(front_ptr)` is called once the workspace exists and returns the device
+// tensors of the plan's original nodes.  Returns a pointer to the back region.
+static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
+                      const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
+                      cudaStream_t s) {
   size_t tc_ws = 0;
   std::vector<Contraction> cs(P.steps.size());
   char* base = nullptr;
@@ -494,7 +581,11 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     tc_ws = tc_workspace_bytes(cs.back());
     need = align_up(need) + tc_ws;
   }
-  base = static_cast<char*>(workspace(ds, need));
+  front = align_up(front);
+  need = align_up(need);
+  char* ws = static_cast<char*>(workspace(ds, front + need + back));
+  base = ws + front;
+  const std::vector<const void*> orig_tensor = pre(ws);
   auto node_ptr = [&](int i) -> const void* {
     const Node& nd = P.nodes[i];
     if (nd.orig >= 0) return orig_tensor[nd.orig];
@@ -550,6 +641,7 @@ static void run_plan(DeviceState& ds, Plan& P, const std::vector<const void*>& o
     if (final_step) g_last_algo = use_tc_final ? (algo == CUTQC_AUTO ? CUTQC_TC_BF16X3 : algo) : CUTQC_CC;
     if (final_step) prof_end(s, ev);
   }
+  return base + need;
 }
 
 }  // namespace cutqc
@@ -574,9 +666,14 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
     for (int i = 0; i < n_problems; ++i) {
       const cutqc_problem* p = &problems[i];
       Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
-      std::vector<const void*> t(p->n_sub);
-      for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
-      run_plan(ds, P, t, out[i], sum_p ? sum_p + i : nullptr, algo, s);
+      run_plan(
+          ds, P, 0, 0,
+          [&](char*) {
+            std::vector<const void*> t(p->n_sub);
+            for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
+            return t;
+          },
+          out[i], sum_p ? sum_p + i : nullptr, algo, s);
     }
   });
 }
@@ -623,7 +720,110 @@ int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates, int32_t 
 
 int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void* bins, int32_t topk,
                          int64_t* top_idx, double* top_val, int32_t algo, void* stream) {
-  return guarded([&] { fail(CUTQC_ERR_UNSUPPORTED, "dynamic definition is not built yet"); });
+  return guarded([&] {
+    validate(problem, true);
+    if (!role) fail(CUTQC_ERR_ARG, "role is NULL");
+    if (!bins) fail(CUTQC_ERR_ARG, "bins is NULL");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X6) fail(CUTQC_ERR_ARG, "unknown algo");
+    if (topk < 0 || topk > 32) fail(CUTQC_ERR_UNSUPPORTED, "topk must be in 0..32");
+    if (topk > 0 && (!top_idx || !top_val)) fail(CUTQC_ERR_ARG, "NULL top_idx / top_val");
+    int na = 0;
+    for (int q = 0; q < problem->n_qubits; ++q) {
+      if (role[q] < 0 || role[q] > 3) fail(CUTQC_ERR_ARG, "role values must be 0..3");
+      na += role[q] == 0;
+    }
+    if (na < 1) fail(CUTQC_ERR_SHAPE, "dynamic definition needs at least one active qubit");
+    if (na > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "more than 34 active qubits");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceState& ds = device_state();
+    const cutqc_problem* p = problem;
+    Plan& P = get_plan(ds, fd_key(p, 1, role, 0), [&](Plan& P) { build_dd_plan(P, p, role); });
+    const int64_t nbins = int64_t(1) << na;
+    int64_t max_rows = 1;
+    for (const DdSubPlan& d : P.dd) max_rows = std::max(max_rows, d.rows);
+    constexpr int NC = 32;
+    size_t back = 0, off_tk = 0, off_cv = 0, off_ci = 0, off_m64 = 0, off_val = 0;
+    if (topk > 0) {
+      off_tk = 0;
+      back = align_up(topk_workspace_bytes(nbins));
+      off_cv = back;
+      back = align_up(back + NC * 4);
+      off_ci = back;
+      back = align_up(back + NC * 8);
+      off_m64 = back;
+      back = align_up(back + (size_t)NC * p->n_sub * max_rows * 8);
+      off_val = back;
+      back = align_up(back + NC * 8);
+    }
+    char* ddtab = static_cast<char*>(P.ddtab);
+    char* back_ptr = run_plan(
+        ds, P, P.dd_front, back,
+        [&](char* front) {
+          std::vector<const void*> t(p->n_sub);
+          for (int c = 0; c < p->n_sub; ++c) {
+            const DdSubPlan& d = P.dd[c];
+            launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
+                            reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
+                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, front + d.ws_merged, s);
+            t[c] = front + d.ws_merged;
+          }
+          return t;
+        },
+        bins, nullptr, algo, s);
+    if (topk > 0) {
+      float* cv = reinterpret_cast<float*>(back_ptr + off_cv);
+      int64_t* ci = reinterpret_cast<int64_t*>(back_ptr + off_ci);
+      launch_topk(bins, P.dtype, nbins, back_ptr + off_tk, cv, ci, s);
+      DdEvalArgs ea{};
+      ea.n_sub = p->n_sub;
+      ea.n_cuts = p->n_cuts;
+      ea.n_active = na;
+      ea.n_cand = NC;
+      ea.max_rows = max_rows;
+      ea.scale = std::ldexp(1.0, -p->n_cuts);
+      ea.cand_idx = ci;
+      for (int c = 0; c < p->n_sub; ++c) {
+        const DdSubPlan& d = P.dd[c];
+        DdEvalSub& e = ea.sub[c];
+        ea.tens[c] = p->sub[c].tensor;
+        e.rows = d.rows;
+        e.cols = int64_t(1) << d.f;
+        e.a = d.a;
+        e.mg = d.mg;
+        e.nbA = (d.a + 7) / 8;
+        e.nbM = (d.mg + 7) / 8;
+        e.zoom = d.zoom;
+        e.depAct = reinterpret_cast<const uint64_t*>(ddtab + d.off_act);
+        e.depMrg = reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg);
+        for (int i = 0; i < d.a; ++i) e.act_rank[i] = d.act_rank[i];
+        e.ncuts = (int)d.cuts.size();
+        for (int j = 0; j < e.ncuts; ++j) e.cuts[j] = d.cuts[j];
+      }
+      double* m64 = reinterpret_cast<double*>(back_ptr + off_m64);
+      double* val = reinterpret_cast<double*>(back_ptr + off_val);
+      launch_dd_rerank(ea, P.dtype, m64, val, s);
+      std::vector<int64_t> hi(NC);
+      std::vector<double> hv(NC);
+      CUTQC_CUDA(cudaMemcpyAsync(hi.data(), ci, NC * 8, cudaMemcpyDeviceToHost, s));
+      CUTQC_CUDA(cudaMemcpyAsync(hv.data(), val, NC * 8, cudaMemcpyDeviceToHost, s));
+      CUTQC_CUDA(cudaStreamSynchronize(s));
+      std::vector<std::pair<double, int64_t>> cand;
+      for (int j = 0; j < NC; ++j)
+        if (hi[j] >= 0 && hi[j] < nbins) cand.emplace_back(hv[j], hi[j]);
+      std::sort(cand.begin(), cand.end(), [](const std::pair<double, int64_t>& x, const std::pair<double, int64_t>& y) {
+        return x.first > y.first || (x.first == y.first && x.second < y.second);
+      });
+      for (int j = 0; j < topk; ++j) {
+        if (j < (int)cand.size()) {
+          top_idx[j] = cand[j].second;
+          top_val[j] = cand[j].first;
+        } else {
+          top_idx[j] = -1;
+          top_val[j] = 0.0;
+        }
+      }
+    }
+  });
 }
 
 int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_out, const cutqc_loss* loss,

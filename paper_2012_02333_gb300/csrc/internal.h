@@ -81,6 +81,31 @@ size_t tc_workspace_bytes(const Contraction& c);
 // index bit first.  Empty when the shape cannot use it.
 std::vector<uint8_t> tc_epilogue_table(const std::vector<uint64_t>& va, const std::vector<uint64_t>& vb);
 
+// k_dd.cu
+struct DdEvalSub {
+  int64_t rows, cols;
+  int a, mg, nbA, nbM;
+  uint64_t zoom;
+  const uint64_t* depAct;
+  const uint64_t* depMrg;
+  int act_rank[36];
+  int cuts[12];
+  int ncuts;
+};
+struct DdEvalArgs {
+  int n_sub, n_cuts, n_active, n_cand;
+  int64_t max_rows;
+  double scale;
+  const int64_t* cand_idx;
+  const void* tens[16];
+  DdEvalSub sub[16];
+};
+void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
+                     const uint64_t* depMrg, uint64_t zoom, void* M, cudaStream_t s);
+size_t topk_workspace_bytes(int64_t n);
+void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
+void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s);
+
 // k_sim.cu
 struct SimPlan {
   int d, k_in, k_out, n_eff;

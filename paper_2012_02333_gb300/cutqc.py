@@ -218,6 +218,25 @@ def reconstruct_fd(cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor], alg
     return out, sp
 
 
+def cutqc_reconstruct_dd(problem: Problem, roles: Sequence[int], bins: torch.Tensor, topk: int = 0,
+                         algo: str = "auto", stream=None):
+    """Binding of cutqc_reconstruct_dd (one dynamic-definition recursion,
+    Algorithm 1).  roles[q]: 0 active, 1 merged, 2 zoomed at 0, 3 zoomed at 1.
+    Fills `bins` (2^#active entries, the tensors' dtype) and returns the topk
+    heaviest bins ranked in FP64 as (indices, values)."""
+    n_act = sum(1 for r in roles if r == 0)
+    if len(roles) != problem.n_qubits:
+        raise ValueError("one role per qubit")
+    if bins.dtype != problem.dtype or bins.numel() != 2 ** n_act or not bins.is_cuda:
+        raise ValueError("bins must be a CUDA tensor of 2^#active entries in the tensors' dtype")
+    r = (C.c_int8 * len(roles))(*[int(x) for x in roles])
+    ti = (C.c_int64 * max(topk, 1))()
+    tv = (C.c_double * max(topk, 1))()
+    _check(_lib.cutqc_reconstruct_dd(C.byref(problem.c), r, C.c_void_p(bins.data_ptr()), topk, ti, tv,
+                                     ALGOS[algo], _stream_ptr(stream)))
+    return [int(ti[j]) for j in range(topk)], [float(tv[j]) for j in range(topk)]
+
+
 def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, device=None, stream=None) -> torch.Tensor:
     """Binding of cutqc_simulate_subcircuit: the attributed tensor of one
     subcircuit, simulated on the GPU (input preparation)."""

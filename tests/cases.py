@@ -21,3 +21,9 @@ SMALL = {
 def supremacy_4x6():
     """4x6 supremacy grid, depth 8, 2 subcircuits of <= 15 qubits (K = 4)."""
     return C.supremacy_4x6(0)
+
+
+def dd_twin():
+    """Scaled twin of the 80-qubit dynamic-definition workload: a 4x5 grid of
+    depth 10 cut into 2x2 blocks (4 subcircuits), K <= 8."""
+    return C.grid_blocks(4, 5, 10, 0, 2, 2, 8, 10)

@@ -1,0 +1,105 @@
+"""GPU parity of dynamic definition (Algorithm 1) against the FP64 oracle:
+bins per recursion element by element, the FP64-ranked top lists, the zoom
+sequence, the Figure 7 example, and a scaled twin of the 80-qubit workload."""
+import json
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(__file__))
+import cases  # noqa: E402
+from test_gpu_fd import env, oracle_case, to_dev  # noqa: E402,F401
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def check_run(env, cc, T, dtype_np, algo, n_active, recursions, strategy, tol):
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    from paper_2012_02333_gb300 import dd
+    Tq = [t.astype(dtype_np) for t in T]
+    T64 = [t.astype(np.float64) for t in Tq]
+    tdt = torch.float64 if dtype_np == np.float64 else torch.float32
+    st = dd.run(cc, to_dev(torch, Tq, tdt), n_active, recursions, strategy, algo)
+    assert len(st.recursions) >= 1
+    for ri, rec in enumerate(st.recursions):
+        want = rc.dd_bins(cc.subs, T64, cc.n, cc.n_cuts, rec.roles)
+        got = rec.bins.double().cpu().numpy()
+        assert np.abs(got - want).max() <= tol, (ri, np.abs(got - want).max())
+        # FP64-ranked top list: values are the oracle's bins at those indices,
+        # in non-increasing order, and nothing outside beats the last one
+        idx = [i for i, _ in rec.top if i >= 0]
+        vals = [v for i, v in rec.top if i >= 0]
+        assert np.allclose(vals, want[idx], atol=1e-12)
+        assert all(vals[j] >= vals[j + 1] for j in range(len(vals) - 1))
+        if len(idx) < len(want):
+            rest = np.delete(want, idx)
+            assert rest.max() <= vals[-1] + 2 * tol
+        if rec.parent is not None:
+            pr, pb = rec.parent
+            # the zoomed bin's probability is split exactly across the child bins
+            parent_val = rc.dd_bins(cc.subs, T64, cc.n, cc.n_cuts, st.recursions[pr].roles)[pb]
+            assert want.sum() == pytest.approx(parent_val, abs=1e-12)
+    return st
+
+
+@pytest.mark.parametrize("name", ["bv6_k1", "qaoa8_k4", "grid4x4_s4", "hwea16_s2", "grid4x5_k5"])
+def test_dd_fp64_cc(env, name):
+    cc, T = oracle_case(name, cases.SMALL[name])
+    check_run(env, cc, T, np.float64, "cc", 3, 5, "bfs", 1e-12)
+
+
+@pytest.mark.parametrize("strategy", ["bfs", "dfs"])
+@pytest.mark.parametrize("name", ["qaoa8_k4", "grid4x4_s4", "hwea16_s2", "grid4x5_k5"])
+def test_dd_fp32_auto(env, name, strategy):
+    cc, T = oracle_case(name, cases.SMALL[name])
+    na = 4 if cc.n >= 12 else 2
+    check_run(env, cc, T, np.float32, "auto", na, 6, strategy, 1e-6)
+
+
+def test_dd_active_covering_tensor_core_shapes(env):
+    """Enough active qubits that the final contraction takes the tensor-core
+    path (2^8 x 2^8 bins) with merged and zoomed qubits interleaved."""
+    cc, T = oracle_case("grid4x5_k5", cases.SMALL["grid4x5_k5"])
+    check_run(env, cc, T, np.float32, "auto", 16, 3, "bfs", 1e-6)
+
+
+def test_figure7_bv_on_gpu(env):
+    torch, cutqc = env
+    from oracle import attribution as at
+    from paper_2012_02333_gb300 import circuits as C
+    from paper_2012_02333_gb300 import dd
+    g = json.load(open(os.path.join(GOLDEN, "fig7_bv4_dd.json")))
+    cc = C.chain_blocks(C.bv(g["n_qubits"], 0, g["secret"]), 2, max_width=3)
+    T = at.tensors(cc)
+    for algo, dt in (("cc", torch.float64), ("auto", torch.float32)):
+        st = dd.run(cc, to_dev(torch, T, dt), g["n_active"], 4, "dfs", algo)
+        for rec, want in zip(st.recursions, g["bins_per_recursion"]):
+            assert np.allclose(rec.bins.double().cpu().numpy(), want, atol=1e-6)
+        last = st.recursions[-1]
+        assert last.top[0][0] == 1 and last.top[0][1] == pytest.approx(g["solution_probability"], abs=1e-6)
+        bits = [1 if r == 3 else 0 for r in last.roles[:3]] + [last.top[0][0]]
+        assert sum(b << (3 - q) for q, b in enumerate(bits)) == g["solution"]
+
+
+def test_dd_resume_reproduces_run(env):
+    torch, cutqc = env
+    from paper_2012_02333_gb300 import dd
+    cc, T = oracle_case("grid4x4_s4", cases.SMALL["grid4x4_s4"])
+    ts = to_dev(torch, [t.astype(np.float32) for t in T], torch.float32)
+    full = dd.run(cc, ts, 3, 6, "bfs")
+    part = dd.run(cc, ts, 3, 3, "bfs")
+    resumed = dd.run(cc, ts, 3, 6, "bfs", state=dd.DDState.from_json(part.to_json()))
+    assert [r.roles for r in resumed.recursions] == [r.roles for r in full.recursions]
+    assert [r.parent for r in resumed.recursions] == [r.parent for r in full.recursions]
+
+
+def test_dd_twin_of_80_qubit_workload(env):
+    """The 80-qubit dynamic-definition workload's scaled twin: a 4x5 grid of
+    depth 10 cut into 2x2 blocks (4 subcircuits), 6 active qubits, 10
+    recursions, BFS, FP32 tensors."""
+    cc, T = oracle_case("grid4x5_s4_dd", cases.dd_twin)
+    check_run(env, cc, T, np.float32, "auto", 6, 10, "bfs", 1e-6)
