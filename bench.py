@@ -11,7 +11,7 @@ checks, compaction, operand preparation, the contraction into all 2^24
 probabilities, the FP64 sum).
 
 Metric: reconstructed probabilities per second (whole job, all ranks).  The
-L2 is flushed (256 MiB write) between timed steps; each step is timed with
+L2 is flushed (256 MiB written, then read back) before each timed step; each step is timed with
 CUDA events on its stream; the max over ranks is reported.  With --gpus N
 under torchrun every rank reconstructs its own replica (weak scaling, no
 collective on the data path).
