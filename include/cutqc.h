@@ -155,6 +155,27 @@ CUTQC_API int cutqc_reconstruct_backward(const cutqc_problem* problem,
                                void* const* grad_tensor, double* loss_value,
                                void* stream);
 
+/* Full definition that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot let the library call
+ * cudaMalloc - processes whose device memory is entirely reserved up front by
+ * another allocator, and latency-sensitive callers that forbid device
+ * allocation after start-up because cudaMalloc / cudaFree can synchronise the
+ * device and stall other streams.  It computes what cutqc_reconstruct_fd
+ * computes with CUTQC_CC (CUDA-core contraction in the tensors' dtype, early
+ * termination, FP64 sum) for a problem of exactly two subcircuits, writing
+ * out (device, 2^n_qubits entries) and, if sum_p is not NULL, the FP64 sum to
+ * sum_p (device double).  All of its scratch lives in one 4 MiB array in
+ * device global memory that the library declares statically; every GPU that
+ * loads the library holds it until the process exits.  Problems that need
+ * more scratch (roughly K > 8 cuts) are rejected with CUTQC_ERR_UNSUPPORTED
+ * and a message giving the bytes needed.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress, with that device
+ * current); make that first call before any stream capture.  Every call
+ * shares the array: calls whose work overlaps on the GPU (for instance on two
+ * streams) race and must not be issued. */
+CUTQC_API int cutqc_reconstruct_fd_noalloc(const cutqc_problem* problem, void* out, double* sum_p,
+                                           void* stream);
+
 /* ---- input preparation: the GPU subcircuit simulator -------------------- */
 
 typedef enum {

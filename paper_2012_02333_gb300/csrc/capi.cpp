@@ -71,6 +71,10 @@ static int guarded(F&& f) {
   }
 }
 
+int run_guarded(void (*f)(void*), void* ctx) {
+  return guarded([&] { f(ctx); });
+}
+
 // ------------------------------------------------------------- validation
 static constexpr int kMaxCuts = 12;
 static constexpr int kMaxSub = 16;
@@ -469,6 +473,39 @@ static void build_fd_plan(Plan& P, const cutqc_problem* p) {
 }
 
 // Run a plan.  `tensor(i)` gives the device pointer of original node i.
+void plan_pair_host(const cutqc_problem* p, PairPlanHost& out) {
+  validate(p, true);
+  if (p->n_sub != 2) fail(CUTQC_ERR_UNSUPPORTED, "this entry point takes exactly two subcircuits");
+  if (p->n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
+  Plan P;
+  P.n_out = p->n_qubits;
+  P.K = p->n_cuts;
+  P.dtype = p->dtype;
+  for (int c = 0; c < 2; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    Node nd;
+    nd.orig = c;
+    for (int j = 0; j < s.k_in; ++j) nd.cuts.push_back(s.in_cut[j]);
+    for (int j = 0; j < s.k_out; ++j) nd.cuts.push_back(s.out_cut[j]);
+    for (int i = 0; i < s.n_eff; ++i) nd.bits.push_back(s.out_qubit[i]);
+    P.nodes.push_back(nd);
+  }
+  plan_contractions(P, p->n_cuts);
+  const Step& st = P.steps.back();
+  out.fA = P.nodes[st.a].f();
+  out.fB = P.nodes[st.b].f();
+  out.kmax = st.kmax;
+  out.vecB = st.vecB;
+  out.sub_a = P.nodes[st.a].orig;
+  out.sub_b = P.nodes[st.b].orig;
+  out.K = p->n_cuts;
+  out.rowsA = (int)P.nodes[st.a].rows();
+  out.rowsB = (int)P.nodes[st.b].rows();
+  out.rows = st.rows;
+  out.depA = st.depA;
+  out.depB = st.depB;
+}
+
 // Dynamic-definition plan: one node per subcircuit holding its merged tensor
 // (rows x 2^#active outputs of the subcircuit), output positions = the bin
 // ranks of the active qubits (lowest-numbered active qubit = most significant).

@@ -23,6 +23,20 @@ void check_cuda(cudaError_t e, const char* what);
 #define CUTQC_CUDA(call) ::cutqc::check_cuda((call), #call)
 
 void count_launch(int n = 1);
+
+// Runs `f` under the library lock, converting errors to a status and the
+// thread's last-error message (the body of every C entry point).
+int run_guarded(void (*f)(void*), void* ctx);
+
+// Host-only plan of a two-subcircuit full-definition contraction (no device
+// allocation): the final step's row pairs, deposit tables and shape.
+struct PairPlanHost {
+  int fA = 0, fB = 0, kmax = 0, vecB = 1, sub_a = 0, sub_b = 1, K = 0;
+  int rowsA = 0, rowsB = 0;
+  std::vector<int32_t> rows;        // [2][kmax]
+  std::vector<uint64_t> depA, depB; // [ceil(f/8)][256]
+};
+void plan_pair_host(const cutqc_problem* p, PairPlanHost& out);
 void check_launch(const char* what);
 
 // Device status word values (written by kernels, read at sync points).

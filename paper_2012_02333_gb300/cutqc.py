@@ -73,6 +73,7 @@ _lib.cutqc_reconstruct_backward.argtypes = [C.POINTER(cutqc_problem), C.c_void_p
 _lib.cutqc_simulate_subcircuit.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+_lib.cutqc_reconstruct_fd_noalloc.argtypes = [C.POINTER(cutqc_problem), C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -80,7 +81,8 @@ _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
-           "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split"):
+           "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
+           "cutqc_reconstruct_fd_noalloc"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -216,6 +218,22 @@ def reconstruct_fd(cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor], alg
     p = Problem.from_cut(cc, dts)
     cutqc_reconstruct_fd([p], [out], algo, sp, s)
     return out, sp
+
+
+def cutqc_reconstruct_fd_noalloc(problem: Problem, out: torch.Tensor, sum_p: Optional[torch.Tensor] = None,
+                                 stream=None) -> None:
+    """Binding of cutqc_reconstruct_fd_noalloc: the two-subcircuit CUDA-core
+    full definition with its scratch in the library's static device array (for
+    callers that cannot let the library allocate device memory)."""
+    if out.dtype != problem.dtype or out.numel() != 2 ** problem.n_qubits or not out.is_cuda:
+        raise ValueError("out must be a CUDA tensor of 2^n entries in the tensors' dtype")
+    sp = None
+    if sum_p is not None:
+        if sum_p.dtype != torch.float64 or not sum_p.is_cuda:
+            raise ValueError("sum_p must be a CUDA float64 tensor")
+        sp = sum_p.data_ptr()
+    _check(_lib.cutqc_reconstruct_fd_noalloc(C.byref(problem.c), C.c_void_p(out.data_ptr()), sp,
+                                             _stream_ptr(stream)))
 
 
 def cutqc_reconstruct_dd(problem: Problem, roles: Sequence[int], bins: torch.Tensor, topk: int = 0,
