@@ -219,6 +219,51 @@ def grad(subs, tensors, n_qubits: int, n_cuts: int, G: np.ndarray):
     return [g * 2.0 ** -K for g in grads]
 
 
+def grad_entry(subs, tensors, n_qubits: int, n_cuts: int, c: int, row: int, xc: int, G_of) -> float:
+    """One entry dL/dT_c[row][xc] of the chain rule above, for large n: the
+    sum over the cut assignments e with e|c = row and over the outputs x with
+    x|c = xc, G given as a function of an array of global indices."""
+    K = n_cuts
+    Ts = [_flat(T, s) for T, s in zip(tensors, subs)]
+    others = [j for j in range(len(subs)) if j != c]
+    # global index contribution of subcircuit c's fixed bits
+    base = 0
+    sc = subs[c]
+    for i, q in enumerate(sc.out_qubit):
+        if (xc >> (sc.n_eff - 1 - i)) & 1:
+            base |= 1 << (n_qubits - 1 - q)
+    total = 0.0
+    for e in range(4 ** K):
+        dg = _digits(e, K)
+        if row_of(sc, dg) != row:
+            continue
+        # Kronecker product of the other subcircuits' vectors over their bits
+        vals = np.ones(1)
+        gidx = np.full(1, base, dtype=np.int64)
+        for j in others:
+            s = subs[j]
+            v = Ts[j][row_of(s, dg)]
+            loc = np.arange(2 ** s.n_eff, dtype=np.int64)
+            off = np.zeros(2 ** s.n_eff, dtype=np.int64)
+            for i, q in enumerate(s.out_qubit):
+                off |= ((loc >> (s.n_eff - 1 - i)) & 1) << (n_qubits - 1 - q)
+            vals = np.multiply.outer(vals, v).reshape(-1)
+            gidx = np.add.outer(gidx, off).reshape(-1)
+        total += float(np.dot(vals, G_of(gidx)))
+    return total * 2.0 ** -K
+
+
+def maxcut_of(n_qubits: int, edges):
+    """G_of for the MaxCut cost: the cut count of each global index."""
+    def f(x):
+        x = np.asarray(x, dtype=np.int64)
+        c = np.zeros(x.shape)
+        for (i, j) in edges:
+            c += ((x >> (n_qubits - 1 - i)) & 1) != ((x >> (n_qubits - 1 - j)) & 1)
+        return c
+    return f
+
+
 def maxcut_values(n_qubits: int, edges) -> np.ndarray:
     """C(x) = number of edges whose endpoints differ in x, for all 2^n x."""
     x = np.arange(2 ** n_qubits, dtype=np.int64)

@@ -865,7 +865,88 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
 
 int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_out, const cutqc_loss* loss,
                                void* const* grad_tensor, double* loss_value, void* stream) {
-  return guarded([&] { fail(CUTQC_ERR_UNSUPPORTED, "backward is not built yet"); });
+  return guarded([&] {
+    validate(problem, true);
+    const cutqc_problem* p = problem;
+    if (p->n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs n_qubits <= 34");
+    if (p->n_sub != 2) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint supports circuits cut into two subcircuits");
+    if (!grad_tensor || !grad_tensor[0] || !grad_tensor[1]) fail(CUTQC_ERR_ARG, "NULL gradient pointer");
+    const bool maxcut = loss && loss->kind == CUTQC_LOSS_MAXCUT;
+    if (loss && loss->kind != CUTQC_LOSS_NONE && !maxcut) fail(CUTQC_ERR_ARG, "unknown loss kind");
+    if (!maxcut && !grad_out) fail(CUTQC_ERR_ARG, "need grad_out or a loss");
+    if (maxcut && (loss->n_edges < 0 || (loss->n_edges && !loss->edges))) fail(CUTQC_ERR_ARG, "bad edge list");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceState& ds = device_state();
+    Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
+    if (P.steps.size() != 1) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint supports a single final contraction");
+    const Step& st = P.steps[0];
+    const Node& A = P.nodes[st.a];
+    const Node& B = P.nodes[st.b];
+    const int sa = A.orig, sb = B.orig;
+    if (sa < 0 || sb < 0) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs two original subcircuits");
+    const int fA = A.f(), fB = B.f();
+    const int64_t rowsA = A.rows(), rowsB = B.rows();
+    const double scale = std::ldexp(1.0, -P.K);
+    char* dtab = static_cast<char*>(P.dtab);
+    const int32_t* rowA = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
+    const int32_t* rowB = rowA + st.kmax;
+    if ((int64_t)st.kmax != rowsA || (int64_t)st.kmax != rowsB)
+      fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs every slot of both subcircuits joined by a cut");
+    void* dA = grad_tensor[sa];
+    void* dB = grad_tensor[sb];
+    const void* TA = p->sub[sa].tensor;
+    const void* TB = p->sub[sb].tensor;
+    if (maxcut) {
+      // index bit (least significant = 0) of each qubit on its side
+      std::vector<int> side(p->n_qubits, -1), bit(p->n_qubits, -1);
+      for (int i = 0; i < fA; ++i) {
+        side[A.bits[fA - 1 - i]] = 0;
+        bit[A.bits[fA - 1 - i]] = i;
+      }
+      for (int i = 0; i < fB; ++i) {
+        side[B.bits[fB - 1 - i]] = 1;
+        bit[B.bits[fB - 1 - i]] = i;
+      }
+      BwdEdges inA{}, inB{};
+      BwdBits brA{}, brB{};
+      for (int k = 0; k < loss->n_edges; ++k) {
+        const int u = loss->edges[2 * k], v = loss->edges[2 * k + 1];
+        if (u < 0 || v < 0 || u >= p->n_qubits || v >= p->n_qubits || u == v) fail(CUTQC_ERR_ARG, "bad edge");
+        if (side[u] == side[v]) {
+          BwdEdges& E = side[u] == 0 ? inA : inB;
+          if (E.n >= 96) fail(CUTQC_ERR_UNSUPPORTED, "more than 96 edges inside one subcircuit");
+          E.p[E.n] = bit[u];
+          E.q[E.n] = bit[v];
+          ++E.n;
+        } else {
+          if (brA.n >= 16) fail(CUTQC_ERR_UNSUPPORTED, "more than 16 edges between the subcircuits");
+          const int ua = side[u] == 0 ? u : v, ub = side[u] == 0 ? v : u;
+          brA.p[brA.n++] = bit[ua];
+          brB.p[brB.n++] = bit[ub];
+        }
+      }
+      const size_t bytesA = align_up((size_t)(2 + brA.n) * rowsA * 8);
+      const size_t bytesB = align_up((size_t)(2 + brB.n) * rowsB * 8);
+      char* ws = static_cast<char*>(workspace(ds, bytesA + bytesB));
+      double* sumsA = reinterpret_cast<double*>(ws);
+      double* sumsB = reinterpret_cast<double*>(ws + bytesA);
+      launch_bwd_rowsums(TA, P.dtype, rowsA, fA, inA, brA, sumsA, s);
+      launch_bwd_rowsums(TB, P.dtype, rowsB, fB, inB, brB, sumsB, s);
+      launch_bwd_maxcut_grad(rowA, rowB, st.kmax, fA, inA, brA, sumsB, rowsB, scale, dA, P.dtype, s);
+      launch_bwd_maxcut_grad(rowB, rowA, st.kmax, fB, inB, brB, sumsA, rowsA, scale, dB, P.dtype, s);
+      if (loss_value)
+        launch_bwd_maxcut_loss(rowA, rowB, st.kmax, sumsA, rowsA, sumsB, rowsB, brA.n, scale, loss_value, s);
+    } else {
+      const uint64_t* depA = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
+      const uint64_t* depB = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
+      launch_bwd_cc(TB, grad_out, rowA, rowB, st.kmax, fA, fB, depA, depB, scale, dA, P.dtype, s);
+      launch_bwd_cc(TA, grad_out, rowB, rowA, st.kmax, fB, fA, depB, depA, scale, dB, P.dtype, s);
+      if (loss_value) {
+        CUTQC_CUDA(cudaMemsetAsync(loss_value, 0, sizeof(double), s));
+        launch_dot(dA, TA, rowsA << fA, P.dtype, loss_value, s);
+      }
+    }
+  });
 }
 
 const char* cutqc_last_error(void) { return g_last_error.c_str(); }

@@ -120,6 +120,26 @@ size_t topk_workspace_bytes(int64_t n);
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
 void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s);
 
+// k_bwd.cu
+struct BwdEdges {   // edges as pairs of index bits (least significant = 0)
+  int n;
+  int p[96], q[96];
+};
+struct BwdBits {
+  int n;
+  int p[16];
+};
+void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const BwdEdges& internal, const BwdBits& sel,
+                        double* out, cudaStream_t s);
+void launch_bwd_maxcut_grad(const int32_t* rowX, const int32_t* rowY, int kmax, int fX, const BwdEdges& internal,
+                            const BwdBits& bitX, const double* sumsY, int64_t rowsY, double scale, void* dX, int dtype,
+                            cudaStream_t s);
+void launch_bwd_maxcut_loss(const int32_t* rowA, const int32_t* rowB, int kmax, const double* sA, int64_t rowsA,
+                            const double* sB, int64_t rowsB, int nbridge, double scale, double* loss, cudaStream_t s);
+void launch_bwd_cc(const void* Y, const void* G, const int32_t* rowX, const int32_t* rowY, int kmax, int fX, int fY,
+                   const uint64_t* depX, const uint64_t* depY, double scale, void* dX, int dtype, cudaStream_t s);
+void launch_dot(const void* a, const void* b, int64_t n, int dtype, double* out, cudaStream_t s);
+
 // k_sim.cu
 struct SimPlan {
   int d, k_in, k_out, n_eff;

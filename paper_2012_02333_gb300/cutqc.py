@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import List, Optional, Sequence
+from typing import List, Optional, Sequence, Tuple
 
 import torch
 
@@ -234,6 +234,40 @@ def cutqc_reconstruct_fd_noalloc(problem: Problem, out: torch.Tensor, sum_p: Opt
         sp = sum_p.data_ptr()
     _check(_lib.cutqc_reconstruct_fd_noalloc(C.byref(problem.c), C.c_void_p(out.data_ptr()), sp,
                                              _stream_ptr(stream)))
+
+
+def cutqc_reconstruct_backward(problem: Problem, grads: Sequence[torch.Tensor], grad_out: Optional[torch.Tensor] = None,
+                               edges: Optional[Sequence[Tuple[int, int]]] = None,
+                               loss_value: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Binding of cutqc_reconstruct_backward: grads[c] <- dL/dT_c for
+    L = sum_x G(x) p(x), with G = grad_out (2^n entries) or, when `edges` is
+    given, the MaxCut cut count of each bit string generated on the fly.
+    loss_value (CUDA float64, 1 entry) receives L."""
+    if len(grads) != len(problem.tensors):
+        raise ValueError("one gradient per subcircuit")
+    for g, t in zip(grads, problem.tensors):
+        if g.dtype != t.dtype or g.numel() != t.numel() or not g.is_cuda or not g.is_contiguous():
+            raise ValueError("each gradient must be a contiguous CUDA tensor shaped like its tensor")
+    gptr = (C.c_void_p * len(grads))(*[g.data_ptr() for g in grads])
+    loss = None
+    keep = None
+    if edges is not None:
+        flat = [int(q) for e in edges for q in e]
+        keep = _i32(flat)
+        loss = cutqc_loss(CUTQC_LOSS_MAXCUT, len(edges), keep)
+    elif grad_out is None:
+        raise ValueError("need grad_out or edges")
+    if grad_out is not None and (grad_out.dtype != problem.dtype or grad_out.numel() != 2 ** problem.n_qubits):
+        raise ValueError("grad_out must have 2^n entries in the tensors' dtype")
+    lv = None
+    if loss_value is not None:
+        if loss_value.dtype != torch.float64 or not loss_value.is_cuda:
+            raise ValueError("loss_value must be a CUDA float64 tensor")
+        lv = loss_value.data_ptr()
+    _check(_lib.cutqc_reconstruct_backward(C.byref(problem.c),
+                                           C.c_void_p(grad_out.data_ptr()) if grad_out is not None else None,
+                                           C.byref(loss) if loss is not None else None, gptr, lv,
+                                           _stream_ptr(stream)))
 
 
 def cutqc_reconstruct_dd(problem: Problem, roles: Sequence[int], bins: torch.Tensor, topk: int = 0,

@@ -329,3 +329,20 @@ def test_maxcut_expectation_matches_brute_force():
     Ts = at.tensors(cc)
     p = rc.fd_full(cc.subs, Ts, cc.n, cc.n_cuts)
     assert Cx @ p == pytest.approx(Cx @ sv.probabilities(cc.circuit), abs=1e-12)
+
+
+def test_grad_entry_central_differences():
+    """The one-entry gradient used at full size, against central differences
+    of the plain sum for a MaxCut loss."""
+    cc = C.qaoa_2cluster(4, 2)
+    Ts = at.tensors(cc)
+    G = rc.maxcut_values(cc.n, cc.edges)
+    f = rc.maxcut_of(cc.n, cc.edges)
+    h = 1e-6
+    for c, r, x in [(0, 0, 0), (0, 7, 3), (1, 12, 9), (1, 255, 15)]:
+        tp = [T.copy() for T in Ts]
+        tm = [T.copy() for T in Ts]
+        tp[c].reshape(tp[c].shape[0] * tp[c].shape[1], -1)[r, x] += h
+        tm[c].reshape(tm[c].shape[0] * tm[c].shape[1], -1)[r, x] -= h
+        fd = (G @ rc.fd_full(cc.subs, tp, cc.n, cc.n_cuts) - G @ rc.fd_full(cc.subs, tm, cc.n, cc.n_cuts)) / (2 * h)
+        assert rc.grad_entry(cc.subs, Ts, cc.n, cc.n_cuts, c, r, x, f) == pytest.approx(fd, abs=1e-8)
