@@ -145,8 +145,7 @@ struct Step {
   std::vector<uint64_t> depA, depB;   // [ceil(f/8)][256]
   uint64_t out_stride = 0;
   int vecB = 1;
-  std::vector<uint8_t> epi;           // tensor-core epilogue table (final step)
-  size_t off_rows = 0, off_depA = 0, off_depB = 0, off_epi = 0;   // in the plan's device block
+  size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
   size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
   size_t ws_bound = 0, ws_nseg = 0;
 };
@@ -194,13 +193,13 @@ static std::map<int, DeviceState> g_dev;
 static bool g_profile = false;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
 
-static void prof_begin(cudaStream_t s, cudaEvent_t* a) {
+void prof_begin(cudaStream_t s, cudaEvent_t* a) {
   *a = nullptr;
   if (!g_profile) return;
   CUTQC_CUDA(cudaEventCreate(a));
   CUTQC_CUDA(cudaEventRecord(*a, s));
 }
-static void prof_end(cudaStream_t s, cudaEvent_t a) {
+void prof_end(cudaStream_t s, cudaEvent_t a) {
   if (!a) return;
   cudaEvent_t b;
   CUTQC_CUDA(cudaEventCreate(&b));
@@ -296,7 +295,6 @@ static Step make_step(Plan& P, int ia, int ib, int result, const std::vector<int
     int run = 0;
     while (run < fB && run < 2 && vb[run] == (uint64_t(1) << run)) ++run;
     st.vecB = 1 << run;
-    st.epi = tc_epilogue_table(va, vb);
   }
   st.depA = deposit_table(va);
   st.depB = deposit_table(vb);
@@ -378,8 +376,6 @@ static void finalize_plan(Plan& P) {
     off = align_up(off + st.depA.size() * 8);
     st.off_depB = off;
     off = align_up(off + st.depB.size() * 8);
-    st.off_epi = off;
-    off = align_up(off + st.epi.size());
   }
   P.dtab_bytes = std::max<size_t>(off, 256);
   CUTQC_CUDA(cudaMalloc(&P.dtab, P.dtab_bytes));
@@ -388,7 +384,6 @@ static void finalize_plan(Plan& P) {
     std::memcpy(host.data() + st.off_rows, st.rows.data(), st.rows.size() * 4);
     std::memcpy(host.data() + st.off_depA, st.depA.data(), st.depA.size() * 8);
     std::memcpy(host.data() + st.off_depB, st.depB.data(), st.depB.size() * 8);
-    if (!st.epi.empty()) std::memcpy(host.data() + st.off_epi, st.epi.data(), st.epi.size());
   }
   CUTQC_CUDA(cudaMemcpy(P.dtab, host.data(), P.dtab_bytes, cudaMemcpyHostToDevice));
   // workspace layout: merge results, row flags, compacted rows, counts
@@ -610,7 +605,6 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     c.scale = (i + 1 == P.steps.size()) ? std::ldexp(1.0, -P.K) : 1.0;
     c.rowsA = (int)P.nodes[st.a].rows();
     c.rowsB = (int)P.nodes[st.b].rows();
-    c.epi_tab = st.epi.empty() ? nullptr : static_cast<const void*>(static_cast<char*>(P.dtab) + st.off_epi);
   }
   size_t need = P.ws_bytes;
   const bool use_tc_final = tc_algo && tc_supported(cs.back());
@@ -630,27 +624,32 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     return base + P.ws_node[i];
   };
   auto dtab = static_cast<char*>(P.dtab);
-  // row flags of the original operands
+  // row flags and max |.| of each step's operands, both in one launch
   std::vector<int> flagged(P.nodes.size(), 0);
-  auto ensure_flags = [&](int i) {
-    if (flagged[i]) return;
-    const Node& nd = P.nodes[i];
-    launch_row_stats(node_ptr(i), P.dtype, (int)nd.rows(), nd.f(), reinterpret_cast<int32_t*>(base + P.ws_nz[i]),
-                     reinterpret_cast<float*>(base + P.ws_rmax[i]), s);
-    flagged[i] = 1;
+  auto ensure_flags = [&](int ia, int ib) {
+    RowStatsJobs j{};
+    for (int i : {ia, ib}) {
+      if (flagged[i]) continue;
+      flagged[i] = 1;
+      const Node& nd = P.nodes[i];
+      j.t[j.n] = node_ptr(i);
+      j.rows[j.n] = nd.rows();
+      j.cols[j.n] = int64_t(1) << nd.f();
+      j.flags[j.n] = reinterpret_cast<int32_t*>(base + P.ws_nz[i]);
+      j.rmax[j.n] = reinterpret_cast<float*>(base + P.ws_rmax[i]);
+      ++j.n;
+    }
+    if (j.n) launch_row_stats(j, P.dtype, s);
   };
-  if (sum) CUTQC_CUDA(cudaMemsetAsync(sum, 0, sizeof(double), s));
   for (size_t i = 0; i < P.steps.size(); ++i) {
     const Step& st = P.steps[i];
     Contraction& c = cs[i];
-    ensure_flags(st.a);
-    ensure_flags(st.b);
+    ensure_flags(st.a, st.b);
     c.A = node_ptr(st.a);
     c.B = node_ptr(st.b);
     c.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
     c.depA = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
     c.depB = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
-    c.epi_tab = st.epi.empty() ? nullptr : static_cast<const void*>(dtab + st.off_epi);
     c.crow = reinterpret_cast<int32_t*>(base + st.ws_crow);
     c.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
     c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
@@ -668,15 +667,16 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     }
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
     c.sum = final_step ? sum : nullptr;
-    launch_compact(c, s);
-    cudaEvent_t ev = nullptr;
-    if (final_step) prof_begin(s, &ev);
+    c.profile = final_step;
+    if (!(final_step && use_tc_final)) {
+      c.sum_zero = c.sum;
+      launch_compact(c, s);   // the tensor-core path compacts inside its operand preparation
+    }
     if (final_step && use_tc_final)
       launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s);
     else
       launch_cc_gemm(c, s);
     if (final_step) g_last_algo = use_tc_final ? (algo == CUTQC_AUTO ? CUTQC_TC_BF16X3 : algo) : CUTQC_CC;
-    if (final_step) prof_end(s, ev);
   }
   return base + need;
 }

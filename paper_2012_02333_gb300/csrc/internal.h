@@ -24,6 +24,11 @@ void check_cuda(cudaError_t e, const char* what);
 
 void count_launch(int n = 1);
 
+// cutqc_profile: bracket one launch of a main-contraction kernel with events
+// recorded on its stream (no-ops while profiling is off)
+void prof_begin(cudaStream_t s, cudaEvent_t* ev);
+void prof_end(cudaStream_t s, cudaEvent_t ev);
+
 // Runs `f` under the library lock, converting errors to a status and the
 // thread's last-error message (the body of every C entry point).
 int run_guarded(void (*f)(void*), void* ctx);
@@ -75,12 +80,21 @@ struct Contraction {
   // if non-zero, else 3 when split_err3 * S <= split_tol, otherwise 6.
   double* bound = nullptr;
   int32_t* nseg = nullptr;
-  const void* epi_tab = nullptr;   // device tensor-core epilogue table (final step)
+  bool profile = false;            // bracket the contraction kernel for cutqc_profile
+  double* sum_zero = nullptr;      // device double the compaction zeroes before the contraction adds to it
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
 };
 
 // k_cc.cu
+struct RowStatsJobs {   // up to two tensors whose rows get non-zero flags and max |.|
+  int n;
+  const void* t[2];
+  int64_t rows[2], cols[2];
+  int32_t* flags[2];
+  float* rmax[2];
+};
+void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s);
 void launch_row_stats(const void* T, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s);
 void launch_compact(const Contraction& c, cudaStream_t s);
 void launch_cc_gemm(const Contraction& c, cudaStream_t s);
@@ -90,10 +104,7 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 bool tc_supported(const Contraction& c);
 void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s);
 size_t tc_workspace_bytes(const Contraction& c);
-// Epilogue table of the tensor-core path for a final step whose index bits
-// map to output bit values va (M side) and vb (N side), least significant
-// index bit first.  Empty when the shape cannot use it.
-std::vector<uint8_t> tc_epilogue_table(const std::vector<uint64_t>& va, const std::vector<uint64_t>& vb);
+
 
 // k_dd.cu
 struct DdEvalSub {

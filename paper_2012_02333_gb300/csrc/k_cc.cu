@@ -11,6 +11,8 @@
 // in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace cutqc {
@@ -29,10 +31,8 @@ __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, in
 
 // ---- row statistics (one block per row): non-zero flag and max |entry| ----
 template <typename T>
-__global__ void k_row_stats(const T* __restrict__ t, int64_t cols, int32_t* __restrict__ flags,
-                            float* __restrict__ rmax) {
+__device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64_t cols, int32_t* flag, float* rmax) {
   __shared__ float red[32];
-  const T* row = t + (int64_t)blockIdx.x * cols;
   float m = 0.0f;
   int nz = 0;
   for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) {
@@ -46,9 +46,22 @@ __global__ void k_row_stats(const T* __restrict__ t, int64_t cols, int32_t* __re
   nz = __syncthreads_or(nz);
   if (threadIdx.x == 0) {
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
-    flags[blockIdx.x] = nz;
-    rmax[blockIdx.x] = m;
+    *flag = nz;
+    *rmax = m;
   }
+}
+
+// one block per row of up to two tensors: row 0 .. rows0-1 of job 0, then job 1
+template <typename T>
+__global__ void k_row_stats(RowStatsJobs jobs) {
+  int j = 0;
+  int64_t r = blockIdx.x;
+  if (r >= jobs.rows[0]) {
+    r -= jobs.rows[0];
+    j = 1;
+  }
+  const T* t = static_cast<const T*>(jobs.t[j]);
+  row_stats_block<T>(t + r * jobs.cols[j], jobs.cols[j], jobs.flags[j] + r, jobs.rmax[j] + r);
 }
 
 // ---- stable compaction of the inner index (one block per batch) ----------
@@ -56,7 +69,8 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
                           const int32_t* __restrict__ nzB, int32_t* __restrict__ crow,
                           int32_t* __restrict__ kcount, const float* __restrict__ rmaxA,
                           const float* __restrict__ rmaxB, double scale, double* __restrict__ bound,
-                          int32_t* __restrict__ nseg, int nseg_fixed, double split_tol) {
+                          int32_t* __restrict__ nseg, int nseg_fixed, double split_tol,
+                          double* __restrict__ sum_zero) {
   __shared__ int warp_tot[32];
   __shared__ double warp_s[32];
   __shared__ int base;
@@ -102,6 +116,7 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
     __syncthreads();
   }
   if (threadIdx.x == 0) {
+    if (sum_zero && b == 0) *sum_zero = 0.0;
     kcount[b] = base;
     if (bound) {
       double S = 0.0;
@@ -332,22 +347,39 @@ void launch_typed(const Contraction& c, cudaStream_t s) {
   const int64_t tilesM = (a.M + BM - 1) / BM;
   a.tilesN = (a.N + BN - 1) / BN;
   dim3 grid((unsigned)(tilesM * a.tilesN), (unsigned)c.batch);
+  cudaEvent_t ev = nullptr;
+  if (c.profile) prof_begin(s, &ev);
   k_cc_gemm<T, BM, BN, BK><<<grid, 256, 0, s>>>(a);
   count_launch();
   check_launch("k_cc_gemm");
+  if (c.profile) prof_end(s, ev);
 }
 
 }  // namespace
 
-void launch_row_stats(const void* T_, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s) {
-  const int64_t cols = int64_t(1) << f;
-  const int threads = cols >= 256 ? 256 : 32;
+void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s) {
+  const int64_t blocks = jobs.rows[0] + (jobs.n > 1 ? jobs.rows[1] : 0);
+  RowStatsJobs j = jobs;
+  if (j.n < 2) j.rows[1] = 0;
+  const int64_t cmax = std::max(j.cols[0], j.n > 1 ? j.cols[1] : int64_t(0));
+  const int threads = cmax >= 256 ? 256 : 32;
   if (dtype == CUTQC_F64)
-    k_row_stats<double><<<rows, threads, 0, s>>>(static_cast<const double*>(T_), cols, flags, rmax);
+    k_row_stats<double><<<(unsigned)blocks, threads, 0, s>>>(j);
   else
-    k_row_stats<float><<<rows, threads, 0, s>>>(static_cast<const float*>(T_), cols, flags, rmax);
+    k_row_stats<float><<<(unsigned)blocks, threads, 0, s>>>(j);
   count_launch();
   check_launch("k_row_stats");
+}
+
+void launch_row_stats(const void* T_, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s) {
+  RowStatsJobs j{};
+  j.n = 1;
+  j.t[0] = T_;
+  j.rows[0] = rows;
+  j.cols[0] = int64_t(1) << f;
+  j.flags[0] = flags;
+  j.rmax[0] = rmax;
+  launch_row_stats(j, dtype, s);
 }
 
 void launch_compact(const Contraction& c, cudaStream_t s) {
@@ -355,7 +387,7 @@ void launch_compact(const Contraction& c, cudaStream_t s) {
   while (threads < c.kmax && threads < 1024) threads *= 2;
   if (c.bound && c.batch != 1) fail(CUTQC_ERR_UNSUPPORTED, "split-precision bound needs batch 1");
   k_compact<<<c.batch, threads, 0, s>>>(c.rows, c.kmax, c.nzA, c.nzB, c.crow, c.kcount, c.rmaxA, c.rmaxB,
-                                        c.scale, c.bound, c.nseg, c.nseg_fixed, c.split_tol);
+                                        c.scale, c.bound, c.nseg, c.nseg_fixed, c.split_tol, c.sum_zero);
   count_launch();
   check_launch("k_compact");
 }

@@ -11,19 +11,22 @@
 // the number of segments is read on the device (chosen by the compaction
 // kernel from an a-priori bound) so no host round trip is needed.
 //
-// k_prep_split (operand preparation): gathers the compacted rows (terms whose
-// factor rows are all zero were dropped: early termination, Sec. 4.2),
-// transposes them to K-major through shared memory and writes the splits.
+// k_prep (operand preparation, both operands in one launch): finds the
+// non-zero Kronecker terms (early termination, Sec. 4.2) and the split count,
+// gathers the kept rows, transposes them to K-major through shared memory and
+// writes the splits.
 //
 // k_tc_gemm: persistent, one CTA per SM, 192 threads:
 //   warp 0     TMA producer: 128x64 A tiles and 256x64 B tiles (128-byte
 //              swizzle) into a 4-stage shared-memory ring;
 //   warp 1     allocates 512 TMEM columns (two 128x256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M=128, N=256, K=16);
-//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes, scale by 2^-K,
-//              deposit (m, n) into the output index, 16-byte stores, FP64
-//              partial sums; it drains one accumulator while the MMA fills
-//              the other.
+//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes (lane = row),
+//              scale by 2^-K, deposit (m, n) into the output index with the
+//              additive per-bit tables held in registers, 16-byte streaming
+//              stores (runs of consecutive columns that are consecutive in
+//              the output), FP64 partial sums; it drains one accumulator
+//              while the MMA fills the other.
 // Every wait on an mbarrier is bounded (2 s); on timeout the kernel raises an
 // abort flag, records a status word, lets in-flight copies land and frees TMEM.
 #include <cuda.h>
@@ -49,25 +52,8 @@ constexpr int B_BYTES = BN * BK * 2;          // 32 KiB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 512;
 constexpr int THREADS = 192;
-constexpr int EPI_PITCH = 33;                 // padded row pitch of the epilogue staging buffer
-constexpr int EPI_WARP_BYTES = 32 * EPI_PITCH * 4;
-constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 4 * EPI_WARP_BYTES + 1024 + 256;
-
-// Epilogue staging.  An epilogue warp holds a 32 x 32 chunk (lane = low 5 bits
-// of m, register = low 5 bits of n).  Those 10 index bits land on 10 output
-// bit positions; ordering them by position gives each chunk element a "slot"
-// whose order is the output address order.  The warp writes the chunk to
-// shared memory row by row ([lane][col], pitch 33: conflict-free), then reads
-// it back slot by slot and stores to global memory in address order: runs of
-// 2^contig consecutive floats become coalesced 16-byte stores.  All maps are
-// additive over disjoint bits, so each is a sum of a low and a high table.
-struct EpiTab {
-  int32_t slo[32], shi[32];      // staging offset (floats) of slot bits 0-4 / 5-9
-  uint64_t glo[32], ghi[32];     // output offset of slot bits 0-4 / 5-9
-  int32_t contig;                // slots 0..2^contig-1 are consecutive in memory
-  int32_t pad[3];
-};
-constexpr uint64_t WAIT_NS = 2000000000ull;
+constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------ operand prep
 // Each FP32 x is split into h = bf16(x), m = bf16(x - h), l = bf16(x - h - m).
@@ -77,23 +63,110 @@ constexpr uint64_t WAIT_NS = 2000000000ull;
 __constant__ int kPartA[6] = {0, 0, 1, 0, 2, 1};
 __constant__ int kPartB[6] = {0, 1, 0, 2, 0, 1};
 
-// out[m][seg * Kp + k] = part(T[rowsel[k]][m]) for k < kcount (0 for
-// kcount <= k < Kp), for the first *nseg segments; row pitch 6 * Kp.
-__global__ void __launch_bounds__(256) k_prep_split(const float* __restrict__ T, int64_t cols,
-                                                    const int32_t* __restrict__ rowsel,
-                                                    const int32_t* __restrict__ kcount,
-                                                    const int32_t* __restrict__ nseg_ptr, int Kp, int which,
-                                                    __nv_bfloat16* __restrict__ out) {
+struct PrepArgs {
+  const float* T[2];          // A, B tensors
+  int64_t cols[2];            // 2^fA, 2^fB
+  int blocks0;                // column blocks of A (cols[0] / 64)
+  int Kp, kmax;
+  int fused;                  // compaction done here (kmax <= 4096) or read from crow / kcount / nseg
+  const int32_t* rows;        // [2][kmax] row pairs (fused)
+  const int32_t* crow;        // [2][kmax] compacted row pairs (not fused)
+  const int32_t* nzA;
+  const int32_t* nzB;
+  const float* rmaxA;
+  const float* rmaxB;
+  double scale, split_tol;
+  int nseg_fixed;
+  int32_t* kcount;
+  int32_t* nseg;
+  double* bound;
+  double* sum_zero;
+  __nv_bfloat16* out[2];      // A', B': [cols][6 * Kp]
+};
+
+// out[m][seg * Kp + k] = part(T[row(k)][m]) for the k-th kept term (0 for
+// kcount <= k < Kp), first nseg segments, row pitch 6 * Kp.  One launch for
+// both operands: blocks [0, blocks0) prepare A, the rest B.  When `fused`,
+// every block finds its own compacted rows (a block-wide stable scan of the
+// row pairs: early termination, Sec. 4.2) and the split count from the bound
+// S = scale * sum_kept max|A| max|B|; block (0, 0) publishes the count, the
+// split count and S for the contraction and zeroes the FP64 sum.
+__global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
   __shared__ float s[64][65];
-  const int tid = threadIdx.x;
-  const int64_t m0 = (int64_t)blockIdx.x * 64;
+  __shared__ int32_t rowsel[64];
+  __shared__ int warp_tot[8];
+  __shared__ double warp_s[8];
+  __shared__ int base_s, kc_s, nseg_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int which = blockIdx.x < (unsigned)a.blocks0 ? 0 : 1;
+  const int64_t m0 = (int64_t)(which == 0 ? blockIdx.x : blockIdx.x - a.blocks0) * 64;
   const int k0 = blockIdx.y * 64;
-  const int kc = *kcount;
-  const int nseg = *nseg_ptr;
+  const int64_t cols = a.cols[which];
+  const float* T = a.T[which];
+  if (a.fused) {
+    if (tid == 0) base_s = 0;
+    __syncthreads();
+    double sacc = 0.0;
+    const int32_t* ra = a.rows;
+    const int32_t* rb = a.rows + a.kmax;
+    for (int t0 = 0; t0 < a.kmax; t0 += 256) {
+      const int t = t0 + tid;
+      int keep = 0, r0 = 0, r1 = 0;
+      if (t < a.kmax) {
+        r0 = ra[t];
+        r1 = rb[t];
+        keep = a.nzA[r0] && a.nzB[r1];
+      }
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      if (lane == 0) warp_tot[warp] = __popc(m);
+      __syncthreads();
+      int off = 0, tot = 0;
+      for (int w = 0; w < 8; ++w) {
+        if (w < warp) off += warp_tot[w];
+        tot += warp_tot[w];
+      }
+      if (keep) {
+        const int ci = base_s + off + __popc(m & ((1u << lane) - 1u));
+        if (ci >= k0 && ci < k0 + 64) rowsel[ci - k0] = which == 0 ? r0 : r1;
+        sacc += (double)a.rmaxA[r0] * (double)a.rmaxB[r1];
+      }
+      __syncthreads();
+      if (tid == 0) base_s += tot;
+      __syncthreads();
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+    if (lane == 0) warp_s[warp] = sacc;
+    __syncthreads();
+    if (tid == 0) {
+      double S = 0.0;
+      for (int w = 0; w < 8; ++w) S += warp_s[w];
+      S *= a.scale;
+      // BF16 x3 drops terms of at most ~3 * 2^-18 |a||b| per product
+      const int ns = a.nseg_fixed ? a.nseg_fixed : (3.0 * 3.814697265625e-06 * S <= a.split_tol ? 3 : 6);
+      kc_s = base_s;
+      nseg_s = ns;
+      if (blockIdx.x == 0 && blockIdx.y == 0) {
+        *a.kcount = base_s;
+        *a.nseg = ns;
+        *a.bound = S;
+        if (a.sum_zero) *a.sum_zero = 0.0;
+      }
+    }
+  } else {
+    if (tid == 0) {
+      kc_s = *a.kcount;
+      nseg_s = *a.nseg;
+    }
+    __syncthreads();
+    if (tid < 64 && k0 + tid < kc_s) rowsel[tid] = a.crow[which * a.kmax + k0 + tid];
+  }
+  __syncthreads();
+  const int kc = kc_s, nseg = nseg_s;
 #pragma unroll
   for (int i = 0; i < 16; ++i) {
     const int kk = i * 4 + tid / 64, mm = tid % 64, k = k0 + kk;
-    s[kk][mm] = (k < kc) ? T[(int64_t)rowsel[k] * cols + m0 + mm] : 0.0f;
+    s[kk][mm] = (k < kc) ? T[(int64_t)rowsel[kk] * cols + m0 + mm] : 0.0f;
   }
   __syncthreads();
   const int ml = tid / 4, kq = (tid % 4) * 16;
@@ -109,11 +182,12 @@ __global__ void __launch_bounds__(256) k_prep_split(const float* __restrict__ T,
     part[1][j] = mid;
     part[2][j] = __float2bfloat16_rn(r2);
   }
-  const int64_t row = (m0 + ml) * (int64_t)(6 * Kp);
+  __nv_bfloat16* out = a.out[which];
+  const int64_t row = (m0 + ml) * (int64_t)(6 * a.Kp);
   for (int seg = 0; seg < nseg; ++seg) {
     const int pi = which == 0 ? kPartA[seg] : kPartB[seg];
     const uint4* src = reinterpret_cast<const uint4*>(part[pi]);
-    uint4* dst = reinterpret_cast<uint4*>(out + row + (int64_t)seg * Kp + k0 + kq);
+    uint4* dst = reinterpret_cast<uint4*>(out + row + (int64_t)seg * a.Kp + k0 + kq);
     dst[0] = src[0];
     dst[1] = src[1];
   }
@@ -147,16 +221,20 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// bounded wait: false on timeout or when another role has aborted
+// bounded wait: false on timeout (about 2 s of SM clock) or when another role
+// has aborted; the clock and the abort flag are looked at every 1024 polls so
+// the poll loop itself stays short
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   if (mbar_try(bar, parity)) return true;
-  const uint64_t t0 = gtimer();
-  while (true) {
+  const long long t0 = clock64();
+  for (uint32_t i = 1;; ++i) {
     if (mbar_try(bar, parity)) return true;
-    if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_NS) {
-      *abort_flag = 1;
-      return false;
+    if ((i & 1023) == 0) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > WAIT_CYCLES) {
+        *abort_flag = 1;
+        return false;
+      }
     }
   }
 }
@@ -225,7 +303,6 @@ struct TcArgs {
   float scale;
   double* sum;
   int vecB;
-  const void* epi;
   int* status;
 };
 
@@ -328,36 +405,29 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 2) {
-    // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. +31
+    // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. +31; lane = row
     const int q = warp & 3;
-    float* stage_buf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES + 256) + (warp - 2) * (32 * EPI_PITCH);
-    const EpiTab* et = static_cast<const EpiTab*>(a.epi);
     double local = 0.0;
-    // per-thread constants of the read-back: slots 4*lane + t (t < 4) of each
-    // 128-slot pass it (< 8): staging offset slo[(4l+t)&31] + shi[4it + l/8]
-    int32_t rs_lo[4];
-    uint64_t rg_lo[4];
+    // the deposit is additive over disjoint index bits, so a row's output
+    // address is dep(row base) + dep(lane) + dep(chunk column base) +
+    // dep(column within the chunk); the per-thread parts live in registers
+    const uint64_t dep_lane = deposit(a.depA, 1, (uint64_t)lane);
+    uint64_t dlow[8], dcol[8], dtiny[4];
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      rs_lo[t] = et->slo[(4 * lane + t) & 31];
-      rg_lo[t] = et->glo[(4 * lane + t) & 31];
+    for (int j = 0; j < 8; ++j) {
+      dlow[j] = deposit(a.depB, 1, (uint64_t)(4 * j));    // n bits 2-4
+      dcol[j] = deposit(a.depB, 1, (uint64_t)(32 * j));   // n bits 5-7: chunk column base
     }
-    int32_t rs_hi[8];
-    uint64_t rg_hi[8], dcol[8];
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      rs_hi[it] = et->shi[4 * it + (lane >> 3)];
-      rg_hi[it] = et->ghi[4 * it + (lane >> 3)];
-      dcol[it] = deposit(a.depB, 1, (uint64_t)(32 * it));   // chunk column base, n bits 5-7
-    }
-    const bool vec = et->contig >= 2;
+    for (int t = 0; t < 4; ++t) dtiny[t] = deposit(a.depB, 1, (uint64_t)t);
+    const bool vec = a.vecB >= 4;
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int tm = tile % a.tilesM, tn = tile / a.tilesM;
-      // chunk base: rows tm*128 + 32q (m bits >= 5), columns tn*256 (n bits >= 8)
-      const uint64_t gT = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) +
-                          deposit(a.depB, a.nbB, (uint64_t)tn * BN);
+      // this thread's row: tm*128 + 32q + lane; columns tn*256 + 32c + j
+      const uint64_t grow = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) + dep_lane +
+                            deposit(a.depB, a.nbB, (uint64_t)tn * BN);
       if (nkb > 0) {
         const bool ok = mbar_wait(&tfull[acc], acc_phase, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -374,37 +444,30 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         // sum of this 32-column row piece: pairwise in FP32 (error <= 5 * 2^-24 *
         // sum |v|), then one FP64 add (the FP64 pipe is narrow on this part)
+        float v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) * a.scale;
         float t16[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j)
-          t16[j] = __uint_as_float(r[2 * j]) * a.scale + __uint_as_float(r[2 * j + 1]) * a.scale;
+        for (int j = 0; j < 16; ++j) t16[j] = v[2 * j] + v[2 * j + 1];
 #pragma unroll
         for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
           for (int j = 0; j < w; ++j) t16[j] += t16[j + w];
         local += (double)t16[0];
-        __syncwarp();
-#pragma unroll
-        for (int j = 0; j < 32; ++j) stage_buf[lane * EPI_PITCH + j] = __uint_as_float(r[j]) * a.scale;
-        __syncwarp();
         uint64_t dc = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
-        float* obase = a.out + gT + dc;
+        float* orow = a.out + grow + dc;
+        if (vec) {
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-          const int32_t sh = rs_hi[it];
-          const uint64_t gh = rg_hi[it];
-          const float v0 = stage_buf[rs_lo[0] + sh], v1 = stage_buf[rs_lo[1] + sh];
-          const float v2 = stage_buf[rs_lo[2] + sh], v3 = stage_buf[rs_lo[3] + sh];
-          if (vec) {
-            __stcs(reinterpret_cast<float4*>(obase + gh + rg_lo[0]), make_float4(v0, v1, v2, v3));
-          } else {
-            obase[gh + rg_lo[0]] = v0;
-            obase[gh + rg_lo[1]] = v1;
-            obase[gh + rg_lo[2]] = v2;
-            obase[gh + rg_lo[3]] = v3;
-          }
+          for (int j = 0; j < 8; ++j)
+            __stcs(reinterpret_cast<float4*>(orow + dlow[j]), make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) orow[dlow[j] + dtiny[t]] = v[4 * j + t];
         }
       }
       if (nkb > 0) {
@@ -477,38 +540,7 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 }  // namespace
 
 bool tc_supported(const Contraction& c) {
-  return c.dtype == CUTQC_F32 && c.batch == 1 && c.fA >= 7 && c.fB >= 8 && c.kmax >= 1 && c.epi_tab;
-}
-
-std::vector<uint8_t> tc_epilogue_table(const std::vector<uint64_t>& va, const std::vector<uint64_t>& vb) {
-  std::vector<uint8_t> bytes;
-  if (va.size() < 5 || vb.size() < 5) return bytes;
-  // the 10 chunk index bits: lane bits (m bits 0-4) and column bits (n bits 0-4)
-  struct Bit {
-    uint64_t value;
-    int32_t stage;
-  };
-  std::vector<Bit> bits;
-  for (int b = 0; b < 5; ++b) bits.push_back({va[b], (int32_t)(EPI_PITCH << b)});
-  for (int b = 0; b < 5; ++b) bits.push_back({vb[b], (int32_t)(1 << b)});
-  std::sort(bits.begin(), bits.end(), [](const Bit& x, const Bit& y) { return x.value < y.value; });
-  EpiTab t{};
-  for (int i = 0; i < 32; ++i) {
-    for (int k = 0; k < 5; ++k) {
-      if ((i >> k) & 1) {
-        t.slo[i] += bits[k].stage;
-        t.shi[i] += bits[5 + k].stage;
-        t.glo[i] += bits[k].value;
-        t.ghi[i] += bits[5 + k].value;
-      }
-    }
-  }
-  int j = 0;
-  while (j < 10 && bits[j].value == (uint64_t(1) << j)) ++j;
-  t.contig = j;
-  bytes.resize(sizeof(EpiTab));
-  std::memcpy(bytes.data(), &t, sizeof(EpiTab));
-  return bytes;
+  return c.dtype == CUTQC_F32 && c.batch == 1 && c.fA >= 7 && c.fB >= 8 && c.kmax >= 1;
 }
 
 size_t tc_workspace_bytes(const Contraction& c) {
@@ -526,15 +558,39 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   auto* Ab = reinterpret_cast<__nv_bfloat16*>(w);
   auto* Bb = reinterpret_cast<__nv_bfloat16*>(w + align256((size_t)M * 6 * Kp * 2));
   int* status = reinterpret_cast<int*>(w + align256((size_t)M * 6 * Kp * 2) + align256((size_t)N * 6 * Kp * 2));
-  if (!c.nseg) fail(CUTQC_ERR_ARG, "tensor-core path needs the split count");
-  k_prep_split<<<dim3((unsigned)(M / 64), (unsigned)(Kp / 64)), 256, 0, s>>>(
-      static_cast<const float*>(c.A), M, c.crow, c.kcount, c.nseg, Kp, 0, Ab);
+  if (!c.nseg || !c.bound) fail(CUTQC_ERR_ARG, "tensor-core path needs the split count");
+  PrepArgs pa{};
+  pa.T[0] = static_cast<const float*>(c.A);
+  pa.T[1] = static_cast<const float*>(c.B);
+  pa.cols[0] = M;
+  pa.cols[1] = N;
+  pa.blocks0 = (int)(M / 64);
+  pa.Kp = Kp;
+  pa.kmax = c.kmax;
+  pa.fused = c.kmax <= 4096;
+  pa.rows = c.rows;
+  pa.crow = c.crow;
+  pa.nzA = c.nzA;
+  pa.nzB = c.nzB;
+  pa.rmaxA = c.rmaxA;
+  pa.rmaxB = c.rmaxB;
+  pa.scale = c.scale;
+  pa.split_tol = c.split_tol;
+  pa.nseg_fixed = c.nseg_fixed;
+  pa.kcount = c.kcount;
+  pa.nseg = c.nseg;
+  pa.bound = c.bound;
+  pa.sum_zero = c.sum;
+  pa.out[0] = Ab;
+  pa.out[1] = Bb;
+  if (!pa.fused) {
+    Contraction cc = c;
+    cc.sum_zero = c.sum;
+    launch_compact(cc, s);
+  }
+  k_prep<<<dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), 256, 0, s>>>(pa);
   count_launch();
-  check_launch("k_prep_split(A)");
-  k_prep_split<<<dim3((unsigned)(N / 64), (unsigned)(Kp / 64)), 256, 0, s>>>(
-      static_cast<const float*>(c.B), N, c.crow + c.kmax, c.kcount, c.nseg, Kp, 1, Bb);
-  count_launch();
-  check_launch("k_prep_split(B)");
+  check_launch("k_prep");
 
   const CUtensorMap tmA = make_map(Ab, (uint64_t)M, (uint64_t)6 * Kp, BM);
   const CUtensorMap tmB = make_map(Bb, (uint64_t)N, (uint64_t)6 * Kp, BN);
@@ -552,7 +608,6 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   a.scale = (float)c.scale;
   a.sum = c.sum;
   a.vecB = c.vecB;
-  a.epi = c.epi_tab;
   a.status = status;
   static int sms = 0;
   static bool attr = false;
@@ -565,9 +620,12 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   }
   const int tiles = a.tilesM * a.tilesN;
   const int grid = tiles < sms ? tiles : sms;
+  cudaEvent_t ev = nullptr;
+  if (c.profile) prof_begin(s, &ev);
   k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(tmA, tmB, a);
   count_launch();
   check_launch("k_tc_gemm");
+  if (c.profile) prof_end(s, ev);
 }
 
 }  // namespace cutqc
