@@ -4,12 +4,12 @@
 // A[e][m] B[e][n], runs on the 5th-generation tensor cores.  Each FP32
 // operand x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi), and
 //   A.B ~= A_hi.B_hi + A_hi.B_lo + A_lo.B_hi
-// (the lo.lo term is ~2^-16 relative).  The three products are one GEMM over a
-// concatenated inner dimension: A' = [A_hi | A_hi | A_lo] and
-// B' = [B_hi | B_lo | B_hi], both stored K-major in bf16.  The x6 form splits
-// into three pieces and appends hl, lh and mm segments (FP32-level accuracy);
-// the number of segments is read on the device (chosen by the compaction
-// kernel from an a-priori bound) so no host round trip is needed.
+// (the lo.lo term is ~2^-16 relative).  The pieces are stored K-major in
+// bf16 and each pipeline stage holds every piece of one 32-wide k step, so
+// one stage feeds all the products (hh, hm, mh; the x6 form splits into three
+// pieces and adds hl, lh, mm for FP32-level accuracy).  The number of
+// products is read on the device (chosen from an a-priori bound while the
+// operands are prepared) so no host round trip is needed.
 //
 // k_prep (operand preparation, both operands in one launch): finds the
 // non-zero Kronecker terms (early termination, Sec. 4.2) and the split count,
@@ -17,8 +17,9 @@
 // writes the splits.
 //
 // k_tc_gemm: persistent, one CTA per SM, 192 threads:
-//   warp 0     TMA producer: 128x64 A tiles and 256x64 B tiles (128-byte
-//              swizzle) into a 4-stage shared-memory ring;
+//   warp 0     TMA producer: the split pieces of 128x32 A tiles and 256x32
+//              B tiles (64-byte swizzle) into a 4-stage (x3) or 3-stage (x6)
+//              shared-memory ring;
 //   warp 1     allocates 512 TMEM columns (two 128x256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M=128, N=256, K=16);
 //   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes (lane = row),
@@ -45,14 +46,16 @@ namespace cutqc {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BK = 64;   // BK bf16 = 128 bytes = one swizzle row
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;          // 16 KiB
-constexpr int B_BYTES = BN * BK * 2;          // 32 KiB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int BM = 128, BN = 256;
+constexpr int BK = 64;                        // operand preparation works in 64-wide k blocks
+constexpr int KS = 32;                        // one pipeline stage: 32 k = 64 bytes = one 64-byte swizzle row
+constexpr int A_PIECE = BM * KS * 2;          // 8 KiB per split piece of A
+constexpr int B_PIECE = BN * KS * 2;          // 16 KiB per split piece of B
+constexpr int MAX_STAGES = 4;
+constexpr int STAGE_AREA = 3 * 3 * (A_PIECE + B_PIECE);   // 216 KiB: 3 stages of 3 pieces or 4 of 2
 constexpr int TMEM_COLS = 512;
 constexpr int THREADS = 192;
-constexpr size_t SMEM_BYTES = size_t(STAGES) * STAGE_BYTES + 1024 + 256;
+constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256;
 constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------ operand prep
@@ -81,11 +84,12 @@ struct PrepArgs {
   int32_t* nseg;
   double* bound;
   double* sum_zero;
-  __nv_bfloat16* out[2];      // A', B': [cols][6 * Kp]
+  __nv_bfloat16* out[2];      // A', B': [piece][cols][Kp]
 };
 
-// out[m][seg * Kp + k] = part(T[row(k)][m]) for the k-th kept term (0 for
-// kcount <= k < Kp), first nseg segments, row pitch 6 * Kp.  One launch for
+// out[piece][m][k] = piece of T[row(k)][m] for the k-th kept term (0 for
+// kcount <= k < Kp): pieces h and m for the x3 form, h, m and l for x6; each
+// piece K-major with row pitch Kp.  One launch for
 // both operands: blocks [0, blocks0) prepare A, the rest B.  When `fused`,
 // every block finds its own compacted rows (a block-wide stable scan of the
 // row pairs: early termination, Sec. 4.2) and the split count from the bound
@@ -183,11 +187,10 @@ __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
     part[2][j] = __float2bfloat16_rn(r2);
   }
   __nv_bfloat16* out = a.out[which];
-  const int64_t row = (m0 + ml) * (int64_t)(6 * a.Kp);
-  for (int seg = 0; seg < nseg; ++seg) {
-    const int pi = which == 0 ? kPartA[seg] : kPartB[seg];
-    const uint4* src = reinterpret_cast<const uint4*>(part[pi]);
-    uint4* dst = reinterpret_cast<uint4*>(out + row + (int64_t)seg * a.Kp + k0 + kq);
+  const int npieces = nseg == 3 ? 2 : 3;
+  for (int pc = 0; pc < npieces; ++pc) {
+    const uint4* src = reinterpret_cast<const uint4*>(part[pc]);
+    uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)pc * cols + m0 + ml) * a.Kp + k0 + kq);
     dst[0] = src[0];
     dst[1] = src[1];
   }
@@ -244,15 +247,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart
-__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+// shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16),
+// 8-row groups 512 bytes apart
+__device__ __forceinline__ uint64_t sw64_desc(const void* p) {
   const uint32_t a = smem_u32(p);
   uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;                  // leading byte offset (unused by swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)(512 >> 4) << 32;         // stride byte offset
   d |= (uint64_t)1 << 46;                  // descriptor version
-  d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+  d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
   return d;
 }
 // instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major
@@ -293,6 +296,7 @@ __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, in
 
 struct TcArgs {
   int Kp;
+  int M, N;                   // rows of one piece of A' / B' (the piece offset of the TMA row coordinate)
   const int32_t* kcount;
   const int32_t* nseg;
   int tilesM, tilesN;
@@ -310,18 +314,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* sA = smem;
-  uint8_t* sB = smem + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);   // 256 bytes of barriers
-  uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGE_AREA);   // 256 bytes of barriers
+  uint64_t* empty = full + MAX_STAGES;
+  uint64_t* tfull = empty + MAX_STAGES;
   uint64_t* tempty = tfull + 2;
   uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tempty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int i = 0; i < STAGES; ++i) {
+    for (int i = 0; i < MAX_STAGES; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
     }
@@ -345,31 +347,42 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t tmem_base = *tmem_holder;
 
   const int kc = *a.kcount;
-  const int nkb = (kc + BK - 1) / BK;
-  const int total_kb = *a.nseg * nkb;
+  const int nseg = *a.nseg;
+  const int npieces = nseg == 3 ? 2 : 3;                    // h, m (x3) or h, m, l (x6)
+  const int stages = nseg == 3 ? 4 : 3;
+  const uint32_t stage_bytes = (uint32_t)npieces * (A_PIECE + B_PIECE);
+  const int nkb = (kc + KS - 1) / KS;                       // 32-wide k steps
   const int ntiles = a.tilesM * a.tilesN;
 
-  if (nkb > 0 && warp == 0 && lane == 0) {
-    // ---- TMA producer
+  if (nkb > 0 && warp == 0) {
+    // ---- TMA producer (the warp waits, lane 0 issues): every split piece of
+    // a 32-wide k step of A (128 rows) and B (256 rows) into one stage
     int stage = 0;
     uint32_t phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
       const int tm = tile % a.tilesM, tn = tile / a.tilesM;
-      for (int kb = 0; kb < total_kb; ++kb) {
-        const int seg = kb / nkb, kk = kb % nkb;
-        const int x = seg * a.Kp + kk * BK;
-        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag)) break;
-        mbar_expect_tx(&full[stage], STAGE_BYTES);
-        tma_load_2d(sA + stage * A_BYTES, &tmA, x, tm * BM, &full[stage]);
-        tma_load_2d(sB + stage * B_BYTES, &tmB, x, tn * BN, &full[stage]);
-        if (++stage == STAGES) {
+      for (int kb = 0; kb < nkb; ++kb) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&empty[stage], phase ^ 1, abort_flag));
+        if (!ok) break;
+        if (lane == 0) {
+          uint8_t* st = smem + stage * stage_bytes;
+          mbar_expect_tx(&full[stage], stage_bytes);
+          for (int pc = 0; pc < npieces; ++pc) {
+            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KS, pc * a.M + tm * BM, &full[stage]);
+            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, &tmB, kb * KS, pc * a.N + tn * BN, &full[stage]);
+          }
+        }
+        __syncwarp();
+        if (++stage == stages) {
           stage = 0;
           phase ^= 1;
         }
       }
     }
-  } else if (nkb > 0 && warp == 1 && lane == 0) {
-    // ---- MMA issuer
+  } else if (nkb > 0 && warp == 1) {
+    // ---- MMA issuer (the warp waits, lane 0 issues): per stage the nseg
+    // products hh, hm, mh (, hl, lh, mm), two K=16 MMAs each
     const uint32_t idesc = idesc_bf16(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
@@ -377,28 +390,34 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag)) break;
+      ok = __all_sync(0xffffffffu, mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag));
+      if (!ok) break;
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + acc * BN;
-      for (int kb = 0; kb < total_kb; ++kb) {
-        if (!mbar_wait(&full[stage], phase, abort_flag)) {
-          ok = false;
-          break;
-        }
+      for (int kb = 0; kb < nkb; ++kb) {
+        ok = __all_sync(0xffffffffu, mbar_wait(&full[stage], phase, abort_flag));
+        if (!ok) break;
         tc_fence_after();
-        const uint64_t ad = sw128_desc(sA + stage * A_BYTES);
-        const uint64_t bd = sw128_desc(sB + stage * B_BYTES);
+        if (lane == 0) {
+          uint8_t* st = smem + stage * stage_bytes;
+          for (int sg = 0; sg < nseg; ++sg) {
+            const uint64_t ad = sw64_desc(st + kPartA[sg] * A_PIECE);
+            const uint64_t bd = sw64_desc(st + npieces * A_PIECE + kPartB[sg] * B_PIECE);
 #pragma unroll
-        for (int k = 0; k < BK / 16; ++k)
-          mma_bf16(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-        mma_commit(&empty[stage]);
-        if (++stage == STAGES) {
+            for (int k = 0; k < KS / 16; ++k)
+              mma_bf16(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(&empty[stage]);
+        }
+        __syncwarp();
+        if (++stage == stages) {
           stage = 0;
           phase ^= 1;
         }
       }
       if (!ok) break;
-      mma_commit(&tfull[acc]);
+      if (lane == 0) mma_commit(&tfull[acc]);
+      __syncwarp();
       if (++acc == 2) {
         acc = 0;
         acc_phase ^= 1;
@@ -524,10 +543,10 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t inner, uint32_t b
   CUtensorMap m;
   const cuuint64_t dims[2] = {inner, rows};
   const cuuint64_t strides[1] = {inner * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)BK, box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)KS, box_rows};
   const cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
-                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) fail(CUTQC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -546,7 +565,7 @@ bool tc_supported(const Contraction& c) {
 size_t tc_workspace_bytes(const Contraction& c) {
   const size_t Kp = kpad(c);
   const size_t M = size_t(1) << c.fA, N = size_t(1) << c.fB;
-  return align256(M * 6 * Kp * 2) + align256(N * 6 * Kp * 2) + 256;
+  return align256(M * 3 * Kp * 2) + align256(N * 3 * Kp * 2) + 256;
 }
 
 void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s) {
@@ -556,8 +575,8 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   const int64_t M = int64_t(1) << c.fA, N = int64_t(1) << c.fB;
   char* w = static_cast<char*>(ws);
   auto* Ab = reinterpret_cast<__nv_bfloat16*>(w);
-  auto* Bb = reinterpret_cast<__nv_bfloat16*>(w + align256((size_t)M * 6 * Kp * 2));
-  int* status = reinterpret_cast<int*>(w + align256((size_t)M * 6 * Kp * 2) + align256((size_t)N * 6 * Kp * 2));
+  auto* Bb = reinterpret_cast<__nv_bfloat16*>(w + align256((size_t)M * 3 * Kp * 2));
+  int* status = reinterpret_cast<int*>(w + align256((size_t)M * 3 * Kp * 2) + align256((size_t)N * 3 * Kp * 2));
   if (!c.nseg || !c.bound) fail(CUTQC_ERR_ARG, "tensor-core path needs the split count");
   PrepArgs pa{};
   pa.T[0] = static_cast<const float*>(c.A);
@@ -592,10 +611,13 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   count_launch();
   check_launch("k_prep");
 
-  const CUtensorMap tmA = make_map(Ab, (uint64_t)M, (uint64_t)6 * Kp, BM);
-  const CUtensorMap tmB = make_map(Bb, (uint64_t)N, (uint64_t)6 * Kp, BN);
+  // three pieces of each operand stacked along rows: [piece * rows + row][k]
+  const CUtensorMap tmA = make_map(Ab, (uint64_t)M * 3, (uint64_t)Kp, BM);
+  const CUtensorMap tmB = make_map(Bb, (uint64_t)N * 3, (uint64_t)Kp, BN);
   TcArgs a;
   a.Kp = Kp;
+  a.M = (int)M;
+  a.N = (int)N;
   a.kcount = c.kcount;
   a.nseg = c.nseg;
   a.tilesM = (int)(M / BM);
