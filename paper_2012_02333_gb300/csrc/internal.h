@@ -24,6 +24,27 @@ void check_cuda(cudaError_t e, const char* what);
 
 void count_launch(int n = 1);
 
+// Programmatic dependent launch: the kernel may start while the previous
+// kernel on the stream finishes; it must execute grid_dep_wait() before it
+// reads anything that kernel wrote.  grid_dep_launch() lets the next
+// programmatically launched kernel start early.
+#define CUTQC_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define CUTQC_PDL_LAUNCH() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+template <typename Kernel, typename... Args>
+inline cudaError_t launch_pdl(Kernel k, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 // cutqc_profile: bracket one launch of a main-contraction kernel with events
 // recorded on its stream (no-ops while profiling is off)
 void prof_begin(cudaStream_t s, cudaEvent_t* ev);

@@ -35,10 +35,19 @@ __device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64
   __shared__ float red[32];
   float m = 0.0f;
   int nz = 0;
-  for (int64_t i = threadIdx.x; i < cols; i += blockDim.x) {
-    const T v = row[i];
-    nz |= (v != T(0));
-    m = fmaxf(m, (float)fabs((double)v));
+  constexpr int U = 4;   // independent loads in flight per thread
+  for (int64_t i0 = threadIdx.x; i0 < cols; i0 += (int64_t)blockDim.x * U) {
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      v[u] = i < cols ? row[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      nz |= (v[u] != T(0));
+      m = fmaxf(m, (float)fabs((double)v[u]));
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -54,6 +63,7 @@ __device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64
 // one block per row of up to two tensors: row 0 .. rows0-1 of job 0, then job 1
 template <typename T>
 __global__ void k_row_stats(RowStatsJobs jobs) {
+  CUTQC_PDL_LAUNCH();   // the operand preparation may launch and wait on this grid
   int j = 0;
   int64_t r = blockIdx.x;
   if (r >= jobs.rows[0]) {

@@ -96,6 +96,8 @@ struct PrepArgs {
 // S = scale * sum_kept max|A| max|B|; block (0, 0) publishes the count, the
 // split count and S for the contraction and zeroes the FP64 sum.
 __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
+  CUTQC_PDL_WAIT();     // row statistics come from the previous kernel
+  CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
   __shared__ float s[64][65];
   __shared__ int32_t rowsel[64];
   __shared__ int warp_tot[8];
@@ -345,6 +347,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_holder;
+  // everything above overlapped the operand preparation; what follows reads it
+  CUTQC_PDL_WAIT();
 
   const int kc = *a.kcount;
   const int nseg = *a.nseg;
@@ -607,7 +611,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
     cc.sum_zero = c.sum;
     launch_compact(cc, s);
   }
-  k_prep<<<dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), 256, 0, s>>>(pa);
+  CUTQC_CUDA(launch_pdl(k_prep, dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), dim3(256), 0, s, pa));
   count_launch();
   check_launch("k_prep");
 
@@ -644,7 +648,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   const int grid = tiles < sms ? tiles : sms;
   cudaEvent_t ev = nullptr;
   if (c.profile) prof_begin(s, &ev);
-  k_tc_gemm<<<grid, THREADS, SMEM_BYTES, s>>>(tmA, tmB, a);
+  CUTQC_CUDA(launch_pdl(k_tc_gemm, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
   count_launch();
   check_launch("k_tc_gemm");
   if (c.profile) prof_end(s, ev);
