@@ -103,3 +103,38 @@ def test_dd_twin_of_80_qubit_workload(env):
     recursions, BFS, FP32 tensors."""
     cc, T = oracle_case("grid4x5_s4_dd", cases.dd_twin)
     check_run(env, cc, T, np.float32, "auto", 6, 10, "bfs", 1e-6)
+
+
+def test_dd_80q_full_size(env):
+    """The 80-qubit workload itself: an 8x10 supremacy-style grid of depth 10
+    cut into 2x2 blocks (4 subcircuits of <= 25 qubits, K = 8), FP32 tensors
+    from the GPU simulator, 30 active qubits (2^30 bins) and 10 BFS recursions.
+    Its tensors come from the CUDA path, so the oracle cannot take them;
+    checked by properties that hold at any size: recursion 1's bins sum to 1
+    (the uncut circuit preserves trace), every zoomed recursion's bins sum to
+    the parent bin's FP64 value, no bin is below -1e-6, and the FP64-ranked top
+    values agree with the stored bins."""
+    torch, cutqc = env
+    from paper_2012_02333_gb300 import circuits as C
+    from paper_2012_02333_gb300 import dd
+    cc = C.grid_blocks(8, 10, 10, 0, 2, 2, 8, 25)
+    assert cc.n == 80 and cc.n_cuts <= 8 and max(s.d for s in cc.subs) <= 25
+    ts = cutqc.simulate_tensors(cc, torch.float32)
+    st = dd.run(cc, ts, 30, 10, "bfs")
+    assert len(st.recursions) == 10
+    top = {}
+    for ri, rec in enumerate(st.recursions):
+        b = rec.bins
+        assert b.numel() == 2 ** sum(1 for r in rec.roles if r == 0)
+        total = torch.sum(b, dtype=torch.float64).item()
+        assert b.min().item() >= -1e-6
+        for i, v in rec.top:
+            assert abs(b[i].item() - v) <= 1e-6 + 1e-5 * abs(v)
+        top[ri] = dict(rec.top)
+        if rec.parent is None:
+            assert total == pytest.approx(1.0, abs=1e-4)
+        else:
+            pr, pb = rec.parent
+            assert total == pytest.approx(top[pr][pb], abs=1e-6 + 1e-4 * top[pr][pb])
+    del st, ts
+    torch.cuda.empty_cache()
