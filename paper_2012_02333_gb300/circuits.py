@@ -500,3 +500,27 @@ def qaoa_2cluster(n_per: int = 15, seed: int = 0) -> CutCircuit:
 def bv_chain(n: int, seed: int, n_sub: int = 2) -> CutCircuit:
     """BV whose CNOTs all target the last qubit, cut into n_sub chain blocks."""
     return chain_blocks(bv(n, seed), n_sub)
+
+
+def batch_instances(count: int = 64, seed: int = 0, max_width: int = 16) -> List[CutCircuit]:
+    """A batch of cut circuits of uneven shape (the batched workload): each
+    instance draws its family from {HWEA, AQFT (rotations below pi/2^4
+    dropped), BV with a random secret}, an even width of 16..28 qubits and 2..4
+    chain blocks of at most `max_width` qubits, with a cut budget K <= 8 and
+    4^K * 2^n <= 2^40 (cut by construction: crossing gates beyond the budget
+    are dropped)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fam = ("hwea", "aqft", "bv")[int(rng.integers(3))]
+        n = int(rng.integers(8, 15)) * 2
+        s = int(rng.integers(2, 5))
+        while n / s > max_width - 2:
+            s += 1
+        kmax = min(8, (40 - n) // 2)
+        cs = int(rng.integers(1 << 30))
+        c = hwea(n, cs) if fam == "hwea" else aqft(n, cs) if fam == "aqft" else bv(n, cs)
+        cc = chain_blocks(c, s, max_cuts=kmax, max_width=max_width)
+        cc.family = fam  # type: ignore[attr-defined]
+        out.append(cc)
+    return out

@@ -163,6 +163,8 @@ struct DdSubPlan {
 
 struct Plan {
   int n_out = 0, K = 0, dtype = CUTQC_F32;
+  int tuned = -1;                      // measured final form under CUTQC_AUTO (batched calls): -1 not yet,
+                                       // CUTQC_CC, or CUTQC_AUTO (tensor core, device-chosen split)
   std::vector<DdSubPlan> dd;           // dynamic definition only
   size_t dd_front = 0;
   void* ddtab = nullptr;
@@ -180,22 +182,34 @@ struct Plan {
   }
 };
 
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t gen = 0;
+};
+
+constexpr int kBranches = 8;      // parallel branches of a captured batch
+
 struct DeviceState {
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  uint64_t ws_gen = 0;            // bumped whenever the workspace moves
   void* one = nullptr;            // a device constant 1.0 (f64) / 1.0f (f32)
   std::unordered_map<std::string, std::unique_ptr<Plan>> plans;
   std::vector<std::string> order;
+  std::unordered_map<std::string, GraphEntry> graphs;   // captured batched calls
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
 };
 static std::map<int, DeviceState> g_dev;
 
 // main-kernel timing (cutqc_profile)
 static bool g_profile = false;
+static bool g_capturing = false;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_prof_events;
 
 void prof_begin(cudaStream_t s, cudaEvent_t* a) {
   *a = nullptr;
-  if (!g_profile) return;
+  if (!g_profile || g_capturing) return;
   CUTQC_CUDA(cudaEventCreate(a));
   CUTQC_CUDA(cudaEventRecord(*a, s));
 }
@@ -213,8 +227,16 @@ static DeviceState& device_state() {
   return g_dev[dev];
 }
 
+static void drop_graphs(DeviceState& ds) {
+  for (auto& kv : ds.graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  ds.graphs.clear();
+}
+
 static void* workspace(DeviceState& ds, size_t bytes) {
   if (bytes > ds.ws_bytes) {
+    drop_graphs(ds);   // captured launches point into the old workspace
+    ++ds.ws_gen;
     if (ds.ws) CUTQC_CUDA(cudaFree(ds.ws));
     ds.ws = nullptr;
     ds.ws_bytes = 0;
@@ -574,7 +596,7 @@ static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
 // tensors of the plan's original nodes.  Returns a pointer to the back region.
 static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
-                      cudaStream_t s) {
+                      cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr) {
   size_t tc_ws = 0;
   std::vector<Contraction> cs(P.steps.size());
   char* base = nullptr;
@@ -588,6 +610,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   }
   const void* one = P.dtype == CUTQC_F64 ? ds.one : static_cast<char*>(ds.one) + 8;
   // decide the algorithm of the final step
+  if (algo == CUTQC_AUTO && P.tuned == CUTQC_CC) algo = CUTQC_CC;
   int final_algo = algo;
   if (final_algo == CUTQC_AUTO) final_algo = (P.dtype == CUTQC_F32) ? CUTQC_TC_BF16X3 : CUTQC_CC;
   const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6;
@@ -614,7 +637,11 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   }
   front = align_up(front);
   need = align_up(need);
-  char* ws = static_cast<char*>(workspace(ds, front + need + back));
+  if (bytes_only) {
+    *bytes_only = front + need + align_up(back);
+    return nullptr;
+  }
+  char* ws = ws_given ? ws_given : static_cast<char*>(workspace(ds, front + need + back));
   base = ws + front;
   const std::vector<const void*> orig_tensor = pre(ws);
   auto node_ptr = [&](int i) -> const void* {
@@ -681,6 +708,125 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   return base + need;
 }
 
+// Batched full definition.  Every problem gets its own region of the
+// workspace, so problems are independent and run on parallel stream branches.
+// The first call with a given set of shapes and pointers runs eagerly (and,
+// under CUTQC_AUTO with FP32 tensors, times the CUDA-core and tensor-core
+// forms of each problem's final contraction once and keeps the faster); the
+// call is then captured into a CUDA graph that later identical calls replay
+// with a single launch.
+static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, void* const* out, int algo,
+                      double* sum_p, cudaStream_t s) {
+  std::vector<Plan*> plans(n);
+  std::ostringstream key;
+  key << algo << '#';
+  for (int i = 0; i < n; ++i) {
+    const cutqc_problem* p = &problems[i];
+    const std::string k = fd_key(p, 0, nullptr, 0);
+    plans[i] = &get_plan(ds, k, [&](Plan& P) { build_fd_plan(P, p); });
+    key << k << '@';
+    for (int c = 0; c < p->n_sub; ++c) key << p->sub[c].tensor << ',';
+    key << out[i] << ',' << (sum_p ? (const void*)(sum_p + i) : nullptr) << ';';
+  }
+  auto tensors_of = [](const cutqc_problem* p) {
+    return [p](char*) {
+      std::vector<const void*> t(p->n_sub);
+      for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
+      return t;
+    };
+  };
+  // autotune the final form once per plan (eager, outside any capture)
+  for (int i = 0; i < n; ++i) {
+    Plan& P = *plans[i];
+    if (algo != CUTQC_AUTO || P.dtype != CUTQC_F32 || P.tuned >= 0) continue;
+    cudaEvent_t e0, e1;
+    CUTQC_CUDA(cudaEventCreate(&e0));
+    CUTQC_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int choice = CUTQC_CC;
+    for (int form : {CUTQC_CC, CUTQC_TC_BF16X3}) {
+      float t = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        CUTQC_CUDA(cudaEventRecord(e0, s));
+        run_plan(ds, P, 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr,
+                 form == CUTQC_TC_BF16X3 ? CUTQC_AUTO : form, s);
+        CUTQC_CUDA(cudaEventRecord(e1, s));
+        CUTQC_CUDA(cudaEventSynchronize(e1));
+        CUTQC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+      }
+      if (g_last_algo == CUTQC_CC && form != CUTQC_CC) t = 1e30f;   // the shape has no tensor-core form
+      if (t < best) {
+        best = t;
+        choice = form;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    P.tuned = choice == CUTQC_CC ? CUTQC_CC : CUTQC_AUTO;
+  }
+  // workspace regions
+  std::vector<size_t> off(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    size_t b = 0;
+    int a = algo;
+    if (a == CUTQC_AUTO && plans[i]->tuned == CUTQC_CC) a = CUTQC_CC;
+    run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], nullptr, a, s, nullptr, &b);
+    off[i + 1] = off[i] + align_up(b);
+  }
+  char* ws = static_cast<char*>(workspace(ds, off[n]));
+  key << "|gen" << ds.ws_gen;
+  const std::string gk = key.str();
+  auto it = ds.graphs.find(gk);
+  if (it != ds.graphs.end() && it->second.gen == ds.ws_gen) {
+    CUTQC_CUDA(cudaGraphLaunch(it->second.exec, s));
+    return;
+  }
+  auto algo_of = [&](int i) {
+    return (algo == CUTQC_AUTO && plans[i]->tuned == CUTQC_CC) ? (int)CUTQC_CC : algo;
+  };
+  // eager run of the whole batch on the caller's stream
+  for (int i = 0; i < n; ++i)
+    run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i), s,
+             ws + off[i]);
+  // capture the same launches over parallel branches for later calls
+  if (!ds.fork) {
+    for (int b = 0; b < kBranches; ++b) {
+      CUTQC_CUDA(cudaStreamCreateWithFlags(&ds.branch[b], cudaStreamNonBlocking));
+      CUTQC_CUDA(cudaEventCreateWithFlags(&ds.join[b], cudaEventDisableTiming));
+    }
+    CUTQC_CUDA(cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming));
+  }
+  cudaGraph_t graph = nullptr;
+  g_capturing = true;
+  try {
+    CUTQC_CUDA(cudaStreamBeginCapture(ds.branch[0], cudaStreamCaptureModeThreadLocal));
+    CUTQC_CUDA(cudaEventRecord(ds.fork, ds.branch[0]));
+    for (int b = 1; b < kBranches; ++b) CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[b], ds.fork, 0));
+    for (int i = 0; i < n; ++i)
+      run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i),
+               ds.branch[i % kBranches], ws + off[i]);
+    for (int b = 1; b < kBranches; ++b) {
+      CUTQC_CUDA(cudaEventRecord(ds.join[b], ds.branch[b]));
+      CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.join[b], 0));
+    }
+    CUTQC_CUDA(cudaStreamEndCapture(ds.branch[0], &graph));
+  } catch (...) {
+    g_capturing = false;
+    cudaGraph_t g2 = nullptr;
+    cudaStreamEndCapture(ds.branch[0], &g2);
+    if (g2) cudaGraphDestroy(g2);
+    throw;
+  }
+  g_capturing = false;
+  GraphEntry e;
+  e.gen = ds.ws_gen;
+  const cudaError_t ie = cudaGraphInstantiate(&e.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  CUTQC_CUDA(ie);
+  if (ds.graphs.size() >= 16) drop_graphs(ds);
+  ds.graphs[gk] = e;
+}
+
 }  // namespace cutqc
 
 using namespace cutqc;
@@ -700,18 +846,20 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceState& ds = device_state();
-    for (int i = 0; i < n_problems; ++i) {
-      const cutqc_problem* p = &problems[i];
+    auto tensors_of = [&](const cutqc_problem* p) {
+      return [p](char*) {
+        std::vector<const void*> t(p->n_sub);
+        for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
+        return t;
+      };
+    };
+    if (n_problems == 1) {
+      const cutqc_problem* p = &problems[0];
       Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
-      run_plan(
-          ds, P, 0, 0,
-          [&](char*) {
-            std::vector<const void*> t(p->n_sub);
-            for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
-            return t;
-          },
-          out[i], sum_p ? sum_p + i : nullptr, algo, s);
+      run_plan(ds, P, 0, 0, tensors_of(p), out[0], sum_p, algo, s);
+      return;
     }
+    run_batch(ds, problems, n_problems, out, algo, sum_p, s);
   });
 }
 
@@ -957,6 +1105,12 @@ void cutqc_release(void) {
   cudaGetDevice(&cur);
   for (auto& kv : g_dev) {
     cudaSetDevice(kv.first);
+    drop_graphs(kv.second);
+    for (int b = 0; b < kBranches; ++b) {
+      if (kv.second.branch[b]) cudaStreamDestroy(kv.second.branch[b]);
+      if (kv.second.join[b]) cudaEventDestroy(kv.second.join[b]);
+    }
+    if (kv.second.fork) cudaEventDestroy(kv.second.fork);
     kv.second.plans.clear();
     kv.second.order.clear();
     if (kv.second.ws) cudaFree(kv.second.ws);
