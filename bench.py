@@ -38,6 +38,10 @@ METRIC = "reconstructed probs/sec & % roofline at ≤1e-6 max abs err vs FP64 or
 UNIT = "probs/s"
 WORKLOAD = "supremacy_4x6_depth8_K4_fd_fp32"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM traffic (read + write bytes) of one k_tc_gemm launch on this workload from
+# the ncu capture summarised in profiles/k_tc_gemm_supremacy_4x6_k4.md, valid while
+# the kernel source is unchanged (first 16 hex digits of its SHA-256)
+TRAFFIC_TC = {"sha256_16": "ceea758f0e99e328", "bytes": 16.72e6}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
@@ -322,7 +326,13 @@ def run_ours(args):
     else:
         roof = {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm["peak_gbs"], "unit": "GB/s",
                 "frac": hbm["frac"]}
-    roof.update({"traffic": None, "kernel_ms": kern_ms, "peak_file": pk_src,
+    traffic = None
+    if used_tc:
+        import hashlib
+        src = os.path.join(ROOT, "paper_2012_02333_gb300", "csrc", "k_tc.cu")
+        if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_TC["sha256_16"]:
+            traffic = TRAFFIC_TC["bytes"]
+    roof.update({"traffic": traffic, "kernel_ms": kern_ms, "peak_file": pk_src,
                  "t_roof_us": max(comp["t_roof_us"], hbm["t_roof_us"]), "compute": comp, "hbm": hbm})
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
