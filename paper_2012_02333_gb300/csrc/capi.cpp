@@ -147,7 +147,7 @@ struct Step {
   int vecB = 1;
   size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
   size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
-  size_t ws_bound = 0, ws_nseg = 0;
+  size_t ws_bound = 0, ws_nseg = 0, ws_counter = 0;
 };
 
 struct DdSubPlan {
@@ -435,6 +435,8 @@ static void finalize_plan(Plan& P) {
     w = align_up(w + 8);
     st.ws_nseg = w;
     w = align_up(w + 4);
+    st.ws_counter = w;
+    w = align_up(w + 4);
   }
   P.ws_bytes = w;
 }
@@ -653,8 +655,9 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   auto dtab = static_cast<char*>(P.dtab);
   // row flags and max |.| of each step's operands, both in one launch
   std::vector<int> flagged(P.nodes.size(), 0);
-  auto ensure_flags = [&](int ia, int ib) {
+  auto ensure_flags = [&](int ia, int ib, const CompactJob* cj = nullptr) {
     RowStatsJobs j{};
+    if (cj) j.cj = *cj;
     for (int i : {ia, ib}) {
       if (flagged[i]) continue;
       flagged[i] = 1;
@@ -667,11 +670,37 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       ++j.n;
     }
     if (j.n) launch_row_stats(j, P.dtype, s);
+    else if (cj) fail(CUTQC_ERR_CUDA, "compaction job without a row-statistics launch");
   };
   for (size_t i = 0; i < P.steps.size(); ++i) {
     const Step& st = P.steps[i];
     Contraction& c = cs[i];
-    ensure_flags(st.a, st.b);
+    const bool last_step = (i + 1 == P.steps.size());
+    const bool both_new = !flagged[st.a] || !flagged[st.b];
+    if (last_step && use_tc_final && both_new && st.kmax <= 4096) {
+      // the last row-statistics block compacts the terms and picks the split
+      CompactJob cj;
+      cj.active = 1;
+      cj.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
+      cj.kmax = st.kmax;
+      cj.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
+      cj.nzB = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.b]);
+      cj.rmaxA = reinterpret_cast<const float*>(base + P.ws_rmax[st.a]);
+      cj.rmaxB = reinterpret_cast<const float*>(base + P.ws_rmax[st.b]);
+      cj.crow = reinterpret_cast<int32_t*>(base + st.ws_crow);
+      cj.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
+      cj.scale = c.scale;
+      cj.bound = reinterpret_cast<double*>(base + st.ws_bound);
+      cj.nseg = reinterpret_cast<int32_t*>(base + st.ws_nseg);
+      cj.nseg_fixed = algo == CUTQC_TC_BF16X3 ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+      cj.sum_zero = sum;
+      cj.counter = reinterpret_cast<unsigned*>(base + st.ws_counter);
+      CUTQC_CUDA(cudaMemsetAsync(cj.counter, 0, sizeof(unsigned), s));
+      ensure_flags(st.a, st.b, &cj);
+      c.compacted = true;
+    } else {
+      ensure_flags(st.a, st.b);
+    }
     c.A = node_ptr(st.a);
     c.B = node_ptr(st.b);
     c.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
@@ -681,7 +710,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     c.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
     c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
     c.nzB = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.b]);
-    const bool final_step = (i + 1 == P.steps.size());
+    const bool final_step = last_step;
     if (final_step && use_tc_final) {
       c.rmaxA = reinterpret_cast<const float*>(base + P.ws_rmax[st.a]);
       c.rmaxB = reinterpret_cast<const float*>(base + P.ws_rmax[st.b]);

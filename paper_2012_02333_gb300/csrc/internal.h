@@ -103,17 +103,39 @@ struct Contraction {
   int32_t* nseg = nullptr;
   bool profile = false;            // bracket the contraction kernel for cutqc_profile
   double* sum_zero = nullptr;      // device double the compaction zeroes before the contraction adds to it
+  bool compacted = false;          // crow / kcount / nseg / bound already written (row statistics did it)
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
 };
 
 // k_cc.cu
+// Stable compaction of a contraction's row pairs (early termination) and the
+// split-count choice, done by the last block of a row-statistics launch.
+struct CompactJob {
+  int active = 0;
+  const int32_t* rows = nullptr;       // [2][kmax]
+  int kmax = 0;
+  const int32_t* nzA = nullptr;
+  const int32_t* nzB = nullptr;
+  const float* rmaxA = nullptr;
+  const float* rmaxB = nullptr;
+  int32_t* crow = nullptr;             // [2][kmax]
+  int32_t* kcount = nullptr;
+  double scale = 1.0;
+  double* bound = nullptr;
+  int32_t* nseg = nullptr;
+  int nseg_fixed = 0;
+  double split_tol = 2.5e-7;
+  double* sum_zero = nullptr;
+  unsigned* counter = nullptr;         // zero before the launch
+};
 struct RowStatsJobs {   // up to two tensors whose rows get non-zero flags and max |.|
   int n;
   const void* t[2];
   int64_t rows[2], cols[2];
   int32_t* flags[2];
   float* rmax[2];
+  CompactJob cj;
 };
 void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s);
 void launch_row_stats(const void* T, int dtype, int rows, int f, int32_t* flags, float* rmax, cudaStream_t s);

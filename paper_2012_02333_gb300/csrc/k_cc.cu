@@ -60,10 +60,69 @@ __device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64
   }
 }
 
-// one block per row of up to two tensors: row 0 .. rows0-1 of job 0, then job 1
+// the block-wide stable compaction of one contraction's row pairs (batch 1),
+// the a-priori bound S and the split count
+__device__ void compact_block(const CompactJob& cj) {
+  __shared__ int warp_tot[32];
+  __shared__ double warp_s[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  double s_acc = 0.0;
+  const int32_t* ra = cj.rows;
+  const int32_t* rb = cj.rows + cj.kmax;
+  for (int k0 = 0; k0 < cj.kmax; k0 += blockDim.x) {
+    const int k = k0 + threadIdx.x;
+    int keep = 0, a = 0, b = 0;
+    if (k < cj.kmax) {
+      a = ra[k];
+      b = rb[k];
+      keep = cj.nzA[a] && cj.nzB[b];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) warp_tot[warp] = __popc(m);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < nw; ++w) {
+      if (w < warp) off += warp_tot[w];
+      tot += warp_tot[w];
+    }
+    if (keep) {
+      const int ci = base + off + __popc(m & ((1u << lane) - 1u));
+      cj.crow[ci] = a;
+      cj.crow[cj.kmax + ci] = b;
+      if (cj.bound) s_acc += (double)cj.rmaxA[a] * (double)cj.rmaxB[b];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base += tot;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s_acc += __shfl_xor_sync(0xffffffffu, s_acc, o);
+  if (lane == 0) warp_s[warp] = s_acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    *cj.kcount = base;
+    if (cj.sum_zero) *cj.sum_zero = 0.0;
+    if (cj.bound) {
+      double S = 0.0;
+      for (int w = 0; w < nw; ++w) S += warp_s[w];
+      S *= cj.scale;
+      *cj.bound = S;
+      // BF16 x3 drops terms of at most ~3 * 2^-18 relative to |a||b| per product
+      *cj.nseg = cj.nseg_fixed ? cj.nseg_fixed : (3.0 * 3.814697265625e-06 * S <= cj.split_tol ? 3 : 6);
+    }
+  }
+}
+
+// one block per row of up to two tensors: row 0 .. rows0-1 of job 0, then job
+// 1; with a compaction job, the block that finishes last (an atomic count
+// after a fence: every other block's statistics are then visible) compacts
 template <typename T>
 __global__ void k_row_stats(RowStatsJobs jobs) {
   CUTQC_PDL_LAUNCH();   // the operand preparation may launch and wait on this grid
+  __shared__ int is_last;
   int j = 0;
   int64_t r = blockIdx.x;
   if (r >= jobs.rows[0]) {
@@ -72,6 +131,16 @@ __global__ void k_row_stats(RowStatsJobs jobs) {
   }
   const T* t = static_cast<const T*>(jobs.t[j]);
   row_stats_block<T>(t + r * jobs.cols[j], jobs.cols[j], jobs.flags[j] + r, jobs.rmax[j] + r);
+  if (!jobs.cj.active) return;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    is_last = atomicAdd(jobs.cj.counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  compact_block(jobs.cj);
+  if (threadIdx.x == 0) *jobs.cj.counter = 0u;
 }
 
 // ---- stable compaction of the inner index (one block per batch) ----------

@@ -22,7 +22,9 @@
 //              shared-memory ring;
 //   warp 1     allocates 512 TMEM columns (two 128x256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M=128, N=256, K=16);
-//   warps 2-5  epilogue: tcgen05.ld of their 32 TMEM lanes (lane = row),
+//   warps 2-5  epilogue (one per TMEM lane quarter; EPI_WARPS = 8 splits the
+//              columns between two warps per quarter): tcgen05.ld of their 32
+//              TMEM lanes (lane = row),
 //              scale by 2^-K, deposit (m, n) into the output index with the
 //              additive per-bit tables held in registers, 16-byte streaming
 //              stores (runs of consecutive columns that are consecutive in
@@ -54,7 +56,8 @@ constexpr int B_PIECE = BN * KS * 2;          // 16 KiB per split piece of B
 constexpr int MAX_STAGES = 4;
 constexpr int STAGE_AREA = 3 * 3 * (A_PIECE + B_PIECE);   // 216 KiB: 3 stages of 3 pieces or 4 of 2
 constexpr int TMEM_COLS = 512;
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 4;                  // one per TMEM lane quarter (8 measured slower)
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256;
 constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 1);
-      mbar_init(&tempty[i], 4);
+      mbar_init(&tempty[i], EPI_WARPS);
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -428,8 +431,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   } else if (warp >= 2) {
-    // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. +31; lane = row
+    // ---- epilogue: warp w reads TMEM lanes 32 * (w % 4) .. +31 (lane = row),
+    // columns 128 * hf .. +127 of the accumulator
     const int q = warp & 3;
+    const int hf = (warp - 2) / 4;
+    constexpr int CPW = BN / 32 / (EPI_WARPS / 4);   // 32-column chunks per warp
     double local = 0.0;
     // the deposit is additive over disjoint index bits, so a row's output
     // address is dep(row base) + dep(lane) + dep(chunk column base) +
@@ -457,7 +463,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         tc_fence_after();
       }
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = hf * CPW; c < (hf + 1) * CPW; ++c) {
         uint32_t r[32];
         if (nkb > 0) {
           tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
@@ -590,7 +596,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   pa.blocks0 = (int)(M / 64);
   pa.Kp = Kp;
   pa.kmax = c.kmax;
-  pa.fused = c.kmax <= 4096;
+  pa.fused = !c.compacted && c.kmax <= 4096;
   pa.rows = c.rows;
   pa.crow = c.crow;
   pa.nzA = c.nzA;
@@ -606,7 +612,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   pa.sum_zero = c.sum;
   pa.out[0] = Ab;
   pa.out[1] = Bb;
-  if (!pa.fused) {
+  if (!pa.fused && !c.compacted) {
     Contraction cc = c;
     cc.sum_zero = c.sum;
     launch_compact(cc, s);
