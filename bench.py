@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="supremacy_4x6",
+                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80"],
+                    help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
 
@@ -144,13 +147,23 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """The maximum of a per-rank number over all ranks (the job's time is its
+    slowest rank's); CUDA tensors under NCCL, host tensors under gloo."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(n_out_per_rank, world, ms):
+    """Whole-job throughput: every rank reconstructs its own replica (weak
+    scaling, no collective on the data path), so the job processes
+    world * n_out probabilities in the slowest rank's time."""
+    return world * n_out_per_rank / (ms / 1e3)
 
 
 def oracle_sample_rate(cc, n_terms: int, T64=None):
@@ -274,7 +287,7 @@ def run_ours(args):
     cutqc.profile(False)
     n_main, main_ms = cutqc.profile_read()
     ms = max_over_ranks(ms, world)
-    value = world * n_out / (ms / 1e3)
+    value = job_value(n_out, world, ms)
     kern_ms = main_ms / max(n_main, 1)
 
     # end to end through the public API: pinned host tensors in, probabilities out
@@ -359,10 +372,104 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_other(args):
+    """Timings of the other configurations (not the benchmark line): the 10-qubit
+    HWEA in FP64 (CUDA core), the 64-instance batch (graph replay), the 30-qubit
+    QAOA MaxCut forward and adjoint, one 80-qubit dynamic-definition recursion
+    with 30 active qubits.  Inputs come from the GPU subcircuit simulator."""
+    import torch
+
+    from paper_2012_02333_gb300 import circuits, cutqc, dd
+
+    rank, world, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    sink = torch.empty((), dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.fill_(1.0)
+        torch.sum(flush, dim=0, out=sink)
+
+    def timed(step):
+        for _ in range(max(args.warmup, 3)):
+            flush_l2()
+            step()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(args.steps):
+            flush_l2()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            step()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return max_over_ranks(statistics.mean(ts), world)
+
+    extra = {}
+    w = args.workload
+    if w == "hwea10":
+        cc = circuits.hwea_10q_k1(0)
+        ts = cutqc.simulate_tensors(cc, torch.float64, dev)
+        problem = cutqc.Problem.from_cut(cc, ts)
+        out = torch.empty(2 ** cc.n, dtype=torch.float64, device=dev)
+        ms = timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc"))
+        units, unit, dtype = 2 ** cc.n, "probs/s", "f64"
+        cfg = {"workload": "hwea10_K1_fd_fp64", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
+    elif w == "batch64":
+        batch = circuits.batch_instances(64, 0)
+        tss = [cutqc.simulate_tensors(cc, torch.float32, dev) for cc in batch]
+        problems = [cutqc.Problem.from_cut(cc, t) for cc, t in zip(batch, tss)]
+        outs = [torch.empty(2 ** cc.n, device=dev) for cc in batch]
+        sums = torch.empty(len(batch), dtype=torch.float64, device=dev)
+        ms = timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "auto", sums))
+        units, unit, dtype = sum(2 ** cc.n for cc in batch), "probs/s", "f32 (per instance cc or bf16x3/x6)"
+        cfg = {"workload": "batch64_hwea_aqft_bv_fd_fp32", "instances": len(batch),
+               "n_qubits": [cc.n for cc in batch], "n_cuts": [cc.n_cuts for cc in batch],
+               "subcircuits": [len(cc.subs) for cc in batch], "launch": "CUDA graph replay"}
+    elif w == "qaoa30":
+        cc = circuits.qaoa_2cluster(15, 0)
+        ts = cutqc.simulate_tensors(cc, torch.float32, dev)
+        problem = cutqc.Problem.from_cut(cc, ts)
+        out = torch.empty(2 ** cc.n, device=dev)
+        sp = torch.empty(1, dtype=torch.float64, device=dev)
+        ms = timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp))
+        grads = [torch.empty_like(t) for t in ts]
+        loss = torch.empty(1, dtype=torch.float64, device=dev)
+        ms_bwd = timed(lambda: cutqc.cutqc_reconstruct_backward(problem, grads, edges=cc.edges, loss_value=loss))
+        extra = {"adjoint_ms": ms_bwd, "adjoint": "MaxCut loss and dL/dT of both subcircuits",
+                 "expected_cut": float(loss.item())}
+        units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
+        cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
+    else:
+        cc = circuits.grid_blocks(8, 10, 10, 0, 2, 2, 8, 25)
+        ts = cutqc.simulate_tensors(cc, torch.float32, dev)
+        problem = cutqc.Problem.from_cut(cc, ts)
+        roles = dd.initial_roles(cc.n, 30)
+        bins = torch.empty(2 ** 30, device=dev)
+        ms = timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto"))
+        units, unit, dtype = 2 ** 30, "bins/s", "f32 bins, FP64 ranking"
+        cfg = {"workload": "dd80_grid8x10_d10_30active_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts,
+               "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
+               "step": "one recursion: merge, contraction into 2^30 bins, top-32 with FP64 re-ranking"}
+    line = {"metric": METRIC, "value": world * units / (ms / 1e3), "unit": unit, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "supremacy_4x6":
+        run_other(args)
     else:
         run_ours(args)
 

@@ -159,6 +159,8 @@ struct DdSubPlan {
   std::vector<int> act_rank;           // bin rank of each active output (x-bit order)
   std::vector<int> cuts;
   size_t ws_merged = 0;                // offset of the merged tensor in the front region
+  size_t ws_merged64 = 0;              // ... and of its FP64 copy (for the bin ranking)
+  bool run = false;                    // merged qubits are the lowest output bits
 };
 
 struct Plan {
@@ -569,8 +571,16 @@ static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
     d.depAct = deposit_table(act_val);
     d.depMrg = deposit_table(mrg_val);
     d.cuts = nd.cuts;
+    // merged outputs exactly on the lowest x index bits 0 .. mg-1?
+    {
+      uint64_t mm = 0;
+      for (uint64_t v : mrg_val) mm |= v;
+      d.run = d.mg > 0 && mm == ((uint64_t(1) << d.mg) - 1);
+    }
     d.ws_merged = front;
     front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * es);
+    d.ws_merged64 = front;
+    front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * 8);
     P.dd.push_back(d);
     P.nodes.push_back(nd);
   }
@@ -970,15 +980,18 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
       back = align_up(back + NC * 8);
     }
     char* ddtab = static_cast<char*>(P.ddtab);
+    char* front_ptr = nullptr;
     char* back_ptr = run_plan(
         ds, P, P.dd_front, back,
         [&](char* front) {
+          front_ptr = front;
           std::vector<const void*> t(p->n_sub);
           for (int c = 0; c < p->n_sub; ++c) {
             const DdSubPlan& d = P.dd[c];
             launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
                             reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
-                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, front + d.ws_merged, s);
+                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run,
+                            front + d.ws_merged, reinterpret_cast<double*>(front + d.ws_merged64), s);
             t[c] = front + d.ws_merged;
           }
           return t;
@@ -1000,6 +1013,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
         const DdSubPlan& d = P.dd[c];
         DdEvalSub& e = ea.sub[c];
         ea.tens[c] = p->sub[c].tensor;
+        e.m64 = reinterpret_cast<const double*>(front_ptr + d.ws_merged64);
         e.rows = d.rows;
         e.cols = int64_t(1) << d.f;
         e.a = d.a;

@@ -152,6 +152,7 @@ size_t tc_workspace_bytes(const Contraction& c);
 // k_dd.cu
 struct DdEvalSub {
   int64_t rows, cols;
+  const double* m64;           // FP64 merged tensor [rows][2^a]
   int a, mg, nbA, nbM;
   uint64_t zoom;
   const uint64_t* depAct;
@@ -169,7 +170,7 @@ struct DdEvalArgs {
   DdEvalSub sub[16];
 };
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
-                     const uint64_t* depMrg, uint64_t zoom, void* M, cudaStream_t s);
+                     const uint64_t* depMrg, uint64_t zoom, bool run, void* M, double* M64, cudaStream_t s);
 size_t topk_workspace_bytes(int64_t n);
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
 void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s);

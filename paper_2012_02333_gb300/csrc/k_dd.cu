@@ -4,16 +4,19 @@
 //   its merged qubits (Algorithm 1: "group shots with common merged qubits"):
 //   M[row][xa] = sum_{xm} T[row][dep_act(xa) | dep_mrg(xm) | zoom], where the
 //   zoomed qubits are fixed at their bits.  Memory-bound: T is read once.
-//   With >= 32 merged values per output a warp owns an output (lanes stride
-//   the merged index, so low merged bits give coalesced reads); each lane
-//   accumulates runs of 16 in FP32 and folds them into FP64.
+//   When the merged qubits are the lowest output bits (the usual case) each
+//   output is a contiguous run read with 16-byte loads; otherwise, with >= 32
+//   merged values per output, a warp owns an output (lanes stride the merged
+//   index).  Runs of up to 32 values are summed pairwise in FP32 and folded
+//   into FP64; the FP64 sums are kept for the bin ranking.
 // k_topk_warps / k_topk_final: the 32 heaviest bins by their stored value
 //   (ties to the lower index): every warp keeps a sorted list of 32 across its
 //   lanes and inserts only values above its current minimum (ballot + shuffle);
 //   a single block merges the warp lists.
-// k_dd_m64 / k_dd_eval: exact FP64 values of the candidate bins from the
-//   original tensors: the merged sums for each candidate's active bits in FP64,
-//   then 2^-K sum_e prod_c M64_c[row_c(e)] in FP64.
+// k_dd_gather64 / k_dd_eval: FP64 values of the candidate bins: the merge
+//   kernels also keep their sums in FP64 (each run accumulated in FP64), the
+//   candidate's merged values are gathered from there, then
+//   2^-K sum_e prod_c M64_c[row_c(e)] in FP64.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -33,7 +36,8 @@ __device__ __forceinline__ uint64_t dep_tab(const uint64_t* __restrict__ tab, in
 template <typename T>
 __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, int mg,
                                 const uint64_t* __restrict__ depAct, int nbA, const uint64_t* __restrict__ depMrg,
-                                int nbM, uint64_t zoom, T* __restrict__ out, int64_t n_out) {
+                                int nbM, uint64_t zoom, T* __restrict__ out, double* __restrict__ out64,
+                                int64_t n_out) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -54,7 +58,10 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) out[o] = (T)acc;
+    if (lane == 0) {
+      out[o] = (T)acc;
+      out64[o] = acc;
+    }
   }
 }
 
@@ -62,7 +69,7 @@ template <typename T>
 __global__ void k_dd_merge_thread(const T* __restrict__ Tin, int64_t cols, int a, int mg,
                                   const uint64_t* __restrict__ depAct, int nbA,
                                   const uint64_t* __restrict__ depMrg, int nbM, uint64_t zoom,
-                                  T* __restrict__ out, int64_t n_out) {
+                                  T* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
   const int nm = 1 << mg;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = o >> a;
@@ -71,6 +78,68 @@ __global__ void k_dd_merge_thread(const T* __restrict__ Tin, int64_t cols, int a
     T acc = T(0);
     for (int xm = 0; xm < nm; ++xm) acc += base[dep_tab(depMrg, nbM, (uint64_t)xm)];
     out[o] = acc;
+    out64[o] = (double)acc;
+  }
+}
+
+// Merged qubits on the lowest output bits: every output sums one contiguous
+// run of 2^mg values.  Thread per output for runs of 4..256 values (16-byte
+// loads, pairwise FP32 over groups of 32, FP64 across groups), warp per
+// output for longer runs.
+__device__ __forceinline__ float sum4(float4 v) { return (v.x + v.y) + (v.z + v.w); }
+
+__global__ void k_dd_merge_run_thread(const float* __restrict__ Tin, int64_t cols, int a, int mg,
+                                      const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom,
+                                      float* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
+  const int ng = 1 << (mg - 2);   // float4 groups in the run
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out; o += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = o >> a;
+    const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
+    const float4* p = reinterpret_cast<const float4*>(Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom));
+    double acc = 0.0;
+    for (int g0 = 0; g0 < ng; g0 += 8) {
+      float t8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t8[j] = g0 + j < ng ? sum4(p[g0 + j]) : 0.0f;
+#pragma unroll
+      for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) t8[j] += t8[j + w];
+      acc += (double)t8[0];
+    }
+    out[o] = (float)acc;
+    out64[o] = acc;
+  }
+}
+
+__global__ void k_dd_merge_run_warp(const float* __restrict__ Tin, int64_t cols, int a, int mg,
+                                    const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom,
+                                    float* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ng = int64_t(1) << (mg - 2);
+  for (int64_t o = warp; o < n_out; o += nwarps) {
+    const int64_t row = o >> a;
+    const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
+    const float4* p = reinterpret_cast<const float4*>(Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom));
+    double acc = 0.0;
+    for (int64_t g0 = lane; g0 < ng; g0 += 32 * 8) {
+      float t8[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t8[j] = g0 + 32 * j < ng ? sum4(p[g0 + 32 * j]) : 0.0f;
+#pragma unroll
+      for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) t8[j] += t8[j + w];
+      acc += (double)t8[0];
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      out[o] = (float)acc;
+      out64[o] = acc;
+    }
   }
 }
 
@@ -106,17 +175,27 @@ __global__ void k_topk_warps(const T* __restrict__ bins, int64_t n, int64_t per_
   float lv = -FLT_MAX;
   int64_t li = INT64_MAX;
   const int64_t lo = warp * per_warp, hi = min(n, lo + per_warp);
-  for (int64_t b0 = lo; b0 < hi; b0 += 32) {
-    const int64_t i = b0 + lane;
-    const float v = i < hi ? (float)bins[i] : -FLT_MAX;
-    const float thr = __shfl_sync(0xffffffffu, lv, 31);
-    unsigned m = __ballot_sync(0xffffffffu, i < hi && v > thr);
-    while (m) {
-      const int src = __ffs(m) - 1;
-      m &= m - 1;
-      const float sv = __shfl_sync(0xffffffffu, v, src);
-      const int64_t si = __shfl_sync(0xffffffffu, i, src);
-      warp_insert(lv, li, sv, si, lane);
+  // 128 consecutive values per step, 4 per lane (lane-major within the step, so
+  // candidates of one lane come in increasing index order and ties resolve low)
+  for (int64_t b0 = lo; b0 < hi; b0 += 128) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = b0 + 32 * u + lane;
+      v[u] = i < hi ? (float)bins[i] : -FLT_MAX;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = b0 + 32 * u + lane;
+      const float thr = __shfl_sync(0xffffffffu, lv, 31);
+      unsigned m = __ballot_sync(0xffffffffu, i < hi && v[u] > thr);
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const float sv = __shfl_sync(0xffffffffu, v[u], src);
+        const int64_t si = __shfl_sync(0xffffffffu, i, src);
+        warp_insert(lv, li, sv, si, lane);
+      }
     }
   }
   cv[warp * KC + lane] = lv;
@@ -166,10 +245,9 @@ __global__ void k_topk_final(const float* __restrict__ cv, const int64_t* __rest
 }
 
 // ---- FP64 re-evaluation of candidate bins ----------------------------------
-// M64[cand][c][row] = sum over merged values of T_c[row][x] in FP64, at the
-// candidate's active bits.  grid: (cand, c, row blocks), block 256.
-template <typename T>
-__global__ void k_dd_m64(const DdEvalArgs a, double* __restrict__ m64) {
+// M64[cand][c][row] = the FP64 merged value of subcircuit c at the candidate's
+// active bits (gathered from the merge kernels' FP64 output).  grid: (cand, c).
+__global__ void k_dd_gather64(const DdEvalArgs a, double* __restrict__ m64) {
   const int cand = blockIdx.x, c = blockIdx.y;
   const DdEvalSub& s = a.sub[c];
   const int64_t bin = a.cand_idx[cand];
@@ -180,25 +258,8 @@ __global__ void k_dd_m64(const DdEvalArgs a, double* __restrict__ m64) {
     const uint64_t bit = (bin >> (a.n_active - 1 - s.act_rank[i])) & 1;
     xa |= bit << (s.a - 1 - i);
   }
-  const uint64_t xbase = dep_tab(s.depAct, s.nbA, xa) | s.zoom;
-  const int64_t nm = int64_t(1) << s.mg;
-  const T* t = static_cast<const T*>(a.tens[c]);
-  __shared__ double red[8];
-  for (int64_t row = blockIdx.z; row < s.rows; row += gridDim.z) {
-    const T* base = t + row * s.cols + xbase;
-    double acc = 0.0;
-    for (int64_t xm = threadIdx.x; xm < nm; xm += blockDim.x) acc += (double)base[dep_tab(s.depMrg, s.nbM, (uint64_t)xm)];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
-      m64[((int64_t)cand * a.n_sub + c) * a.max_rows + row] = tot;
-    }
-    __syncthreads();
-  }
+  for (int64_t row = threadIdx.x; row < s.rows; row += blockDim.x)
+    m64[((int64_t)cand * a.n_sub + c) * a.max_rows + row] = s.m64[(row << s.a) + xa];
 }
 
 // value[cand] = 2^-K sum_e prod_c M64[cand][c][row_c(e)].  grid: cand, block 256.
@@ -237,26 +298,34 @@ unsigned grid_for(int64_t work, int per_block) {
 }  // namespace
 
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
-                     const uint64_t* depMrg, uint64_t zoom, void* M, cudaStream_t s) {
+                     const uint64_t* depMrg, uint64_t zoom, bool run, void* M, double* M64, cudaStream_t s) {
   const int64_t n_out = rows << a;
   const int64_t cols = int64_t(1) << f;
   const int nbA = (a + 7) / 8, nbM = (mg + 7) / 8;
-  if (mg >= 5) {
+  run = run && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
+  if (run && dtype == CUTQC_F32 && mg >= 2 && mg <= 8) {
+    k_dd_merge_run_thread<<<grid_for(n_out, 256), 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct,
+                                                                nbA, zoom, static_cast<float*>(M), M64, n_out);
+  } else if (run && dtype == CUTQC_F32 && mg > 8) {
+    k_dd_merge_run_warp<<<grid_for(n_out * 32, 256), 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg,
+                                                                   depAct, nbA, zoom, static_cast<float*>(M), M64,
+                                                                   n_out);
+  } else if (mg >= 5) {
     const unsigned g = grid_for(n_out * 32, 256);
     if (dtype == CUTQC_F64)
       k_dd_merge_warp<double><<<g, 256, 0, s>>>(static_cast<const double*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                                zoom, static_cast<double*>(M), n_out);
+                                                zoom, static_cast<double*>(M), M64, n_out);
     else
       k_dd_merge_warp<float><<<g, 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                               zoom, static_cast<float*>(M), n_out);
+                                               zoom, static_cast<float*>(M), M64, n_out);
   } else {
     const unsigned g = grid_for(n_out, 256);
     if (dtype == CUTQC_F64)
       k_dd_merge_thread<double><<<g, 256, 0, s>>>(static_cast<const double*>(T), cols, a, mg, depAct, nbA, depMrg,
-                                                  nbM, zoom, static_cast<double*>(M), n_out);
+                                                  nbM, zoom, static_cast<double*>(M), M64, n_out);
     else
       k_dd_merge_thread<float><<<g, 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                                 zoom, static_cast<float*>(M), n_out);
+                                                 zoom, static_cast<float*>(M), M64, n_out);
   }
   count_launch();
   check_launch("k_dd_merge");
@@ -269,8 +338,8 @@ size_t topk_workspace_bytes(int64_t n) {
 
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s) {
   const int64_t warps_max = 152 * 8 * 4;
-  int64_t per_warp = ((n + warps_max - 1) / warps_max + 31) / 32 * 32;
-  if (per_warp < 32) per_warp = 32;
+  int64_t per_warp = ((n + warps_max - 1) / warps_max + 127) / 128 * 128;
+  if (per_warp < 128) per_warp = 128;
   const int64_t warps = (n + per_warp - 1) / per_warp;
   const unsigned blocks = (unsigned)((warps + 7) / 8);
   float* cv = static_cast<float*>(ws);
@@ -287,13 +356,9 @@ void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v,
 }
 
 void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s) {
-  dim3 g(a.n_cand, a.n_sub, (unsigned)(a.max_rows < 1024 ? a.max_rows : 1024));
-  if (dtype == CUTQC_F64)
-    k_dd_m64<double><<<g, 256, 0, s>>>(a, m64);
-  else
-    k_dd_m64<float><<<g, 256, 0, s>>>(a, m64);
+  k_dd_gather64<<<dim3(a.n_cand, a.n_sub), 256, 0, s>>>(a, m64);
   count_launch();
-  check_launch("k_dd_m64");
+  check_launch("k_dd_gather64");
   k_dd_eval<<<a.n_cand, 256, 0, s>>>(a, m64, val);
   count_launch();
   check_launch("k_dd_eval");
