@@ -159,8 +159,10 @@ struct DdSubPlan {
   std::vector<int> act_rank;           // bin rank of each active output (x-bit order)
   std::vector<int> cuts;
   size_t ws_merged = 0;                // offset of the merged tensor in the front region
-  size_t ws_merged64 = 0;              // ... and of its FP64 copy (for the bin ranking)
+  size_t ws_mc = 0;                    // ... and of its compensation terms (FP32 tensors)
+  size_t ws_part = 0;                  // partial sums of split runs (contiguous-run merge)
   bool run = false;                    // merged qubits are the lowest output bits
+  bool dense = false;                  // ... and the active qubits the bits directly above them
 };
 
 struct Plan {
@@ -576,11 +578,16 @@ static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
       uint64_t mm = 0;
       for (uint64_t v : mrg_val) mm |= v;
       d.run = d.mg > 0 && mm == ((uint64_t(1) << d.mg) - 1);
+      uint64_t am = 0;
+      for (uint64_t v : act_val) am |= v;
+      d.dense = d.run && am == (((uint64_t(1) << d.a) - 1) << d.mg);
     }
     d.ws_merged = front;
     front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * es);
-    d.ws_merged64 = front;
-    front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * 8);
+    d.ws_mc = front;
+    if (p->dtype == CUTQC_F32) front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * 4);
+    d.ws_part = front;
+    if (d.run) front = align_up(front + ((size_t)d.rows << (d.a + dd_merge_chunks(d.rows, d.a, d.mg))) * 8);
     P.dd.push_back(d);
     P.nodes.push_back(nd);
   }
@@ -966,7 +973,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
     int64_t max_rows = 1;
     for (const DdSubPlan& d : P.dd) max_rows = std::max(max_rows, d.rows);
     constexpr int NC = 32;
-    size_t back = 0, off_tk = 0, off_cv = 0, off_ci = 0, off_m64 = 0, off_val = 0;
+    size_t back = 0, off_tk = 0, off_cv = 0, off_ci = 0, off_m64 = 0, off_val = 0, off_part = 0;
     if (topk > 0) {
       off_tk = 0;
       back = align_up(topk_workspace_bytes(nbins));
@@ -978,6 +985,8 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
       back = align_up(back + (size_t)NC * p->n_sub * max_rows * 8);
       off_val = back;
       back = align_up(back + NC * 8);
+      off_part = back;
+      back = align_up(back + (size_t)NC * dd_eval_chunks(p->n_cuts) * 8);
     }
     char* ddtab = static_cast<char*>(P.ddtab);
     char* front_ptr = nullptr;
@@ -990,8 +999,9 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
             const DdSubPlan& d = P.dd[c];
             launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
                             reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
-                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run,
-                            front + d.ws_merged, reinterpret_cast<double*>(front + d.ws_merged64), s);
+                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run, d.dense,
+                            front + d.ws_merged, reinterpret_cast<float*>(front + d.ws_mc), front + d.ws_part,
+                            s);
             t[c] = front + d.ws_merged;
           }
           return t;
@@ -1006,6 +1016,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
       ea.n_cuts = p->n_cuts;
       ea.n_active = na;
       ea.n_cand = NC;
+      ea.f64 = P.dtype == CUTQC_F64;
       ea.max_rows = max_rows;
       ea.scale = std::ldexp(1.0, -p->n_cuts);
       ea.cand_idx = ci;
@@ -1013,7 +1024,8 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
         const DdSubPlan& d = P.dd[c];
         DdEvalSub& e = ea.sub[c];
         ea.tens[c] = p->sub[c].tensor;
-        e.m64 = reinterpret_cast<const double*>(front_ptr + d.ws_merged64);
+        e.m = front_ptr + d.ws_merged;
+        e.mc = reinterpret_cast<const float*>(front_ptr + d.ws_mc);
         e.rows = d.rows;
         e.cols = int64_t(1) << d.f;
         e.a = d.a;
@@ -1029,7 +1041,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
       }
       double* m64 = reinterpret_cast<double*>(back_ptr + off_m64);
       double* val = reinterpret_cast<double*>(back_ptr + off_val);
-      launch_dd_rerank(ea, P.dtype, m64, val, s);
+      launch_dd_rerank(ea, P.dtype, m64, reinterpret_cast<double*>(back_ptr + off_part), val, s);
       std::vector<int64_t> hi(NC);
       std::vector<double> hv(NC);
       CUTQC_CUDA(cudaMemcpyAsync(hi.data(), ci, NC * 8, cudaMemcpyDeviceToHost, s));

@@ -152,7 +152,8 @@ size_t tc_workspace_bytes(const Contraction& c);
 // k_dd.cu
 struct DdEvalSub {
   int64_t rows, cols;
-  const double* m64;           // FP64 merged tensor [rows][2^a]
+  const void* m;               // merged tensor [rows][2^a] in the problem's dtype
+  const float* mc;             // FP32 tensors: compensation term of each merged value
   int a, mg, nbA, nbM;
   uint64_t zoom;
   const uint64_t* depAct;
@@ -163,17 +164,23 @@ struct DdEvalSub {
 };
 struct DdEvalArgs {
   int n_sub, n_cuts, n_active, n_cand;
+  int f64;                     // merged tensors are FP64
   int64_t max_rows;
   double scale;
   const int64_t* cand_idx;
   const void* tens[16];
   DdEvalSub sub[16];
 };
+// log2 of the chunks each output's run is split into by the contiguous-run merge (0 = none)
+int dd_merge_chunks(int64_t rows, int a, int mg);
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
-                     const uint64_t* depMrg, uint64_t zoom, bool run, void* M, double* M64, cudaStream_t s);
+                     const uint64_t* depMrg, uint64_t zoom, bool run, bool dense_bits, void* M, float* MC,
+                     void* part, cudaStream_t s);
 size_t topk_workspace_bytes(int64_t n);
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
-void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s);
+// chunks of the Kronecker terms per candidate in the FP64 re-evaluation (<= 64)
+int dd_eval_chunks(int n_cuts);
+void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* part, double* val, cudaStream_t s);
 
 // k_bwd.cu
 struct BwdEdges {   // edges as pairs of index bits (least significant = 0)

@@ -8,7 +8,9 @@
 // Sec. 4.2) by a stable compaction of the inner index.  The epilogue deposits
 // (m, n) into the output index g = depA(m) + depB(n) (the Kronecker product's
 // bit interleave; qubit 0 = most significant bit) and accumulates sum_x p(x)
-// in FP64.
+// in FP64.  Register-tiled GEMM in general; a matrix-vector form when one side
+// has at most 8 outputs (k_cc_skinny), which is then bound by reading the
+// other side once.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -404,6 +406,138 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
   }
 }
 
+// Skinny contraction: one operand has NS <= 8 outputs (for example a
+// subcircuit whose qubits are all merged), so the work is a batch of
+// matrix-vector products bound by reading the long operand L once.  A thread
+// owns W consecutive long outputs and all NS short ones; per pass the block
+// stages 256 of the batch's kept row pairs (the short operand's values and the
+// long operand's row numbers) in shared memory.  `swap`: A is the short side.
+template <typename T, int NS>
+__global__ __launch_bounds__(256) void k_cc_skinny(const CCArgs<T> a, int swap) {
+  constexpr int W = Vec<T>::W;
+  constexpr int KT = 256;
+  using V = typename Vec<T>::type;
+  __shared__ T Ss[KT][NS];
+  __shared__ int32_t Rl[KT];
+  __shared__ double red[8];
+  const int tid = threadIdx.x, batch = blockIdx.y;
+  const T* L = swap ? a.B : a.A;
+  const T* S = swap ? a.A : a.B;
+  const int64_t ML = swap ? a.N : a.M;
+  const int32_t* rA = a.crow + (int64_t)batch * 2 * a.kmax;
+  const int32_t* rB = rA + a.kmax;
+  const int32_t* rl = swap ? rB : rA;
+  const int32_t* rs = swap ? rA : rB;
+  const int kc = a.kcount[batch];
+  const int64_t m0 = ((int64_t)blockIdx.x * 256 + tid) * W;
+  T acc[W][NS];
+#pragma unroll
+  for (int w = 0; w < W; ++w)
+#pragma unroll
+    for (int n = 0; n < NS; ++n) acc[w][n] = T(0);
+  for (int k0 = 0; k0 < kc; k0 += KT) {
+    __syncthreads();
+    for (int i = tid; i < KT * NS; i += 256) {
+      const int k = i / NS, n = i % NS;
+      Ss[k][n] = k0 + k < kc ? S[(int64_t)rs[k0 + k] * NS + n] : T(0);
+    }
+    for (int i = tid; i < KT; i += 256) Rl[i] = k0 + i < kc ? rl[k0 + i] : 0;
+    __syncthreads();
+    const int kn = min(KT, kc - k0);
+    if (m0 < ML) {
+#pragma unroll 8
+      for (int k = 0; k < kn; ++k) {
+        const V v = __ldcs(reinterpret_cast<const V*>(L + (int64_t)Rl[k] * ML + m0));
+        const T* vp = reinterpret_cast<const T*>(&v);
+#pragma unroll
+        for (int w = 0; w < W; ++w)
+#pragma unroll
+          for (int n = 0; n < NS; ++n) acc[w][n] = fma(vp[w], Ss[k][n], acc[w][n]);
+      }
+    }
+  }
+  double local = 0.0;
+  if (m0 < ML) {
+    T* out = a.out + (uint64_t)batch * a.out_batch_stride;
+    const uint64_t* depL = swap ? a.depB : a.depA;
+    const uint64_t* depS = swap ? a.depA : a.depB;
+    const int nbL = swap ? a.nbB : a.nbA, nbS = swap ? a.nbA : a.nbB;
+    uint64_t gS[NS];
+#pragma unroll
+    for (int n = 0; n < NS; ++n) gS[n] = deposit(depS, nbS, (uint64_t)n);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const uint64_t gL = deposit(depL, nbL, (uint64_t)(m0 + w));
+      T v[NS];
+#pragma unroll
+      for (int n = 0; n < NS; ++n) {
+        v[n] = acc[w][n] * a.scale;
+        out[gL + gS[n]] = v[n];
+      }
+#pragma unroll
+      for (int h = NS / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int n = 0; n < h; ++n) v[n] += v[n + h];
+      local += (double)v[0];
+    }
+  }
+  if (a.sum) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+    if ((tid & 31) == 0) red[tid >> 5] = local;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0;
+      for (int w = 0; w < 8; ++w) t += red[w];
+      atomicAdd(a.sum, t);
+    }
+  }
+}
+
+template <typename T>
+CCArgs<T> cc_args(const Contraction& c) {
+  CCArgs<T> a;
+  a.A = static_cast<const T*>(c.A);
+  a.B = static_cast<const T*>(c.B);
+  a.M = int64_t(1) << c.fA;
+  a.N = int64_t(1) << c.fB;
+  a.kmax = c.kmax;
+  a.crow = c.crow;
+  a.kcount = c.kcount;
+  a.depA = c.depA;
+  a.depB = c.depB;
+  a.nbA = (c.fA + 7) / 8;
+  a.nbB = (c.fB + 7) / 8;
+  a.out_batch_stride = c.out_batch_stride;
+  a.out = static_cast<T*>(c.out);
+  a.scale = T(c.scale);
+  a.sum = c.sum;
+  a.vecB = c.vecB;
+  a.tilesN = 1;
+  return a;
+}
+
+template <typename T>
+void launch_skinny(const Contraction& c, cudaStream_t s) {
+  const CCArgs<T> a = cc_args<T>(c);
+  const int swap = c.fA < c.fB ? 1 : 0;
+  const int fS = swap ? c.fA : c.fB;
+  const int64_t ML = int64_t(1) << (swap ? c.fB : c.fA);
+  constexpr int W = Vec<T>::W;
+  const dim3 grid((unsigned)((ML + 256 * W - 1) / (256 * W)), (unsigned)c.batch);
+  cudaEvent_t ev = nullptr;
+  if (c.profile) prof_begin(s, &ev);
+  switch (fS) {
+    case 0: k_cc_skinny<T, 1><<<grid, 256, 0, s>>>(a, swap); break;
+    case 1: k_cc_skinny<T, 2><<<grid, 256, 0, s>>>(a, swap); break;
+    case 2: k_cc_skinny<T, 4><<<grid, 256, 0, s>>>(a, swap); break;
+    default: k_cc_skinny<T, 8><<<grid, 256, 0, s>>>(a, swap); break;
+  }
+  count_launch();
+  check_launch("k_cc_skinny");
+  if (c.profile) prof_end(s, ev);
+}
+
 template <typename T, int BM, int BN, int BK>
 void launch_typed(const Contraction& c, cudaStream_t s) {
   CCArgs<T> a;
@@ -471,7 +605,16 @@ void launch_compact(const Contraction& c, cudaStream_t s) {
   check_launch("k_compact");
 }
 
+bool cc_is_skinny(int fA, int fB) { return std::min(fA, fB) <= 3 && std::max(fA, fB) >= 9; }
+
 void launch_cc_gemm(const Contraction& c, cudaStream_t s) {
+  if (cc_is_skinny(c.fA, c.fB)) {
+    if (c.dtype == CUTQC_F64)
+      launch_skinny<double>(c, s);
+    else
+      launch_skinny<float>(c, s);
+    return;
+  }
   if (c.dtype == CUTQC_F64)
     launch_typed<double, 64, 64, 8>(c, s);
   else

@@ -7,19 +7,21 @@
 //   When the merged qubits are the lowest output bits (the usual case) each
 //   output is a contiguous run read with 16-byte loads; otherwise, with >= 32
 //   merged values per output, a warp owns an output (lanes stride the merged
-//   index).  Runs of up to 32 values are summed pairwise in FP32 and folded
-//   into FP64; the FP64 sums are kept for the bin ranking.
+//   index).  FP32 tensors are summed in compensated FP32 (runs of up to 32
+//   values plainly, then TwoSum); the rounded sum feeds the contraction and
+//   the compensation term is kept for the FP64 bin ranking.
 // k_topk_warps / k_topk_final: the 32 heaviest bins by their stored value
 //   (ties to the lower index): every warp keeps a sorted list of 32 across its
 //   lanes and inserts only values above its current minimum (ballot + shuffle);
 //   a single block merges the warp lists.
-// k_dd_gather64 / k_dd_eval: FP64 values of the candidate bins: the merge
-//   kernels also keep their sums in FP64 (each run accumulated in FP64), the
-//   candidate's merged values are gathered from there, then
-//   2^-K sum_e prod_c M64_c[row_c(e)] in FP64.
+// k_dd_gather64 / k_dd_eval: FP64 values of the candidate bins: the
+//   candidate's merged values (rounded sum + compensation) are gathered in
+//   FP64, then 2^-K sum_e prod_c M64_c[row_c(e)] in FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cfloat>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -33,11 +35,48 @@ __device__ __forceinline__ uint64_t dep_tab(const uint64_t* __restrict__ tab, in
   return g;
 }
 
+// Compensated FP32 accumulation: a value is carried as s + c, s the rounded
+// sum and c the accumulated rounding error.  ff_add is Knuth's TwoSum (the
+// error of s = a + b is recovered exactly with six FP32 operations) plus the
+// sum of the incoming error terms; ff_norm moves the error into s once at the
+// end (Fast2Sum), so fl(s) is the rounded result and s + c holds the extra
+// bits.  All of it runs on the FP32 pipes, which on this GPU outrun the FP64
+// pipe by far more than the six-fold operation count.
+struct FF {
+  float s, c;
+};
+
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = a.s + b.s;
+  const float bb = s - a.s;
+  const float err = (a.s - (s - bb)) + (b.s - bb);
+  return {s, (a.c + b.c) + err};
+}
+
+__device__ __forceinline__ FF ff_norm(FF a) {
+  const float s = a.s + a.c;
+  return {s, a.c - (s - a.s)};
+}
+
+__device__ __forceinline__ FF ff_shfl_xor(FF a, int off) {
+  return {__shfl_xor_sync(0xffffffffu, a.s, off), __shfl_xor_sync(0xffffffffu, a.c, off)};
+}
+
+__device__ __forceinline__ void store_merged(float* out, float* outc, int64_t o, FF v) {
+  v = ff_norm(v);
+  out[o] = v.s;
+  outc[o] = v.c;
+}
+__device__ __forceinline__ void store_merged(double* out, float*, int64_t o, double v) { out[o] = v; }
+
+// Generic merge: a warp owns an output when there are >= 32 merged values;
+// lanes stride the merged index and sum runs of 16 in the tensor's type.
 template <typename T>
 __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, int mg,
                                 const uint64_t* __restrict__ depAct, int nbA, const uint64_t* __restrict__ depMrg,
-                                int nbM, uint64_t zoom, T* __restrict__ out, double* __restrict__ out64,
+                                int nbM, uint64_t zoom, T* __restrict__ out, float* __restrict__ outc,
                                 int64_t n_out) {
+  using Acc = typename std::conditional<sizeof(T) == 4, FF, double>::type;
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -46,7 +85,7 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
     const int64_t row = o >> a;
     const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
     const T* base = Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom);
-    double acc = 0.0;
+    Acc acc{};
     for (int64_t x0 = lane; x0 < nm; x0 += 32 * 16) {
       T run = T(0);
 #pragma unroll 4
@@ -54,92 +93,155 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
         const int64_t xm = x0 + 32 * r;
         if (xm < nm) run += base[dep_tab(depMrg, nbM, (uint64_t)xm)];
       }
-      acc += (double)run;
+      if constexpr (sizeof(T) == 4)
+        acc = ff_add(acc, FF{run, 0.0f});
+      else
+        acc += run;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) {
-      out[o] = (T)acc;
-      out64[o] = acc;
+    for (int off = 16; off > 0; off >>= 1) {
+      if constexpr (sizeof(T) == 4)
+        acc = ff_add(acc, ff_shfl_xor(acc, off));
+      else
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
     }
+    if (lane == 0) store_merged(out, outc, o, acc);
   }
 }
 
+// Generic merge with < 32 merged values: a thread per output.
 template <typename T>
 __global__ void k_dd_merge_thread(const T* __restrict__ Tin, int64_t cols, int a, int mg,
                                   const uint64_t* __restrict__ depAct, int nbA,
                                   const uint64_t* __restrict__ depMrg, int nbM, uint64_t zoom,
-                                  T* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
+                                  T* __restrict__ out, float* __restrict__ outc, int64_t n_out) {
   const int nm = 1 << mg;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out; o += (int64_t)gridDim.x * blockDim.x) {
     const int64_t row = o >> a;
     const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
     const T* base = Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom);
-    T acc = T(0);
-    for (int xm = 0; xm < nm; ++xm) acc += base[dep_tab(depMrg, nbM, (uint64_t)xm)];
-    out[o] = acc;
-    out64[o] = (double)acc;
+    if constexpr (sizeof(T) == 4) {
+      FF acc{};
+      for (int xm = 0; xm < nm; ++xm) acc = ff_add(acc, FF{base[dep_tab(depMrg, nbM, (uint64_t)xm)], 0.0f});
+      store_merged(out, outc, o, acc);
+    } else {
+      T acc = T(0);
+      for (int xm = 0; xm < nm; ++xm) acc += base[dep_tab(depMrg, nbM, (uint64_t)xm)];
+      out[o] = acc;
+    }
   }
 }
 
 // Merged qubits on the lowest output bits: every output sums one contiguous
-// run of 2^mg values.  Thread per output for runs of 4..256 values (16-byte
-// loads, pairwise FP32 over groups of 32, FP64 across groups), warp per
-// output for longer runs.
+// run of 2^mg FP32 values.  A group of G = min(32, 2^mg / 4) lanes owns an
+// output and reads its run with 16-byte loads, lane j taking float4 j, j + G,
+// ... (one warp instruction covers 32 consecutive float4 of one run, or
+// several whole runs).  With runs of at most 1024 values (PER = float4 per
+// lane <= 8) a group takes 8 / PER outputs per step, so every lane has 8
+// independent loads in flight.  Sums cover up to 32 values in plain FP32
+// (pairwise), everything above in compensated FP32.  `dense`: the active bits
+// are the bits directly above the merged ones, so a run starts at
+// row * cols + zoom + (xa << mg) without the deposit table.  Outputs too few
+// to fill the GPU are split into 2^lnch chunks whose partial sums go to
+// `part` and are combined in chunk order by k_dd_merge_finish.
 __device__ __forceinline__ float sum4(float4 v) { return (v.x + v.y) + (v.z + v.w); }
 
-__global__ void k_dd_merge_run_thread(const float* __restrict__ Tin, int64_t cols, int a, int mg,
-                                      const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom,
-                                      float* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
-  const int ng = 1 << (mg - 2);   // float4 groups in the run
-  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_out; o += (int64_t)gridDim.x * blockDim.x) {
+template <int G, int PER>
+__global__ void k_dd_merge_run(const float* __restrict__ Tin, int64_t cols, int a, int mg,
+                               const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom, int dense, int lnch,
+                               float* __restrict__ out, float* __restrict__ outc, float2* __restrict__ part,
+                               int64_t n_out) {
+  constexpr int GPW = 32 / G;                    // groups per warp
+  constexpr int U = PER == 0 ? 1 : 8 / PER;      // outputs per group per step
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1), gi = lane / G;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n_units = n_out << lnch;
+  const int64_t per = (int64_t(1) << (mg - 2 - lnch)) / G;   // float4 per lane in one chunk
+  const uint64_t amask = (uint64_t(1) << a) - 1;
+  const int64_t chmask = (int64_t(1) << lnch) - 1;
+  auto unit_ptr = [&](int64_t u) {
+    const int64_t o = u >> lnch, ch = u & chmask;
     const int64_t row = o >> a;
-    const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
-    const float4* p = reinterpret_cast<const float4*>(Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom));
-    double acc = 0.0;
-    for (int g0 = 0; g0 < ng; g0 += 8) {
-      float t8[8];
+    const uint64_t xa = (uint64_t)o & amask;
+    const uint64_t off = dense ? zoom + (xa << mg) : (dep_tab(depAct, nbA, xa) | zoom);
+    return reinterpret_cast<const float4*>(Tin + row * cols + off) + ch * per * G + gl;
+  };
+  for (int64_t ub = warp * GPW * U; ub < n_units; ub += nwarps * GPW * U) {
+    FF acc[U];
+    if constexpr (PER > 0) {
+      float t[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) t8[j] = g0 + j < ng ? sum4(p[g0 + j]) : 0.0f;
+      for (int k = 0; k < U; ++k) {
+        const int64_t u = ub + k * GPW + gi;
+        const bool ok = u < n_units;
+        const float4* p = unit_ptr(ok ? u : 0);
 #pragma unroll
-      for (int w = 4; w > 0; w >>= 1)
+        for (int e = 0; e < PER; ++e) t[k * PER + e] = ok ? sum4(__ldcs(p + e * G)) : 0.0f;
+      }
 #pragma unroll
-        for (int j = 0; j < w; ++j) t8[j] += t8[j + w];
-      acc += (double)t8[0];
+      for (int w = 1; w < PER; w <<= 1)
+#pragma unroll
+        for (int j = 0; j < 8; j += 2 * w) t[j] += t[j + w];
+#pragma unroll
+      for (int k = 0; k < U; ++k) acc[k] = FF{t[k * PER], 0.0f};
+    } else {
+      const int64_t u = ub + gi;
+      acc[0] = FF{0.0f, 0.0f};
+      if (u < n_units) {
+        const float4* p = unit_ptr(u);
+        for (int64_t j0 = 0; j0 < per; j0 += 8) {   // per is a power of two >= 16 here
+          float t[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = sum4(__ldcs(p + (j0 + j) * G));
+#pragma unroll
+          for (int w = 4; w > 0; w >>= 1)
+#pragma unroll
+            for (int j = 0; j < w; ++j) t[j] += t[j + w];
+          acc[0] = ff_add(acc[0], FF{t[0], 0.0f});
+        }
+      }
     }
-    out[o] = (float)acc;
-    out64[o] = acc;
+    // across the group: plain FP32 while a partial covers <= 32 values
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (PER > 0 && 8 * PER * off <= 32)
+          acc[k].s += __shfl_xor_sync(0xffffffffu, acc[k].s, off);
+        else
+          acc[k] = ff_add(acc[k], ff_shfl_xor(acc[k], off));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t u = ub + k * GPW + gi;
+      if (gl == 0 && u < n_units) {
+        if (lnch == 0)
+          store_merged(out, outc, u, acc[k]);
+        else
+          part[u] = make_float2(acc[k].s, acc[k].c);
+      }
+    }
   }
 }
 
-__global__ void k_dd_merge_run_warp(const float* __restrict__ Tin, int64_t cols, int a, int mg,
-                                    const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom,
-                                    float* __restrict__ out, double* __restrict__ out64, int64_t n_out) {
+// warp per output: lanes take chunks lane, lane + 32, ... of its partial sums
+__global__ void k_dd_merge_finish(const float2* __restrict__ part, int lnch, float* __restrict__ out,
+                                  float* __restrict__ outc, int64_t n_out) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t ng = int64_t(1) << (mg - 2);
+  const int64_t nch = int64_t(1) << lnch;
   for (int64_t o = warp; o < n_out; o += nwarps) {
-    const int64_t row = o >> a;
-    const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
-    const float4* p = reinterpret_cast<const float4*>(Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom));
-    double acc = 0.0;
-    for (int64_t g0 = lane; g0 < ng; g0 += 32 * 8) {
-      float t8[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) t8[j] = g0 + 32 * j < ng ? sum4(p[g0 + 32 * j]) : 0.0f;
-#pragma unroll
-      for (int w = 4; w > 0; w >>= 1)
-#pragma unroll
-        for (int j = 0; j < w; ++j) t8[j] += t8[j + w];
-      acc += (double)t8[0];
+    FF acc{};
+    for (int64_t c = lane; c < nch; c += 32) {
+      const float2 v = part[(o << lnch) + c];
+      acc = ff_add(acc, FF{v.x, v.y});
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) {
-      out[o] = (float)acc;
-      out64[o] = acc;
-    }
+    for (int off = 16; off > 0; off >>= 1) acc = ff_add(acc, ff_shfl_xor(acc, off));
+    if (lane == 0) store_merged(out, outc, o, acc);
   }
 }
 
@@ -202,6 +304,66 @@ __global__ void k_topk_warps(const T* __restrict__ bins, int64_t n, int64_t per_
   ci[warp * KC + lane] = li;
 }
 
+// FP32 bins, 16-byte aligned, n a multiple of 4: each lane loads 4 float4 per
+// step (512 consecutive values per warp), candidates filtered by the exact (value, index)
+// order so the insertion order does not matter; at the end warp 0 of each
+// block merges its warps' lists, so one list of KC per block is written.
+__global__ void k_topk_warps4(const float4* __restrict__ bins4, int64_t n, int64_t per_warp,
+                              float* __restrict__ cv, int64_t* __restrict__ ci) {
+  __shared__ float sv[8 * KC];
+  __shared__ int64_t si[8 * KC];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  float lv = -FLT_MAX;
+  int64_t li = INT64_MAX;
+  const int64_t lo = warp * per_warp, hi = min(n, lo + per_warp);
+  for (int64_t b0 = lo; b0 < hi; b0 += 512) {
+    float v[16];
+    int64_t i0[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      i0[h] = b0 + 128 * h + 4 * lane;
+      const float4 q = i0[h] < hi ? __ldcs(bins4 + (i0[h] >> 2)) : make_float4(-FLT_MAX, -FLT_MAX, -FLT_MAX, -FLT_MAX);
+      v[4 * h + 0] = q.x;
+      v[4 * h + 1] = q.y;
+      v[4 * h + 2] = q.z;
+      v[4 * h + 3] = q.w;
+    }
+#pragma unroll
+    for (int u = 0; u < 16; ++u) {
+      const int64_t i = i0[u >> 2] + (u & 3);
+      const float tv = __shfl_sync(0xffffffffu, lv, 31);
+      const int64_t ti = __shfl_sync(0xffffffffu, li, 31);
+      unsigned m = __ballot_sync(0xffffffffu, i < hi && before(v[u], i, tv, ti));
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        warp_insert(lv, li, __shfl_sync(0xffffffffu, v[u], src), __shfl_sync(0xffffffffu, i, src), lane);
+      }
+    }
+  }
+  sv[w * KC + lane] = lv;
+  si[w * KC + lane] = li;
+  __syncthreads();
+  if (w == 0) {
+    lv = -FLT_MAX;
+    li = INT64_MAX;
+    for (int j0 = 0; j0 < (int)(blockDim.x >> 5) * KC; j0 += 32) {
+      const float v = sv[j0 + lane];
+      const int64_t idx = si[j0 + lane];
+      unsigned m = __ballot_sync(0xffffffffu, before(v, idx, __shfl_sync(0xffffffffu, lv, 31),
+                                                      __shfl_sync(0xffffffffu, li, 31)));
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        warp_insert(lv, li, __shfl_sync(0xffffffffu, v, src), __shfl_sync(0xffffffffu, idx, src), lane);
+      }
+    }
+    cv[(int64_t)blockIdx.x * KC + lane] = lv;
+    ci[(int64_t)blockIdx.x * KC + lane] = li;
+  }
+}
+
 // one block of 1024 threads merges `m` candidate pairs into the best KC
 __global__ void k_topk_final(const float* __restrict__ cv, const int64_t* __restrict__ ci, int64_t m,
                              float* __restrict__ ov, int64_t* __restrict__ oi) {
@@ -245,8 +407,9 @@ __global__ void k_topk_final(const float* __restrict__ cv, const int64_t* __rest
 }
 
 // ---- FP64 re-evaluation of candidate bins ----------------------------------
-// M64[cand][c][row] = the FP64 merged value of subcircuit c at the candidate's
-// active bits (gathered from the merge kernels' FP64 output).  grid: (cand, c).
+// M64[cand][c][row] = the merged value of subcircuit c at the candidate's
+// active bits in FP64: the FP64 merged tensor, or for FP32 tensors the merge's
+// rounded sum plus its compensation term.  grid: (cand, c).
 __global__ void k_dd_gather64(const DdEvalArgs a, double* __restrict__ m64) {
   const int cand = blockIdx.x, c = blockIdx.y;
   const DdEvalSub& s = a.sub[c];
@@ -258,17 +421,24 @@ __global__ void k_dd_gather64(const DdEvalArgs a, double* __restrict__ m64) {
     const uint64_t bit = (bin >> (a.n_active - 1 - s.act_rank[i])) & 1;
     xa |= bit << (s.a - 1 - i);
   }
-  for (int64_t row = threadIdx.x; row < s.rows; row += blockDim.x)
-    m64[((int64_t)cand * a.n_sub + c) * a.max_rows + row] = s.m64[(row << s.a) + xa];
+  for (int64_t row = threadIdx.x; row < s.rows; row += blockDim.x) {
+    const int64_t i = (row << s.a) + xa;
+    m64[((int64_t)cand * a.n_sub + c) * a.max_rows + row] =
+        a.f64 ? static_cast<const double*>(s.m)[i] : (double)static_cast<const float*>(s.m)[i] + (double)s.mc[i];
+  }
 }
 
-// value[cand] = 2^-K sum_e prod_c M64[cand][c][row_c(e)].  grid: cand, block 256.
-__global__ void k_dd_eval(const DdEvalArgs a, const double* __restrict__ m64, double* __restrict__ val) {
-  const int cand = blockIdx.x;
+// part[cand][chunk] = sum over the chunk's terms e of prod_c M64[cand][c][row_c(e)];
+// grid: (cand, chunk), block 256.  k_dd_eval_final adds the chunks in order and
+// scales by 2^-K.
+__global__ void k_dd_eval(const DdEvalArgs a, const double* __restrict__ m64, int nchunk,
+                          double* __restrict__ part) {
+  const int cand = blockIdx.x, chunk = blockIdx.y;
   __shared__ double red[8];
   const int64_t nterms = int64_t(1) << (2 * a.n_cuts);
+  const int64_t per = nterms / nchunk;
   double acc = 0.0;
-  for (int64_t e = threadIdx.x; e < nterms; e += blockDim.x) {
+  for (int64_t e = chunk * per + threadIdx.x; e < (chunk + 1) * per; e += blockDim.x) {
     double prod = 1.0;
     for (int c = 0; c < a.n_sub; ++c) {
       const DdEvalSub& s = a.sub[c];
@@ -285,8 +455,17 @@ __global__ void k_dd_eval(const DdEvalArgs a, const double* __restrict__ m64, do
   if (threadIdx.x == 0) {
     double tot = 0.0;
     for (int w = 0; w < 8; ++w) tot += red[w];
-    val[cand] = tot * a.scale;
+    part[cand * nchunk + chunk] = tot;
   }
+}
+
+__global__ void k_dd_eval_final(const double* __restrict__ part, int n_cand, int nchunk, double scale,
+                                double* __restrict__ val) {
+  const int cand = threadIdx.x;
+  if (cand >= n_cand) return;
+  double tot = 0.0;
+  for (int c = 0; c < nchunk; ++c) tot += part[cand * nchunk + c];
+  val[cand] = tot * scale;
 }
 
 unsigned grid_for(int64_t work, int per_block) {
@@ -295,37 +474,80 @@ unsigned grid_for(int64_t work, int per_block) {
   return (unsigned)(g < 1 ? 1 : g);
 }
 
+template <int G, int PER>
+void launch_run(const float* T, int64_t cols, int a, int mg, const uint64_t* depAct, int nbA, uint64_t zoom,
+                int dense, int lnch, float* M, float* MC, float2* part, int64_t n_out, cudaStream_t s) {
+  constexpr int U = PER == 0 ? 1 : 8 / PER;
+  const int64_t threads = ((n_out << lnch) + U - 1) / U * G;
+  k_dd_merge_run<G, PER><<<grid_for(threads, 256), 256, 0, s>>>(T, cols, a, mg, depAct, nbA, zoom, dense, lnch, M,
+                                                                 MC, part, n_out);
+}
+
 }  // namespace
 
+int dd_merge_chunks(int64_t rows, int a, int mg) {
+  if (mg < 2) return 0;
+  const int64_t ng = int64_t(1) << (mg - 2), G = std::min<int64_t>(32, ng), n_out = rows << a;
+  int lnch = 0;
+  while ((n_out << lnch) * G < 152 * 2048 && (ng >> (lnch + 1)) >= 8 * G) ++lnch;
+  return lnch;
+}
+
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
-                     const uint64_t* depMrg, uint64_t zoom, bool run, void* M, double* M64, cudaStream_t s) {
+                     const uint64_t* depMrg, uint64_t zoom, bool run, bool dense_bits, void* M, float* MC,
+                     void* part, cudaStream_t s) {
   const int64_t n_out = rows << a;
   const int64_t cols = int64_t(1) << f;
   const int nbA = (a + 7) / 8, nbM = (mg + 7) / 8;
-  run = run && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
-  if (run && dtype == CUTQC_F32 && mg >= 2 && mg <= 8) {
-    k_dd_merge_run_thread<<<grid_for(n_out, 256), 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct,
-                                                                nbA, zoom, static_cast<float*>(M), M64, n_out);
-  } else if (run && dtype == CUTQC_F32 && mg > 8) {
-    k_dd_merge_run_warp<<<grid_for(n_out * 32, 256), 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg,
-                                                                   depAct, nbA, zoom, static_cast<float*>(M), M64,
-                                                                   n_out);
+  run = run && dtype == CUTQC_F32 && mg >= 2 && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
+  if (run) {
+    const int lnch = dd_merge_chunks(rows, a, mg);
+    const int dense = dense_bits ? 1 : 0;
+    const float* Tf = static_cast<const float*>(T);
+    float* Mf = static_cast<float*>(M);
+    float2* pf = static_cast<float2*>(part);
+    const int G = std::min(32, 1 << std::min(mg - 2, 5));
+    const int64_t per = (int64_t(1) << (mg - 2 - lnch)) / G;
+#define CUTQC_RUN(g, q) launch_run<g, q>(Tf, cols, a, mg, depAct, nbA, zoom, dense, lnch, Mf, MC, pf, n_out, s)
+    if (G < 32) {
+      switch (G) {
+        case 1: CUTQC_RUN(1, 1); break;
+        case 2: CUTQC_RUN(2, 1); break;
+        case 4: CUTQC_RUN(4, 1); break;
+        case 8: CUTQC_RUN(8, 1); break;
+        default: CUTQC_RUN(16, 1); break;
+      }
+    } else {
+      switch (per) {
+        case 1: CUTQC_RUN(32, 1); break;
+        case 2: CUTQC_RUN(32, 2); break;
+        case 4: CUTQC_RUN(32, 4); break;
+        case 8: CUTQC_RUN(32, 8); break;
+        default: CUTQC_RUN(32, 0); break;
+      }
+    }
+#undef CUTQC_RUN
+    if (lnch > 0) {
+      count_launch();
+      check_launch("k_dd_merge_run");
+      k_dd_merge_finish<<<grid_for(n_out * 32, 256), 256, 0, s>>>(pf, lnch, Mf, MC, n_out);
+    }
   } else if (mg >= 5) {
     const unsigned g = grid_for(n_out * 32, 256);
     if (dtype == CUTQC_F64)
       k_dd_merge_warp<double><<<g, 256, 0, s>>>(static_cast<const double*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                                zoom, static_cast<double*>(M), M64, n_out);
+                                                zoom, static_cast<double*>(M), nullptr, n_out);
     else
       k_dd_merge_warp<float><<<g, 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                               zoom, static_cast<float*>(M), M64, n_out);
+                                               zoom, static_cast<float*>(M), MC, n_out);
   } else {
     const unsigned g = grid_for(n_out, 256);
     if (dtype == CUTQC_F64)
       k_dd_merge_thread<double><<<g, 256, 0, s>>>(static_cast<const double*>(T), cols, a, mg, depAct, nbA, depMrg,
-                                                  nbM, zoom, static_cast<double*>(M), M64, n_out);
+                                                  nbM, zoom, static_cast<double*>(M), nullptr, n_out);
     else
       k_dd_merge_thread<float><<<g, 256, 0, s>>>(static_cast<const float*>(T), cols, a, mg, depAct, nbA, depMrg, nbM,
-                                                 zoom, static_cast<float*>(M), M64, n_out);
+                                                 zoom, static_cast<float*>(M), MC, n_out);
   }
   count_launch();
   check_launch("k_dd_merge");
@@ -337,31 +559,54 @@ size_t topk_workspace_bytes(int64_t n) {
 }
 
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s) {
-  const int64_t warps_max = 152 * 8 * 4;
-  int64_t per_warp = ((n + warps_max - 1) / warps_max + 127) / 128 * 128;
-  if (per_warp < 128) per_warp = 128;
-  const int64_t warps = (n + per_warp - 1) / per_warp;
-  const unsigned blocks = (unsigned)((warps + 7) / 8);
+  const int64_t lists_max = 152 * 8 * 4;   // capacity of the workspace in lists of KC
   float* cv = static_cast<float*>(ws);
-  int64_t* ci = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + (size_t)warps_max * KC * 4);
-  if (dtype == CUTQC_F64)
-    k_topk_warps<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(bins), n, per_warp, cv, ci);
-  else
-    k_topk_warps<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(bins), n, per_warp, cv, ci);
+  int64_t* ci = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + (size_t)lists_max * KC * 4);
+  int64_t lists;
+  if (dtype == CUTQC_F32 && n % 4 == 0 && (reinterpret_cast<uintptr_t>(bins) & 15) == 0) {
+    // up to 64 warps per SM, one list per block of 8 warps
+    const int64_t warps_max = 152 * 64;
+    int64_t per_warp = ((n + warps_max - 1) / warps_max + 511) / 512 * 512;
+    const int64_t warps = (n + per_warp - 1) / per_warp;
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    k_topk_warps4<<<blocks, 256, 0, s>>>(static_cast<const float4*>(bins), n, per_warp, cv, ci);
+    lists = blocks;
+  } else {
+    const int64_t warps_max = lists_max;
+    int64_t per_warp = ((n + warps_max - 1) / warps_max + 127) / 128 * 128;
+    if (per_warp < 128) per_warp = 128;
+    const int64_t warps = (n + per_warp - 1) / per_warp;
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
+    if (dtype == CUTQC_F64)
+      k_topk_warps<double><<<blocks, 256, 0, s>>>(static_cast<const double*>(bins), n, per_warp, cv, ci);
+    else
+      k_topk_warps<float><<<blocks, 256, 0, s>>>(static_cast<const float*>(bins), n, per_warp, cv, ci);
+    lists = (int64_t)blocks * 8;
+  }
   count_launch();
   check_launch("k_topk_warps");
-  k_topk_final<<<1, 1024, 0, s>>>(cv, ci, (int64_t)blocks * 8 * KC, out_v, out_i);
+  k_topk_final<<<1, 1024, 0, s>>>(cv, ci, lists * KC, out_v, out_i);
   count_launch();
   check_launch("k_topk_final");
 }
 
-void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* val, cudaStream_t s) {
+int dd_eval_chunks(int n_cuts) {
+  const int64_t nterms = int64_t(1) << (2 * n_cuts);
+  int64_t c = nterms / 2048;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(64, c));
+}
+
+void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* part, double* val, cudaStream_t s) {
   k_dd_gather64<<<dim3(a.n_cand, a.n_sub), 256, 0, s>>>(a, m64);
   count_launch();
   check_launch("k_dd_gather64");
-  k_dd_eval<<<a.n_cand, 256, 0, s>>>(a, m64, val);
+  const int nchunk = dd_eval_chunks(a.n_cuts);
+  k_dd_eval<<<dim3(a.n_cand, nchunk), 256, 0, s>>>(a, m64, nchunk, part);
   count_launch();
   check_launch("k_dd_eval");
+  k_dd_eval_final<<<1, 32, 0, s>>>(part, a.n_cand, nchunk, a.scale, val);
+  count_launch();
+  check_launch("k_dd_eval_final");
 }
 
 }  // namespace cutqc

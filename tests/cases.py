@@ -15,7 +15,13 @@ SMALL = {
     "grid4x5_k5": lambda: C.grid_blocks(4, 5, 8, 2, 1, 2, 5, 13),            # multi-tile, 2 subcircuits
     "hwea16_s2": lambda: C.chain_blocks(C.hwea(16, 4), 2),                   # 2^8 x 2^8 tiles
     "nocut6": lambda: C.cut_circuit(C.hwea(6, 4), [0] * 6),                  # S = 1, K = 0
+    "hwea14_skinny": lambda: C.cut_circuit(C.hwea(14, 6), [0] * 11 + [1] * 3),  # 2^11 x 2^3 outputs
 }
+
+
+def hwea22_chain():
+    """22-qubit HWEA cut once between qubits 10 and 11 (2 subcircuits, K = 1)."""
+    return C.chain_blocks(C.hwea(22, 5), 2)
 
 
 def supremacy_4x6():

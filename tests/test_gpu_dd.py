@@ -138,3 +138,24 @@ def test_dd_80q_full_size(env):
             assert total == pytest.approx(top[pr][pb], abs=1e-6 + 1e-4 * top[pr][pb])
     del st, ts
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n_active", [1, 3])
+def test_dd_long_merged_runs(env, n_active):
+    """Few active qubits on the 24-qubit supremacy-grid workload: the merged
+    qubits of each subcircuit form runs of 2^9 .. 2^12 values over only 256
+    .. 2048 outputs, so the contiguous-run merge splits each run into chunks
+    and adds their FP64 partial sums in a second pass."""
+    cc, T = oracle_case("sup4x6", cases.supremacy_4x6)
+    check_run(env, cc, T, np.float32, "auto", n_active, 4, "bfs", 1e-6)
+
+
+@pytest.mark.parametrize("dtype_np,algo,tol", [(np.float32, "auto", 1e-6), (np.float64, "cc", 1e-12)])
+@pytest.mark.parametrize("n_active", [10, 11, 12])
+def test_dd_skinny_contraction(env, n_active, dtype_np, algo, tol):
+    """A 22-qubit HWEA chain cut once into qubits 0..10 and 11..21 with the
+    first 10 .. 12 qubits active: one subcircuit keeps 2^10 .. 2^11 active
+    outputs, the other 1 or 2, so the contraction is a batch of matrix-vector
+    products (the skinny CUDA-core form, both operand orders)."""
+    cc, T = oracle_case("hwea22_s2", cases.hwea22_chain)
+    check_run(env, cc, T, dtype_np, algo, n_active, 3, "bfs", tol)
