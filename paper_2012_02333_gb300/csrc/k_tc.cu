@@ -26,10 +26,10 @@
 //              columns between two warps per quarter): tcgen05.ld of their 32
 //              TMEM lanes (lane = row),
 //              scale by 2^-K, deposit (m, n) into the output index with the
-//              additive per-bit tables held in registers, 16-byte streaming
-//              stores (runs of consecutive columns that are consecutive in
-//              the output), FP64 partial sums; it drains one accumulator
-//              while the MMA fills the other.
+//              additive per-bit tables held in registers, restage 16 x 32
+//              blocks through shared memory so 16-byte streaming stores go
+//              out in output-address order, FP64 partial sums; it drains one
+//              accumulator while the MMA fills the other.
 // Every wait on an mbarrier is bounded (2 s); on timeout the kernel raises an
 // abort flag, records a status word, lets in-flight copies land and frees TMEM.
 #include <cuda.h>
@@ -58,7 +58,12 @@ constexpr int STAGE_AREA = 3 * 3 * (A_PIECE + B_PIECE);   // 216 KiB: 3 stages o
 constexpr int TMEM_COLS = 512;
 constexpr int EPI_WARPS = 4;                  // one per TMEM lane quarter (8 measured slower)
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256;
+// epilogue staging: per epilogue warp 16 rows x 32 columns of FP32, rows
+// padded to 36 floats (conflict-free 16-byte writes)
+constexpr int EPI_LD = 36;
+constexpr int EPI_BUF = 16 * EPI_LD * 4;
+constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256 + size_t(EPI_WARPS) * EPI_BUF;
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
 // ------------------------------------------------------------ operand prep
@@ -312,6 +317,7 @@ struct TcArgs {
   float scale;
   double* sum;
   int vecB;
+  int staged;                 // restage the epilogue through shared memory (large outputs)
   int* status;
 };
 
@@ -450,13 +456,53 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int t = 0; t < 4; ++t) dtiny[t] = deposit(a.depB, 1, (uint64_t)t);
     const bool vec = a.vecB >= 4;
+    const bool staged = vec && a.staged;
+    // Staged stores (outputs larger than L2, where the store stream is
+    // DRAM-bound; an output that stays in L2 goes out directly from the
+    // registers, 16 bytes per row, which costs less latency): a warp's 32-column chunk goes out in two passes of
+    // 16 rows.  The 512 values of a pass are written to shared memory by row
+    // and read back in output-address order: the 9 index bits (row bits 0-3,
+    // column bits 0-4) are ranked by the output bit they deposit to, and lane
+    // l of store step s takes ranks 128 s + 4 l .. + 3.  Column bits 0 and 1
+    // deposit to output bits 0 and 1 (vec), so those 4 ranks are 4
+    // consecutive columns and 4 consecutive outputs: one 16-byte store, and a
+    // warp instruction writes 128 values in address order (whole lines where
+    // the layout allows) instead of 16 bytes in each of 32 rows.
+    float* ebuf = reinterpret_cast<float*>(smem + STAGE_AREA + 256) + (warp - 2) * (EPI_BUF / 4);
+    int so[4];            // shared-memory offset (row * EPI_LD + column) of step s
+    uint64_t rel[4];      // output offset of step s relative to the pass base
+    {
+      int pos[9], rk[9];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) pos[b] = __ffsll((long long)deposit(a.depA, 1, 1ull << b)) - 1;
+#pragma unroll
+      for (int b = 0; b < 5; ++b) pos[4 + b] = __ffsll((long long)deposit(a.depB, 1, 1ull << b)) - 1;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        rk[i] = 0;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) rk[i] += pos[j] < pos[i] ? 1 : 0;
+      }
+#pragma unroll
+      for (int st = 0; st < 4; ++st) {
+        const int r = 128 * st + 4 * lane;
+        int mm = 0, nn = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) mm |= ((r >> rk[b]) & 1) << b;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) nn |= ((r >> rk[4 + b]) & 1) << b;
+        so[st] = mm * EPI_LD + nn;
+        rel[st] = deposit(a.depA, 1, (uint64_t)mm) + deposit(a.depB, 1, (uint64_t)nn);
+      }
+    }
+    const uint64_t dpass1 = deposit(a.depA, 1, 16ull);   // row bit 4: second pass
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
       const int tm = tile % a.tilesM, tn = tile / a.tilesM;
       // this thread's row: tm*128 + 32q + lane; columns tn*256 + 32c + j
-      const uint64_t grow = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) + dep_lane +
-                            deposit(a.depB, a.nbB, (uint64_t)tn * BN);
+      const uint64_t gbase = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) +
+                             deposit(a.depB, a.nbB, (uint64_t)tn * BN);
       if (nkb > 0) {
         const bool ok = mbar_wait(&tfull[acc], acc_phase, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -487,12 +533,29 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint64_t dc = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
-        float* orow = a.out + grow + dc;
-        if (vec) {
+        if (staged) {
+          float* cbase = a.out + gbase + dc;
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            if ((lane >> 4) == p) {
+              float4* dst = reinterpret_cast<float4*>(ebuf + (lane & 15) * EPI_LD);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            }
+            __syncwarp();
+            float* pbase = cbase + (p ? dpass1 : 0);
+#pragma unroll
+            for (int st = 0; st < 4; ++st)
+              __stcs(reinterpret_cast<float4*>(pbase + rel[st]), *reinterpret_cast<const float4*>(ebuf + so[st]));
+            __syncwarp();
+          }
+        } else if (vec) {
+          float* orow = a.out + gbase + dep_lane + dc;
 #pragma unroll
           for (int j = 0; j < 8; ++j)
             __stcs(reinterpret_cast<float4*>(orow + dlow[j]), make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]));
         } else {
+          float* orow = a.out + gbase + dep_lane + dc;
 #pragma unroll
           for (int j = 0; j < 8; ++j)
 #pragma unroll
@@ -640,6 +703,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   a.scale = (float)c.scale;
   a.sum = c.sum;
   a.vecB = c.vecB;
+  a.staged = M * N >= (int64_t(1) << 25) ? 1 : 0;   // 128 MiB of FP32 output: beyond L2
   a.status = status;
   static int sms = 0;
   static bool attr = false;

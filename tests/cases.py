@@ -33,3 +33,8 @@ def dd_twin():
     """Scaled twin of the 80-qubit dynamic-definition workload: a 4x5 grid of
     depth 10 cut into 2x2 blocks (4 subcircuits), K <= 8."""
     return C.grid_blocks(4, 5, 10, 0, 2, 2, 8, 10)
+
+
+def hwea26_chain():
+    """26-qubit HWEA cut once between qubits 12 and 13: 2^13 x 2^13 outputs."""
+    return C.chain_blocks(C.hwea(26, 7), 2)

@@ -154,6 +154,31 @@ def test_supremacy_4x6_full_size_sampled(env, sup, algo):
     assert abs(float(sp.item()) - 1.0) <= tol + 1e-6    # trace preservation of the uncut circuit
 
 
+@pytest.mark.parametrize("algo", ["tc_bf16x3", "tc_bf16x6"])
+def test_large_output_sampled(env, algo):
+    """2^26 outputs (256 MiB of FP32, larger than L2): a 26-qubit HWEA chain
+    cut once into two 13-qubit halves.  At this size the tensor-core epilogue
+    restages its blocks through shared memory and stores them in output-address
+    order; 4096 sampled outputs are checked against the oracle's plain sum and
+    the fused FP64 sum against the sum of the returned outputs."""
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    cc, Ts = oracle_case("hwea26_s2", cases.hwea26_chain)
+    T32 = [T.astype(np.float32) for T in Ts]
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
+    assert cutqc.last_algo() == cutqc.ALGOS[algo]
+    got = out.double().cpu().numpy()
+    rng = np.random.default_rng(12)
+    xs = sorted(set(int(x) for x in rng.integers(0, 2 ** cc.n, 4096)) | {0, 1, 2, 3, 2 ** cc.n - 1})
+    want = rc.fd_entries(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts, xs)
+    err = np.abs(got[xs] - want).max()
+    assert err <= TOL32, f"max abs err {err:.3e}"
+    assert float(sp.item()) == pytest.approx(got.sum(), abs=1e-9)
+    assert float(sp.item()) == pytest.approx(1.0, abs=1e-5)
+    del out
+    torch.cuda.empty_cache()
+
+
 def test_supremacy_gpu_simulated_inputs(env, sup):
     """The benchmark's own input preparation (GPU simulator) reproduces the
     oracle's FP32 tensors of the full-size workload."""
