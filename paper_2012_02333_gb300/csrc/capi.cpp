@@ -694,7 +694,18 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     Contraction& c = cs[i];
     const bool last_step = (i + 1 == P.steps.size());
     const bool both_new = !flagged[st.a] || !flagged[st.b];
-    if (last_step && use_tc_final && both_new && st.kmax <= 4096) {
+    TcFusedStats fstats{};
+    bool fused_stats = false;
+    if (last_step && use_tc_final && !flagged[st.a] && !flagged[st.b] && st.kmax <= 4096) {
+      // the row statistics of both operands run inside the operand preparation
+      flagged[st.a] = flagged[st.b] = 1;
+      fstats.nzA = reinterpret_cast<int32_t*>(base + P.ws_nz[st.a]);
+      fstats.nzB = reinterpret_cast<int32_t*>(base + P.ws_nz[st.b]);
+      fstats.rmaxA = reinterpret_cast<float*>(base + P.ws_rmax[st.a]);
+      fstats.rmaxB = reinterpret_cast<float*>(base + P.ws_rmax[st.b]);
+      fstats.barrier = reinterpret_cast<unsigned*>(base + st.ws_counter);
+      fused_stats = true;
+    } else if (last_step && use_tc_final && both_new && st.kmax <= 4096) {
       // the last row-statistics block compacts the terms and picks the split
       CompactJob cj;
       cj.active = 1;
@@ -746,7 +757,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       launch_compact(c, s);   // the tensor-core path compacts inside its operand preparation
     }
     if (final_step && use_tc_final)
-      launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s);
+      launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s, fused_stats ? &fstats : nullptr);
     else
       launch_cc_gemm(c, s);
     if (final_step) g_last_algo = use_tc_final ? (algo == CUTQC_AUTO ? CUTQC_TC_BF16X3 : algo) : CUTQC_CC;

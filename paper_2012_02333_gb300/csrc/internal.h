@@ -145,7 +145,20 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 
 // k_tc.cu
 bool tc_supported(const Contraction& c);
-void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s);
+// With `fused`, the row statistics of both operands (non-zero flags and row
+// max |.| into the given arrays), the compaction and the operand preparation
+// run as one cooperative launch with a grid barrier (kmax <= 4096; `barrier`
+// is a device counter the launch zeroes first); otherwise the statistics come
+// from an earlier launch.
+struct TcFusedStats {
+  int32_t* nzA;
+  int32_t* nzB;
+  float* rmaxA;
+  float* rmaxB;
+  unsigned* barrier;
+};
+void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s,
+                      const TcFusedStats* fused = nullptr);
 size_t tc_workspace_bytes(const Contraction& c);
 
 

@@ -35,20 +35,52 @@ __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, in
 template <typename T>
 __device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64_t cols, int32_t* flag, float* rmax) {
   __shared__ float red[32];
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  constexpr int U = 4;   // vector loads per thread per step: a 256-thread block reads 4096 FP32 values at once
   float m = 0.0f;
   int nz = 0;
-  constexpr int U = 4;   // independent loads in flight per thread
-  for (int64_t i0 = threadIdx.x; i0 < cols; i0 += (int64_t)blockDim.x * U) {
-    T v[U];
+  auto take = [&](T x) {
+    nz |= (x != T(0));
+    // FP32 tensors stay on the FP32 pipes (the FP64 pipe is narrow here)
+    if constexpr (sizeof(T) == 4)
+      m = fmaxf(m, fabsf(x));
+    else
+      m = fmaxf(m, (float)fabs(x));
+  };
+  if (cols % W == 0 && (reinterpret_cast<uintptr_t>(row) % sizeof(V)) == 0) {
+    const V* rv = reinterpret_cast<const V*>(row);
+    const int64_t nv = cols / W;
+    for (int64_t i0 = threadIdx.x; i0 < nv; i0 += (int64_t)blockDim.x * U) {
+      V v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t i = i0 + (int64_t)u * blockDim.x;
-      v[u] = i < cols ? row[i] : T(0);
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i < nv) {
+          v[u] = __ldg(rv + i);
+        } else {
+          T* z = reinterpret_cast<T*>(&v[u]);
+#pragma unroll
+          for (int w = 0; w < W; ++w) z[w] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const T* x = reinterpret_cast<const T*>(&v[u]);
+#pragma unroll
+        for (int w = 0; w < W; ++w) take(x[w]);
+      }
     }
+  } else {
+    for (int64_t i0 = threadIdx.x; i0 < cols; i0 += (int64_t)blockDim.x * U) {
+      T v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      nz |= (v[u] != T(0));
-      m = fmaxf(m, (float)fabs((double)v[u]));
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        v[u] = i < cols ? row[i] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) take(v[u]);
     }
   }
 #pragma unroll
@@ -66,12 +98,12 @@ __device__ __forceinline__ void row_stats_block(const T* __restrict__ row, int64
 // the a-priori bound S and the split count
 __device__ void compact_block(const CompactJob& cj) {
   __shared__ int warp_tot[32];
-  __shared__ double warp_s[32];
+  __shared__ float warp_s[32];
   __shared__ int base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (threadIdx.x == 0) base = 0;
   __syncthreads();
-  double s_acc = 0.0;
+  float s_acc = 0.0f;   // the bound in FP32 (a magnitude estimate; the FP64 pipe is narrow)
   const int32_t* ra = cj.rows;
   const int32_t* rb = cj.rows + cj.kmax;
   for (int k0 = 0; k0 < cj.kmax; k0 += blockDim.x) {
@@ -94,7 +126,7 @@ __device__ void compact_block(const CompactJob& cj) {
       const int ci = base + off + __popc(m & ((1u << lane) - 1u));
       cj.crow[ci] = a;
       cj.crow[cj.kmax + ci] = b;
-      if (cj.bound) s_acc += (double)cj.rmaxA[a] * (double)cj.rmaxB[b];
+      if (cj.bound) s_acc = fmaf(cj.rmaxA[a], cj.rmaxB[b], s_acc);
     }
     __syncthreads();
     if (threadIdx.x == 0) base += tot;
@@ -108,9 +140,10 @@ __device__ void compact_block(const CompactJob& cj) {
     *cj.kcount = base;
     if (cj.sum_zero) *cj.sum_zero = 0.0;
     if (cj.bound) {
-      double S = 0.0;
-      for (int w = 0; w < nw; ++w) S += warp_s[w];
-      S *= cj.scale;
+      float Sf = 0.0f;
+      for (int w = 0; w < nw; ++w) Sf += warp_s[w];
+      // FP32 accumulation error is far below 1e-4 relative: inflate so S stays an upper bound
+      const double S = (double)Sf * cj.scale * (1.0 + 1e-4);
       *cj.bound = S;
       // BF16 x3 drops terms of at most ~3 * 2^-18 relative to |a||b| per product
       *cj.nseg = cj.nseg_fixed ? cj.nseg_fixed : (3.0 * 3.814697265625e-06 * S <= cj.split_tol ? 3 : 6);
@@ -153,9 +186,9 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
                           int32_t* __restrict__ nseg, int nseg_fixed, double split_tol,
                           double* __restrict__ sum_zero) {
   __shared__ int warp_tot[32];
-  __shared__ double warp_s[32];
+  __shared__ float warp_s[32];
   __shared__ int base;
-  double s_acc = 0.0;
+  float s_acc = 0.0f;   // the bound in FP32 (a magnitude estimate; the FP64 pipe is narrow)
   const int b = blockIdx.x;
   const int32_t* ra = rows + (int64_t)b * 2 * kmax;
   const int32_t* rb = ra + kmax;
@@ -184,7 +217,7 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
     if (keep) {
       ca[base + off + before] = a;
       cb[base + off + before] = bb;
-      if (bound) s_acc += (double)rmaxA[a] * (double)rmaxB[bb];
+      if (bound) s_acc = fmaf(rmaxA[a], rmaxB[bb], s_acc);
     }
     __syncthreads();
     if (threadIdx.x == 0) base += tot;
@@ -200,9 +233,10 @@ __global__ void k_compact(const int32_t* __restrict__ rows, int kmax, const int3
     if (sum_zero && b == 0) *sum_zero = 0.0;
     kcount[b] = base;
     if (bound) {
-      double S = 0.0;
-      for (int w = 0; w < nw; ++w) S += warp_s[w];
-      S *= scale;
+      float Sf = 0.0f;
+      for (int w = 0; w < nw; ++w) Sf += warp_s[w];
+      // FP32 accumulation error is far below 1e-4 relative: inflate so S stays an upper bound
+      const double S = (double)Sf * scale * (1.0 + 1e-4);
       bound[b] = S;
       // BF16 x3 drops terms of at most ~3 * 2^-18 relative to |a||b| per product
       const double err3 = 3.0 * 3.814697265625e-06 * S;

@@ -66,6 +66,17 @@ constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256 + size_t(EPI_WARPS
 static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
 
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
 // ------------------------------------------------------------ operand prep
 // Each FP32 x is split into h = bf16(x), m = bf16(x - h), l = bf16(x - h - m).
 // Segment s of the concatenated inner dimension pairs part PA[s] of A with
@@ -103,33 +114,39 @@ struct PrepArgs {
 // row pairs: early termination, Sec. 4.2) and the split count from the bound
 // S = scale * sum_kept max|A| max|B|; block (0, 0) publishes the count, the
 // split count and S for the contraction and zeroes the FP64 sum.
-__global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
-  CUTQC_PDL_WAIT();     // row statistics come from the previous kernel
-  CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
+// One 64 (k) x 64 (m) tile of the operand preparation; (bx, by) = (column
+// block over A then B, k block).  The row statistics it reads (fused mode)
+// may have been written by the same kernel before a grid barrier, so they are
+// read through L2 (__ldcg), never through a stale L1 line.
+// pre_r0 / pre_r1: this thread's row pair t = threadIdx.x, read before the
+// call (pre = true), for the first pass of the fused scan
+__device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const int by, const bool pre = false,
+                                          const int pre_r0 = 0, const int pre_r1 = 0) {
+  __syncthreads();   // the shared arrays may still be read by the previous tile
   __shared__ float s[64][65];
   __shared__ int32_t rowsel[64];
   __shared__ int warp_tot[8];
-  __shared__ double warp_s[8];
+  __shared__ float warp_s[8];
   __shared__ int base_s, kc_s, nseg_s;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int which = blockIdx.x < (unsigned)a.blocks0 ? 0 : 1;
-  const int64_t m0 = (int64_t)(which == 0 ? blockIdx.x : blockIdx.x - a.blocks0) * 64;
-  const int k0 = blockIdx.y * 64;
+  const int which = bx < a.blocks0 ? 0 : 1;
+  const int64_t m0 = (int64_t)(which == 0 ? bx : bx - a.blocks0) * 64;
+  const int k0 = by * 64;
   const int64_t cols = a.cols[which];
   const float* T = a.T[which];
   if (a.fused) {
     if (tid == 0) base_s = 0;
     __syncthreads();
-    double sacc = 0.0;
+    float sacc = 0.0f;   // the bound in FP32 (a magnitude estimate; the FP64 pipe is narrow)
     const int32_t* ra = a.rows;
     const int32_t* rb = a.rows + a.kmax;
     for (int t0 = 0; t0 < a.kmax; t0 += 256) {
       const int t = t0 + tid;
       int keep = 0, r0 = 0, r1 = 0;
       if (t < a.kmax) {
-        r0 = ra[t];
-        r1 = rb[t];
-        keep = a.nzA[r0] && a.nzB[r1];
+        r0 = (pre && t0 == 0) ? pre_r0 : ra[t];
+        r1 = (pre && t0 == 0) ? pre_r1 : rb[t];
+        keep = __ldcg(a.nzA + r0) && __ldcg(a.nzB + r1);
       }
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) warp_tot[warp] = __popc(m);
@@ -142,7 +159,7 @@ __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
       if (keep) {
         const int ci = base_s + off + __popc(m & ((1u << lane) - 1u));
         if (ci >= k0 && ci < k0 + 64) rowsel[ci - k0] = which == 0 ? r0 : r1;
-        sacc += (double)a.rmaxA[r0] * (double)a.rmaxB[r1];
+        sacc = fmaf(__ldcg(a.rmaxA + r0), __ldcg(a.rmaxB + r1), sacc);
       }
       __syncthreads();
       if (tid == 0) base_s += tot;
@@ -153,14 +170,15 @@ __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
     if (lane == 0) warp_s[warp] = sacc;
     __syncthreads();
     if (tid == 0) {
-      double S = 0.0;
-      for (int w = 0; w < 8; ++w) S += warp_s[w];
-      S *= a.scale;
+      float Sf = 0.0f;
+      for (int w = 0; w < 8; ++w) Sf += warp_s[w];
+      // FP32 accumulation error is far below 1e-4 relative: inflate so S stays an upper bound
+      const double S = (double)Sf * a.scale * (1.0 + 1e-4);
       // BF16 x3 drops terms of at most ~3 * 2^-18 |a||b| per product
       const int ns = a.nseg_fixed ? a.nseg_fixed : (3.0 * 3.814697265625e-06 * S <= a.split_tol ? 3 : 6);
       kc_s = base_s;
       nseg_s = ns;
-      if (blockIdx.x == 0 && blockIdx.y == 0) {
+      if (bx == 0 && by == 0) {
         *a.kcount = base_s;
         *a.nseg = ns;
         *a.bound = S;
@@ -177,10 +195,20 @@ __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
   }
   __syncthreads();
   const int kc = kc_s, nseg = nseg_s;
+  // the contraction reads k < 32 * ceil(kc / 32): tiles past that write nothing
+  if (k0 >= (kc + 31) / 32 * 32) return;
+  {
+    // all 16 loads first (read-only path), then the shared-memory stores: a
+    // load interleaved with stores through a generic pointer would wait for
+    // each of them in turn
+    float ld[16];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    const int kk = i * 4 + tid / 64, mm = tid % 64, k = k0 + kk;
-    s[kk][mm] = (k < kc) ? T[(int64_t)rowsel[kk] * cols + m0 + mm] : 0.0f;
+    for (int i = 0; i < 16; ++i) {
+      const int kk = i * 4 + tid / 64, mm = tid % 64, k = k0 + kk;
+      ld[i] = (k < kc) ? __ldg(T + (int64_t)rowsel[kk] * cols + m0 + mm) : 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s[i * 4 + tid / 64][tid % 64] = ld[i];
   }
   __syncthreads();
   const int ml = tid / 4, kq = (tid % 4) * 16;
@@ -206,14 +234,111 @@ __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
+  CUTQC_PDL_WAIT();     // row statistics come from the previous kernel
+  CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
+  prep_tile(a, blockIdx.x, blockIdx.y);
+}
+
+// ---- row statistics + compaction + operand preparation in one launch -----
+// Phase 1: one block per row of A then B (grid-stride): non-zero flag and
+// max |x| (the early-termination test of Sec. 4.2 and the split bound).
+// A grid barrier (cooperative launch, so every block is resident; the wait is
+// bounded and a timeout sets the status word and ends the block).  Phase 2:
+// the operand-preparation tiles (grid-stride), each block scanning the row
+// flags itself (fused compaction).
+struct StatsArgs {
+  int64_t rows[2];
+  int32_t* nz[2];
+  float* rmax[2];
+  unsigned* barrier;   // zeroed before the launch
+  int* status;
+  int tilesX, tilesY;
+};
+
+__device__ __forceinline__ void stats_row(const float* __restrict__ row, int64_t cols, int32_t* flag, float* rmax) {
+  __shared__ float red[8];
+  __shared__ int nzs[8];
+  float m = 0.0f;
+  int nz = 0;
+  const float4* rv = reinterpret_cast<const float4*>(row);
+  const int64_t nv = cols / 4;
+  for (int64_t i0 = threadIdx.x; i0 < nv; i0 += 4 * (int64_t)blockDim.x) {
+    float4 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      v[u] = i < nv ? __ldg(rv + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      nz |= (v[u].x != 0.f) | (v[u].y != 0.f) | (v[u].z != 0.f) | (v[u].w != 0.f);
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)), fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    nz |= __shfl_xor_sync(0xffffffffu, nz, o);
+  }
+  __syncthreads();   // red / nzs may still be read for the previous row
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = m;
+    nzs[threadIdx.x >> 5] = nz;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmaxf(m, red[w]);
+      nz |= nzs[w];
+    }
+    *flag = nz;
+    *rmax = m;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stats_prep(const PrepArgs a, const StatsArgs sa) {
+  CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
+  // the first 256 row pairs of the compaction are plan data: read them now
+  int pre_r0 = 0, pre_r1 = 0;
+  if ((int)threadIdx.x < a.kmax) {
+    pre_r0 = __ldg(a.rows + threadIdx.x);
+    pre_r1 = __ldg(a.rows + a.kmax + threadIdx.x);
+  }
+  const int64_t nrows = sa.rows[0] + sa.rows[1];
+  for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int j = r < sa.rows[0] ? 0 : 1;
+    const int64_t rr = j == 0 ? r : r - sa.rows[0];
+    stats_row(a.T[j] + rr * a.cols[j], a.cols[j], sa.nz[j] + rr, sa.rmax[j] + rr);
+  }
+  // grid barrier
+  __shared__ int pass;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // release: this block's statistics (written by this thread) are visible
+    // to any block whose acquire load sees the count
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(sa.barrier) : "memory");
+    const uint64_t t0 = gtimer();
+    int ok = 1;
+    while (ld_acquire(sa.barrier) < gridDim.x) {
+      if (gtimer() - t0 > 2000000000ull) {   // 2 s
+        ok = 0;
+        atomicExch(sa.status, (int)DEV_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+    }
+    pass = ok;
+  }
+  __syncthreads();
+  if (!pass) return;
+  for (int t = blockIdx.x; t < sa.tilesX * sa.tilesY; t += gridDim.x)
+    prep_tile(a, t % sa.tilesX, t / sa.tilesX, true, pre_r0, pre_r1);
+}
+
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ uint64_t gtimer() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
 }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -296,6 +421,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// the same load without the wait, and a wait that names the destination
+// registers, so their uses cannot be scheduled before it
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, int nbytes, uint64_t v) {
@@ -442,6 +591,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;
     const int hf = (warp - 2) / 4;
     constexpr int CPW = BN / 32 / (EPI_WARPS / 4);   // 32-column chunks per warp
+    static_assert(CPW % 2 == 0, "chunks go in pairs");
     double local = 0.0;
     // the deposit is additive over disjoint index bits, so a row's output
     // address is dep(row base) + dep(lane) + dep(chunk column base) +
@@ -508,15 +658,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!__all_sync(0xffffffffu, ok)) break;
         tc_fence_after();
       }
-#pragma unroll 1
-      for (int c = hf * CPW; c < (hf + 1) * CPW; ++c) {
-        uint32_t r[32];
-        if (nkb > 0) {
-          tmem_ld32(tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c), r);
-        } else {
-#pragma unroll
-          for (int j = 0; j < 32; ++j) r[j] = 0u;
-        }
+      // the TMEM load of the next 32-column chunk is in flight while this one
+      // is processed (two register buffers)
+      auto taddr = [&](int c) {
+        return tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * BN + 32 * c);
+      };
+      auto process = [&](const int c, uint32_t (&r)[32]) {
         // sum of this 32-column row piece: pairwise in FP32 (error <= 5 * 2^-24 *
         // sum |v|), then one FP64 add (the FP64 pipe is narrow on this part)
         float v[32];
@@ -561,6 +708,24 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int t = 0; t < 4; ++t) orow[dlow[j] + dtiny[t]] = v[4 * j + t];
         }
+      };
+      uint32_t ra[32], rb[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) ra[j] = rb[j] = 0u;
+      const int c0 = hf * CPW;
+      if (nkb > 0) tmem_ld32_issue(taddr(c0), ra);
+#pragma unroll 1
+      for (int c = c0; c < c0 + CPW; c += 2) {
+        if (nkb > 0) {
+          tmem_wait32(ra);
+          tmem_ld32_issue(taddr(c + 1), rb);
+        }
+        process(c, ra);
+        if (nkb > 0) {
+          tmem_wait32(rb);
+          if (c + 2 < c0 + CPW) tmem_ld32_issue(taddr(c + 2), ra);
+        }
+        process(c + 1, rb);
       }
       if (nkb > 0) {
         tc_fence_before();
@@ -641,7 +806,7 @@ size_t tc_workspace_bytes(const Contraction& c) {
   return align256(M * 3 * Kp * 2) + align256(N * 3 * Kp * 2) + 256;
 }
 
-void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s) {
+void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s, const TcFusedStats* fused) {
   if (!tc_supported(c)) fail(CUTQC_ERR_UNSUPPORTED, "shape not supported by the tensor-core path");
   if (ws_bytes < tc_workspace_bytes(c)) fail(CUTQC_ERR_OOM, "tensor-core workspace too small");
   const int Kp = kpad(c);
@@ -675,14 +840,59 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   pa.sum_zero = c.sum;
   pa.out[0] = Ab;
   pa.out[1] = Bb;
-  if (!pa.fused && !c.compacted) {
-    Contraction cc = c;
-    cc.sum_zero = c.sum;
-    launch_compact(cc, s);
+  if (fused) {
+    if (c.kmax > 4096) fail(CUTQC_ERR_UNSUPPORTED, "fused row statistics need kmax <= 4096");
+    pa.fused = 1;
+    pa.nzA = fused->nzA;
+    pa.nzB = fused->nzB;
+    pa.rmaxA = fused->rmaxA;
+    pa.rmaxB = fused->rmaxB;
+    StatsArgs sa{};
+    sa.rows[0] = c.rowsA;
+    sa.rows[1] = c.rowsB;
+    sa.nz[0] = fused->nzA;
+    sa.nz[1] = fused->nzB;
+    sa.rmax[0] = fused->rmaxA;
+    sa.rmax[1] = fused->rmaxB;
+    sa.barrier = fused->barrier;
+    sa.status = status;
+    sa.tilesX = (int)((M + N) / 64);
+    sa.tilesY = Kp / 64;
+    static int coop_blocks = 0;   // resident blocks per SM
+    static int coop_sms = 0;
+    if (!coop_blocks) {
+      int dev = 0;
+      CUTQC_CUDA(cudaGetDevice(&dev));
+      CUTQC_CUDA(cudaDeviceGetAttribute(&coop_sms, cudaDevAttrMultiProcessorCount, dev));
+      CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_blocks, k_stats_prep, 256, 0));
+      if (coop_blocks < 1) fail(CUTQC_ERR_CUDA, "operand preparation cannot be resident");
+    }
+    const int64_t want = std::max<int64_t>(sa.rows[0] + sa.rows[1], (int64_t)sa.tilesX * sa.tilesY);
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)coop_blocks * coop_sms);
+    CUTQC_CUDA(cudaMemsetAsync(fused->barrier, 0, sizeof(unsigned), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every block resident: the grid barrier cannot starve
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_stats_prep, pa, sa));
+    count_launch();
+    check_launch("k_stats_prep");
+  } else {
+    if (!pa.fused && !c.compacted) {
+      Contraction cc = c;
+      cc.sum_zero = c.sum;
+      launch_compact(cc, s);
+    }
+    CUTQC_CUDA(launch_pdl(k_prep, dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), dim3(256), 0, s, pa));
+    count_launch();
+    check_launch("k_prep");
   }
-  CUTQC_CUDA(launch_pdl(k_prep, dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), dim3(256), 0, s, pa));
-  count_launch();
-  check_launch("k_prep");
 
   // three pieces of each operand stacked along rows: [piece * rows + row][k]
   const CUtensorMap tmA = make_map(Ab, (uint64_t)M * 3, (uint64_t)Kp, BM);
