@@ -233,6 +233,25 @@ CUTQC_API int32_t cutqc_last_algo(void);
  * tensor-core contraction has run on this thread. */
 CUTQC_API int cutqc_last_split(int32_t* nseg, double* bound);
 
+/* Every kernel that waits (on an mbarrier, a grid barrier or a flag) gives
+ * up after a bounded time instead of hanging the GPU, and records that in a
+ * per-device status word; its outputs are then invalid.  cutqc_device_status
+ * synchronises `stream` and reports the word: CUTQC_OK, CUTQC_ERR_TIMEOUT (a
+ * bounded wait ran out) or CUTQC_ERR_DEVICE (another device-side check
+ * failed), then clears it.  cutqc_reconstruct_dd (when it returns a top
+ * list) and cutqc_last_split check it themselves, as they synchronise.  The
+ * full-definition and backward calls are asynchronous and do not: a caller
+ * that needs the guarantee calls cutqc_device_status after them. */
+CUTQC_API int cutqc_device_status(void* stream);
+
+/* Failure-path self-test: launches one thread that waits on a device flag
+ * nothing ever sets, with a limit of `limit_us` microseconds (0 .. 2e6);
+ * when the limit runs out it records CUTQC_ERR_TIMEOUT in the status word,
+ * exactly as a timed-out wait in the reconstruction kernels does, and ends
+ * normally, so the context stays usable.  The paper has no counterpart: it
+ * exists so the error path can be tested without a fault. */
+CUTQC_API int cutqc_selftest_wait(int32_t limit_us, void* stream);
+
 /* Kernel timing for roofline measurement.  While enabled, every launch of
  * the main contraction kernel of a full-definition call (the 4^K sum of the
  * final step) is bracketed by CUDA events recorded on the stream it is

@@ -203,6 +203,7 @@ struct DeviceState {
   std::unordered_map<std::string, GraphEntry> graphs;   // captured batched calls
   cudaStream_t branch[kBranches] = {};
   cudaEvent_t fork = nullptr, join[kBranches] = {};
+  int* status = nullptr;          // device status word written by kernels with bounded waits
 };
 static std::map<int, DeviceState> g_dev;
 
@@ -229,6 +230,29 @@ static DeviceState& device_state() {
   int dev = 0;
   CUTQC_CUDA(cudaGetDevice(&dev));
   return g_dev[dev];
+}
+
+// The device status word (DeviceStatus) of this device, allocated and zeroed
+// on first use (outside any stream capture: every entry point that launches a
+// waiting kernel asks for it before launching).
+static int* status_word(DeviceState& ds) {
+  if (!ds.status) {
+    CUTQC_CUDA(cudaMalloc(&ds.status, 256));
+    CUTQC_CUDA(cudaMemset(ds.status, 0, sizeof(int)));
+  }
+  return ds.status;
+}
+
+// After the caller has synchronised: report and clear a recorded device status.
+static void check_status(DeviceState& ds) {
+  if (!ds.status) return;
+  int v = 0;
+  CUTQC_CUDA(cudaMemcpy(&v, ds.status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v == DEV_OK) return;
+  CUTQC_CUDA(cudaMemset(ds.status, 0, sizeof(int)));
+  if (v == DEV_TIMEOUT)
+    fail(CUTQC_ERR_TIMEOUT, "a bounded device wait ran out; outputs of the calls since the last check are invalid");
+  fail(CUTQC_ERR_DEVICE, "a device-side check failed; outputs of the calls since the last check are invalid");
 }
 
 static void drop_graphs(DeviceState& ds) {
@@ -749,6 +773,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       g_last_bound = c.bound;
       g_last_stream = s;
     }
+    c.status = status_word(ds);
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
     c.sum = final_step ? sum : nullptr;
     c.profile = final_step;
@@ -1058,6 +1083,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
       CUTQC_CUDA(cudaMemcpyAsync(hi.data(), ci, NC * 8, cudaMemcpyDeviceToHost, s));
       CUTQC_CUDA(cudaMemcpyAsync(hv.data(), val, NC * 8, cudaMemcpyDeviceToHost, s));
       CUTQC_CUDA(cudaStreamSynchronize(s));
+      check_status(ds);
       std::vector<std::pair<double, int64_t>> cand;
       for (int j = 0; j < NC; ++j)
         if (hi[j] >= 0 && hi[j] < nbins) cand.emplace_back(hv[j], hi[j]);
@@ -1181,6 +1207,8 @@ void cutqc_release(void) {
     kv.second.order.clear();
     if (kv.second.ws) cudaFree(kv.second.ws);
     if (kv.second.one) cudaFree(kv.second.one);
+    if (kv.second.status) cudaFree(kv.second.status);
+    kv.second.status = nullptr;
     kv.second.ws = nullptr;
     kv.second.one = nullptr;
     kv.second.ws_bytes = 0;
@@ -1198,8 +1226,25 @@ int cutqc_last_split(int32_t* nseg, double* bound) {
     if (!nseg || !bound) fail(CUTQC_ERR_ARG, "NULL output");
     if (!g_last_nseg || g_last_algo == CUTQC_CC) fail(CUTQC_ERR_ARG, "no tensor-core contraction has run");
     CUTQC_CUDA(cudaStreamSynchronize(g_last_stream));
+    check_status(device_state());
     CUTQC_CUDA(cudaMemcpy(nseg, g_last_nseg, sizeof(int32_t), cudaMemcpyDeviceToHost));
     CUTQC_CUDA(cudaMemcpy(bound, g_last_bound, sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+int cutqc_device_status(void* stream) {
+  return guarded([&] {
+    DeviceState& ds = device_state();
+    CUTQC_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    check_status(ds);
+  });
+}
+
+int cutqc_selftest_wait(int32_t limit_us, void* stream) {
+  return guarded([&] {
+    if (limit_us < 0 || limit_us > 2000000) fail(CUTQC_ERR_ARG, "limit_us outside [0, 2000000]");
+    DeviceState& ds = device_state();
+    launch_wait_selftest(status_word(ds), limit_us, static_cast<cudaStream_t>(stream));
   });
 }
 

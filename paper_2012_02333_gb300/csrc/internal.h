@@ -106,6 +106,7 @@ struct Contraction {
   bool compacted = false;          // crow / kcount / nseg / bound already written (row statistics did it)
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
+  int* status = nullptr;           // device status word (DeviceStatus) of this device
 };
 
 // k_cc.cu
@@ -144,6 +145,10 @@ void launch_cc_gemm(const Contraction& c, cudaStream_t s);
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 
 // k_tc.cu
+// One block, one thread: waits on a device flag that nothing sets, bounded by
+// `limit_us`, then records DEV_TIMEOUT in *status (the bounded-wait path of
+// every kernel that waits, exercised without any other work).
+void launch_wait_selftest(int* status, int limit_us, cudaStream_t s);
 bool tc_supported(const Contraction& c);
 // With `fused`, the row statistics of both operands (non-zero flags and row
 // max |.| into the given arrays), the compaction and the operand preparation

@@ -761,6 +761,21 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
+// ------------------------------------------------------------ wait self-test
+__global__ void k_wait_selftest(int* status, long long limit_ns) {
+  __shared__ unsigned flag;
+  flag = 0u;
+  __syncwarp();
+  const uint64_t t0 = gtimer();
+  while (*reinterpret_cast<volatile unsigned*>(&flag) == 0u) {
+    if ((long long)(gtimer() - t0) > limit_ns) {
+      atomicExch(status, (int)DEV_TIMEOUT);
+      return;
+    }
+    __nanosleep(1000);
+  }
+}
+
 // ------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -796,6 +811,12 @@ size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 }  // namespace
 
+void launch_wait_selftest(int* status, int limit_us, cudaStream_t s) {
+  k_wait_selftest<<<1, 1, 0, s>>>(status, (long long)limit_us * 1000);
+  count_launch();
+  check_launch("k_wait_selftest");
+}
+
 bool tc_supported(const Contraction& c) {
   return c.dtype == CUTQC_F32 && c.batch == 1 && c.fA >= 7 && c.fB >= 8 && c.kmax >= 1;
 }
@@ -814,7 +835,8 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   char* w = static_cast<char*>(ws);
   auto* Ab = reinterpret_cast<__nv_bfloat16*>(w);
   auto* Bb = reinterpret_cast<__nv_bfloat16*>(w + align256((size_t)M * 3 * Kp * 2));
-  int* status = reinterpret_cast<int*>(w + align256((size_t)M * 3 * Kp * 2) + align256((size_t)N * 3 * Kp * 2));
+  int* status = c.status;
+  if (!status) fail(CUTQC_ERR_ARG, "tensor-core path needs the device status word");
   if (!c.nseg || !c.bound) fail(CUTQC_ERR_ARG, "tensor-core path needs the split count");
   PrepArgs pa{};
   pa.T[0] = static_cast<const float*>(c.A);

@@ -77,12 +77,14 @@ _lib.cutqc_reconstruct_fd_noalloc.argtypes = [C.POINTER(cutqc_problem), C.c_void
 _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+_lib.cutqc_device_status.argtypes = [C.c_void_p]
+_lib.cutqc_selftest_wait.argtypes = [C.c_int32, C.c_void_p]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
-           "cutqc_reconstruct_fd_noalloc"):
+           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -139,6 +141,19 @@ def profile_read():
 def _i32(xs: Sequence[int]):
     arr = (C.c_int32 * max(len(xs), 1))(*[int(x) for x in xs])
     return arr
+
+
+def device_status(stream=None) -> None:
+    """Synchronise `stream` and raise CutQCError if a kernel since the last
+    check recorded a timed-out bounded wait (CUTQC_ERR_TIMEOUT) or a failed
+    device-side check (CUTQC_ERR_DEVICE); the record is cleared either way."""
+    _check(_lib.cutqc_device_status(_stream_ptr(stream)))
+
+
+def selftest_wait(limit_us: int, stream=None) -> None:
+    """Launch the bounded-wait self-test (a wait nothing satisfies, limited to
+    `limit_us` microseconds); device_status() then reports the timeout."""
+    _check(_lib.cutqc_selftest_wait(int(limit_us), _stream_ptr(stream)))
 
 
 def _stream_ptr(stream) -> Optional[int]:
