@@ -114,11 +114,17 @@ typedef struct {
 } cutqc_problem;
 
 /* Full definition (Sec. 4.2).  For each of n_problems cut circuits write all
- * 2^n_qubits probabilities to out[i] (device, the problem's dtype, index =
- * bit string with qubit 0 most significant).  Kronecker terms whose factor
- * rows are all zero are skipped (early termination, Sec. 4.2).  sum_p:
- * device double [n_problems] receiving sum_x p(x) accumulated in FP64, or
- * NULL.  No host synchronisation. */
+ * 2^n_qubits probabilities to out[i] (the problem's dtype, index = bit string
+ * with qubit 0 most significant).  out[i] is device memory of the current
+ * device, or pinned host memory mapped for the device (cudaHostAlloc /
+ * cudaHostRegister, or a pinned torch tensor): the contraction then writes
+ * the probabilities straight into host memory over the host link, with no
+ * separate copy; they are there once the stream has passed the call.  Any
+ * other pointer (unregistered host memory, another device's memory) is
+ * rejected with CUTQC_ERR_ARG before anything runs.  Kronecker terms whose
+ * factor rows are all zero are skipped (early termination, Sec. 4.2).
+ * sum_p: device double [n_problems] receiving sum_x p(x) accumulated in FP64,
+ * or NULL.  No host synchronisation. */
 CUTQC_API int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems,
                          void* const* out, int32_t algo, double* sum_p,
                          void* stream);

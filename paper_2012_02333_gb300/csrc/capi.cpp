@@ -637,6 +637,42 @@ static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
 // Run a plan.  The workspace holds [front | the plan's own buffers | back];
 // `pre(front_ptr)` is called once the workspace exists and returns the device
 // tensors of the plan's original nodes.  Returns a pointer to the back region.
+// Output of a full-definition call: device (or managed) memory of the current
+// device, or pinned host memory mapped into the device's address space; the
+// kernels then write the probabilities straight into host memory over the
+// host link, and the device alias of the buffer is what they are given.
+// Unregistered host memory and other devices' memory are rejected here,
+// before anything is launched.
+static void* resolve_out(void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    fail(CUTQC_ERR_ARG, "out is not a pointer CUDA knows");
+  }
+  int dev = 0;
+  CUTQC_CUDA(cudaGetDevice(&dev));
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      if (at.type == cudaMemoryTypeDevice && at.device != dev) fail(CUTQC_ERR_ARG, "out is on another device");
+      return p;
+    case cudaMemoryTypeHost:
+      if (!at.devicePointer) fail(CUTQC_ERR_ARG, "out is pinned host memory not mapped for the device");
+      return at.devicePointer;
+    default:
+      fail(CUTQC_ERR_ARG, "out must be device memory or pinned (page-locked, mapped) host memory");
+  }
+}
+
+static bool is_host_memory(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeHost;
+}
+
 static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
                       cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr) {
@@ -775,6 +811,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     }
     c.status = status_word(ds);
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
+    c.out_host = final_step && is_host_memory(out);
     c.sum = final_step ? sum : nullptr;
     c.profile = final_step;
     if (!(final_step && use_tc_final)) {
@@ -926,6 +963,8 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
       if (problems[i].n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
       if (!out[i]) fail(CUTQC_ERR_ARG, "out[i] is NULL");
     }
+    std::vector<void*> dout(n_problems);
+    for (int i = 0; i < n_problems; ++i) dout[i] = resolve_out(out[i]);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceState& ds = device_state();
     auto tensors_of = [&](const cutqc_problem* p) {
@@ -938,10 +977,10 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
     if (n_problems == 1) {
       const cutqc_problem* p = &problems[0];
       Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
-      run_plan(ds, P, 0, 0, tensors_of(p), out[0], sum_p, algo, s);
+      run_plan(ds, P, 0, 0, tensors_of(p), dout[0], sum_p, algo, s);
       return;
     }
-    run_batch(ds, problems, n_problems, out, algo, sum_p, s);
+    run_batch(ds, problems, n_problems, dout.data(), algo, sum_p, s);
   });
 }
 

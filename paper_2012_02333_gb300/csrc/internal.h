@@ -107,6 +107,7 @@ struct Contraction {
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
   int* status = nullptr;           // device status word (DeviceStatus) of this device
+  bool out_host = false;           // `out` is pinned host memory (written over the host link)
 };
 
 // k_cc.cu

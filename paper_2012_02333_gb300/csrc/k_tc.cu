@@ -608,8 +608,9 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool vec = a.vecB >= 4;
     const bool staged = vec && a.staged;
     // Staged stores (outputs larger than L2, where the store stream is
-    // DRAM-bound; an output that stays in L2 goes out directly from the
-    // registers, 16 bytes per row, which costs less latency): a warp's 32-column chunk goes out in two passes of
+    // DRAM-bound, and outputs in host memory; an output that stays in L2 goes
+    // out directly from the registers, 16 bytes per row, which costs less
+    // latency): a warp's 32-column chunk goes out in two passes of
     // 16 rows.  The 512 values of a pass are written to shared memory by row
     // and read back in output-address order: the 9 index bits (row bits 0-3,
     // column bits 0-4) are ranked by the output bit they deposit to, and lane
@@ -935,7 +936,9 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   a.scale = (float)c.scale;
   a.sum = c.sum;
   a.vecB = c.vecB;
-  a.staged = M * N >= (int64_t(1) << 25) ? 1 : 0;   // 128 MiB of FP32 output: beyond L2
+  // restage through shared memory for outputs beyond L2 (128 MiB of FP32) and
+  // for outputs in host memory, where whole-line stores matter most
+  a.staged = (c.out_host || M * N >= (int64_t(1) << 25)) ? 1 : 0;
   a.status = status;
   static int sms = 0;
   static bool attr = false;

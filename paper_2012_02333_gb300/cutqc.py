@@ -207,8 +207,8 @@ def cutqc_reconstruct_fd(problems: Sequence[Problem], outs: Sequence[torch.Tenso
     parr = (cutqc_problem * n)(*[p.c for p in problems])
     optr = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
     for p, o in zip(problems, outs):
-        if o.dtype != p.dtype or o.numel() != 2 ** p.n_qubits or not o.is_cuda:
-            raise ValueError("out must be a CUDA tensor of 2^n entries in the tensors' dtype")
+        if o.dtype != p.dtype or o.numel() != 2 ** p.n_qubits or not (o.is_cuda or o.is_pinned()):
+            raise ValueError("out must be a CUDA or pinned CPU tensor of 2^n entries in the tensors' dtype")
     sp = None
     if sum_p is not None:
         if sum_p.dtype != torch.float64 or sum_p.numel() < n or not sum_p.is_cuda:
@@ -221,14 +221,19 @@ def reconstruct_fd(cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor], alg
                    out: Optional[torch.Tensor] = None, with_sum: bool = True, stream=None,
                    device: Optional[torch.device] = None):
     """Full-definition reconstruction of one cut circuit.  Tensors on the host
-    are copied to the device first (pinned, on `stream`).  Returns
-    (probabilities on the device, FP64 sum on the device or None)."""
+    are copied to the device first (pinned, on `stream`).  `out` may be a CUDA
+    tensor or a pinned CPU tensor of 2^n entries; in the second case the
+    kernels write the probabilities straight into it (no separate copy).
+    Returns (out, FP64 sum on the device or None)."""
     dev = device or (tensors[0].device if tensors[0].is_cuda else torch.device("cuda", torch.cuda.current_device()))
     s = stream or torch.cuda.current_stream(dev)
     with torch.cuda.stream(s):
         dts = [t if t.is_cuda else t.to(dev, non_blocking=True) for t in tensors]
         if out is None:
             out = torch.empty(2 ** cc.n, dtype=dts[0].dtype, device=dev)
+        elif out.dtype != dts[0].dtype or out.numel() != 2 ** cc.n or not out.is_contiguous() or \
+                not (out.is_cuda or out.is_pinned()):
+            raise ValueError("out must be a contiguous CUDA or pinned CPU tensor of 2^n entries in the tensors' dtype")
         sp = torch.empty(1, dtype=torch.float64, device=dev) if with_sum else None
     p = Problem.from_cut(cc, dts)
     cutqc_reconstruct_fd([p], [out], algo, sp, s)

@@ -187,3 +187,33 @@ def test_supremacy_gpu_simulated_inputs(env, sup):
     for s, T in zip(cc.subs, T32):
         g = cutqc.cutqc_simulate_subcircuit(s, torch.float32).cpu().numpy()
         assert np.abs(g - T.reshape(-1)).max() <= 1e-6
+
+
+@pytest.mark.parametrize("algo", ["cc", "tc_bf16x3"])
+def test_output_into_pinned_host_memory(env, algo):
+    """out may be pinned host memory: the contraction writes the probabilities
+    into it directly; the result equals the device-output call exactly (the
+    same kernels and summation order), and the FP64 sum matches."""
+    torch, cutqc = env
+    cc, Ts = oracle_case("hwea26_s2", cases.hwea26_chain)
+    ts = to_dev(torch, [T.astype(np.float32) for T in Ts], torch.float32)
+    dev_out, dev_sp = cutqc.reconstruct_fd(cc, ts, algo=algo)
+    host_out = torch.full((2 ** cc.n,), -1.0, dtype=torch.float32).pin_memory()
+    o, sp = cutqc.reconstruct_fd(cc, ts, algo=algo, out=host_out)
+    torch.cuda.synchronize()
+    assert o.data_ptr() == host_out.data_ptr()
+    assert torch.equal(host_out, dev_out.cpu())
+    assert float(sp.item()) == pytest.approx(float(dev_sp.item()), abs=1e-9)
+
+
+def test_unregistered_host_output_is_rejected(env):
+    """Pageable host memory is refused before anything is launched."""
+    torch, cutqc = env
+    cc, Ts = oracle_case("hwea10_k1", cases.SMALL["hwea10_k1"])
+    p = cutqc.Problem.from_cut(cc, to_dev(torch, Ts, torch.float64))
+    buf = np.zeros(2 ** cc.n, dtype=np.float64)
+    arr = (cutqc.C.c_void_p * 1)(buf.ctypes.data)
+    st = cutqc._lib.cutqc_reconstruct_fd(cutqc.C.byref(p.c), 1, arr, cutqc.CUTQC_AUTO, None,
+                                          cutqc._stream_ptr(None))
+    assert st == cutqc.CUTQC_ERR_ARG
+    assert "pinned" in cutqc._lib.cutqc_last_error().decode()
