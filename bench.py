@@ -427,6 +427,8 @@ def run_other(args):
         outs = [torch.empty(2 ** cc.n, device=dev) for cc in batch]
         sums = torch.empty(len(batch), dtype=torch.float64, device=dev)
         ms = timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "auto", sums))
+        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "cc", sums)),
+                 "cc_only": "every instance on the FP32 CUDA-core form, same graph replay"}
         units, unit, dtype = sum(2 ** cc.n for cc in batch), "probs/s", "f32 (per instance cc or bf16x3/x6)"
         cfg = {"workload": "batch64_hwea_aqft_bv_fd_fp32", "instances": len(batch),
                "n_qubits": [cc.n for cc in batch], "n_cuts": [cc.n_cuts for cc in batch],
@@ -442,7 +444,9 @@ def run_other(args):
         loss = torch.empty(1, dtype=torch.float64, device=dev)
         ms_bwd = timed(lambda: cutqc.cutqc_reconstruct_backward(problem, grads, edges=cc.edges, loss_value=loss))
         extra = {"adjoint_ms": ms_bwd, "adjoint": "MaxCut loss and dL/dT of both subcircuits",
-                 "expected_cut": float(loss.item())}
+                 "expected_cut": float(loss.item()),
+                 "cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc", sp)),
+                 "cc_only": "forward on the FP32 CUDA-core form"}
         units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
         cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
     else:
@@ -452,6 +456,16 @@ def run_other(args):
         roles = dd.initial_roles(cc.n, 30)
         bins = torch.empty(2 ** 30, device=dev)
         ms = timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto"))
+        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "cc")),
+                 "cc_only": "one recursion with the final contraction on the FP32 CUDA-core form"}
+        del bins
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = dd.run(cc, ts, 30, 10, "bfs")
+        torch.cuda.synchronize()
+        extra.update({"ten_recursions_s": time.perf_counter() - t0, "recursions": len(st.recursions),
+                      "ten_recursions": "Algorithm 1 driver, BFS, 10 recursions of 2^30 bins, host wall clock"})
+        del st
         units, unit, dtype = 2 ** 30, "bins/s", "f32 bins, FP64 ranking"
         cfg = {"workload": "dd80_grid8x10_d10_30active_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts,
                "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
