@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
-                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80"],
+                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30"],
                     help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
@@ -449,6 +449,32 @@ def run_other(args):
                  "cc_only": "forward on the FP32 CUDA-core form"}
         units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
         cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
+    elif w == "attr_qaoa30":
+        # attribution of both QAOA-30 subcircuits from seeded synthetic variant
+        # distributions (uniform numbers normalised per variant, the shape of
+        # shot-count frequencies): 4^2 x 3^2 variants of 2^17 outcomes each
+        cc = circuits.qaoa_2cluster(15, 0)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        probs, outs = [], []
+        for sub in cc.subs:
+            v = torch.rand((4 ** sub.k_in) * (3 ** sub.k_out), 2 ** sub.d, generator=gen, device=dev)
+            probs.append((v / v.sum(dim=1, keepdim=True)).reshape(-1).contiguous())
+            outs.append(torch.empty((4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff), device=dev))
+
+        def attr_step():
+            for sub, p, o in zip(cc.subs, probs, outs):
+                cutqc.cutqc_attribute(sub, p, o)
+        ms = timed(attr_step)
+        bytes_alg = sum(p.numel() * 4 + o.numel() * 4 for p, o in zip(probs, outs))
+        pk, pk_src = peaks()
+        extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                              "traffic": None, "algorithmic_bytes": bytes_alg, "peak_file": pk_src}}
+        units, unit, dtype = sum(o.numel() for o in outs), "tensor entries/s", "f32 in, compensated f32 sums"
+        cfg = {"workload": "attr_qaoa30_fp32", "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
+               "inputs": "seeded uniform variant distributions normalised per variant (synthetic shot frequencies)",
+               "step": "Eq. 3 then Eq. 2 for both subcircuits"}
     else:
         cc = circuits.grid_blocks(8, 10, 10, 0, 2, 2, 8, 25)
         ts = cutqc.simulate_tensors(cc, torch.float32, dev)

@@ -198,6 +198,27 @@ typedef struct {
   double param;      /* angle for RX/RY/RZ/CP                                 */
 } cutqc_gate;
 
+/* Attribution of measured variant distributions (Sec. 3.2.2, Eq. 2 and
+ * Eq. 3): the tensor T[4^k_in][4^k_out][2^n_eff] of one subcircuit from the
+ * output distributions of its 4^k_in x 3^k_out physical variants (Fig. 3),
+ * for example normalised shot counts from a quantum device.
+ * variant_probs: device [4^k_in][3^k_out][2^d] in `dtype`; variant index s
+ * has one base-4 digit per init slot (slot 0 most significant; 0 = |0>,
+ * 1 = |1>, 2 = |+>, 3 = |+i>), then one base-3 digit per measurement slot
+ * (0 = Z basis, 1 = X, 2 = Y; X measured after H, Y after S^dagger then H),
+ * then the d local qubits (local qubit 0 most significant).  meas_qubit[j]:
+ * the local qubit measured for slot j; out_local[i]: the local qubit of output
+ * i (output 0 = most significant bit of x); every local qubit is exactly one
+ * of the two.  Eq. 3 weights outcome 0 by +1 and 1 by -1 for X, Y, Z and both
+ * by +1 for I (I and Z read the Z-basis variant); Eq. 2 combines the inits
+ * as I = |0><0| + |1><1|, Z = |0><0| - |1><1|, X = 2|+><+| - I,
+ * Y = 2|+i><+i| - I.  Entries below 2^-40 in magnitude are written as 0.
+ * tensor: device, caller-owned.  No workspace, no host synchronisation.
+ * Shape errors are returned before anything is launched; d <= 30. */
+CUTQC_API int cutqc_attribute(const void* variant_probs, int32_t d, int32_t k_in, const int32_t* meas_qubit,
+                              int32_t k_out, const int32_t* out_local, int32_t n_eff, int32_t dtype,
+                              void* tensor, void* stream);
+
 /* Produce one subcircuit's attributed tensor on the GPU (Fig. 3, Eq. 2-3):
  * simulates, in complex FP64, every variant (each init slot in |0>, |1>,
  * |+>, |+i>; each measurement slot measured in the Z, X, Y basis) of a

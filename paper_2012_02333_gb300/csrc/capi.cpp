@@ -984,6 +984,28 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
   });
 }
 
+int cutqc_attribute(const void* variant_probs, int32_t d, int32_t k_in, const int32_t* meas_qubit, int32_t k_out,
+                    const int32_t* out_local, int32_t n_eff, int32_t dtype, void* tensor, void* stream) {
+  return guarded([&] {
+    if (d < 1 || d > 30) fail(CUTQC_ERR_UNSUPPORTED, "attribution needs 1 <= d <= 30");
+    if (k_in < 0 || k_out < 0 || n_eff < 0 || k_in + k_out > kMaxCuts) fail(CUTQC_ERR_SHAPE, "bad slot counts");
+    if (k_out + n_eff != d) fail(CUTQC_ERR_SHAPE, "every local qubit must be an output or a measured cut qubit");
+    if (!variant_probs || !tensor || (k_out && !meas_qubit) || (n_eff && !out_local)) fail(CUTQC_ERR_ARG, "NULL array");
+    if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
+    std::vector<int> seen(d, 0), mq(k_out), oq(n_eff);
+    for (int j = 0; j < k_out; ++j) {
+      if (meas_qubit[j] < 0 || meas_qubit[j] >= d || seen[meas_qubit[j]]++) fail(CUTQC_ERR_SHAPE, "bad measured qubit");
+      mq[j] = meas_qubit[j];
+    }
+    for (int j = 0; j < n_eff; ++j) {
+      if (out_local[j] < 0 || out_local[j] >= d || seen[out_local[j]]++) fail(CUTQC_ERR_SHAPE, "bad output qubit");
+      oq[j] = out_local[j];
+    }
+    launch_attribute(variant_probs, dtype, d, k_in, mq.data(), k_out, oq.data(), n_eff, tensor,
+                     static_cast<cudaStream_t>(stream));
+  });
+}
+
 int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates, int32_t d, const int32_t* init_qubit,
                               int32_t k_in, const int32_t* meas_qubit, int32_t k_out, const int32_t* out_local,
                               int32_t n_eff, int32_t dtype, void* tensor, void* stream) {

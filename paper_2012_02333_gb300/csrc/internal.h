@@ -145,6 +145,11 @@ void launch_compact(const Contraction& c, cudaStream_t s);
 void launch_cc_gemm(const Contraction& c, cudaStream_t s);
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 
+// k_attr.cu: tensor T[a][b][x] of one subcircuit from its variant distributions
+// P[s][mb][y] (Eq. 2, Eq. 3); arguments already validated
+void launch_attribute(const void* P, int dtype, int d, int k_in, const int* meas_q, int k_out, const int* out_q,
+                      int n_eff, void* tensor, cudaStream_t s);
+
 // k_tc.cu
 // One block, one thread: waits on a device flag that nothing sets, bounded by
 // `limit_us`, then records DEV_TIMEOUT in *status (the bounded-wait path of

@@ -78,13 +78,15 @@ _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
 _lib.cutqc_device_status.argtypes = [C.c_void_p]
+_lib.cutqc_attribute.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                 C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
 _lib.cutqc_selftest_wait.argtypes = [C.c_int32, C.c_void_p]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
-           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait"):
+           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -323,6 +325,29 @@ def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, dev
         gates, len(sub.gates), sub.d, _i32([q for q, _ in sub.in_slots]), sub.k_in,
         _i32([q for q, _ in sub.out_slots]), sub.k_out, _i32([q for q, _ in sub.outputs]), sub.n_eff,
         CUTQC_F64 if dtype == torch.float64 else CUTQC_F32, C.c_void_p(out.data_ptr()), s.cuda_stream))
+    return out
+
+
+def cutqc_attribute(sub: circuits.Subcircuit, variant_probs: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """Binding of cutqc_attribute: the attributed tensor of one subcircuit from
+    the output distributions of its variants, a CUDA tensor of
+    4^k_in * 3^k_out * 2^d entries ([s][mb][y], see the C header)."""
+    n_in = (4 ** sub.k_in) * (3 ** sub.k_out) * (2 ** sub.d)
+    if not variant_probs.is_cuda or not variant_probs.is_contiguous() or variant_probs.numel() != n_in or \
+            variant_probs.dtype not in (torch.float32, torch.float64):
+        raise ValueError("variant_probs must be a contiguous CUDA float tensor of 4^k_in*3^k_out*2^d entries")
+    n_out = (4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff)
+    if out is None:
+        out = torch.empty(n_out, dtype=variant_probs.dtype, device=variant_probs.device)
+    elif out.numel() != n_out or out.dtype != variant_probs.dtype or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor of 4^k_in*4^k_out*2^n_eff entries")
+    s = stream or torch.cuda.current_stream(variant_probs.device)
+    _check(_lib.cutqc_attribute(
+        C.c_void_p(variant_probs.data_ptr()), sub.d, sub.k_in, _i32([q for q, _ in sub.out_slots]), sub.k_out,
+        _i32([q for q, _ in sub.outputs]), sub.n_eff,
+        CUTQC_F64 if variant_probs.dtype == torch.float64 else CUTQC_F32, C.c_void_p(out.data_ptr()),
+        s.cuda_stream))
     return out
 
 

@@ -95,3 +95,22 @@ def test_simulator_argument_errors(capi):
     assert st == capi.CUTQC_ERR_SHAPE
     st = capi._lib.cutqc_simulate_subcircuit(g, 1, 40, None, 0, None, 0, capi._i32([0]), 1, 1, t, None)
     assert st == capi.CUTQC_ERR_UNSUPPORTED
+
+
+def test_attribution_argument_errors(capi):
+    p, t = C.c_void_p(0x2000), C.c_void_p(0x3000)
+    i32 = capi._i32
+    # 3 local qubits: one measured cut qubit and two outputs
+    ok_args = (p, 3, 1, i32([2]), 1, i32([0, 1]), 2, capi.CUTQC_F32, t, None)
+    bad = [
+        ((p, 3, 1, i32([2]), 1, i32([0, 1]), 1, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_SHAPE),   # a qubit unassigned
+        ((p, 3, 1, i32([1]), 1, i32([0, 1]), 2, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_SHAPE),   # qubit used twice
+        ((p, 3, 1, i32([3]), 1, i32([0, 1]), 2, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_SHAPE),   # out of range
+        ((p, 3, 7, i32([2]), 6, i32([0, 1]), 2, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_SHAPE),   # K > 12 slots
+        ((None, 3, 1, i32([2]), 1, i32([0, 1]), 2, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_ARG),
+        ((p, 3, 1, i32([2]), 1, i32([0, 1]), 2, 7, t, None), capi.CUTQC_ERR_ARG),                   # dtype
+        ((p, 31, 0, None, 0, i32(list(range(31))), 31, capi.CUTQC_F32, t, None), capi.CUTQC_ERR_UNSUPPORTED),
+    ]
+    for args, status in bad:
+        assert capi._lib.cutqc_attribute(*args) == status, args
+    assert ok_args[1] == 3

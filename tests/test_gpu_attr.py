@@ -1,0 +1,118 @@
+"""GPU parity of the attribution entry point (Sec. 3.2.2, Eq. 2 then Eq. 3):
+variant distributions -> Pauli-indexed subcircuit tensors, against the FP64
+oracle's einsum form of the same equations, element by element.  Inputs: the
+oracle's own simulated variant distributions of the test circuits, and seeded
+random distributions (any non-negative numbers normalised per variant, as from
+shot counts) so that every sign and coefficient is exercised with values the
+physics would not produce."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+sys.path.insert(0, os.path.dirname(__file__))
+import cases  # noqa: E402
+from test_gpu_fd import env  # noqa: E402,F401
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["hwea10_k1", "bv6_k1", "grid3x4_k3", "qaoa8_k4", "aqft8_k4", "grid4x4_s4", "grid4x5_k5", "hwea14_skinny",
+         "nocut6"]   # k_in 0..4 (4: the single-kernel form), k_out 0..4
+
+
+def subcircuits():
+    for name in NAMES:
+        cc = cases.SMALL[name]()
+        for i, s in enumerate(cc.subs):
+            yield f"{name}/{i}", s
+
+
+@pytest.mark.parametrize("label,sub", list(subcircuits()), ids=lambda v: v if isinstance(v, str) else "")
+def test_attribute_simulated_variants(env, label, sub):
+    torch, cutqc = env
+    from oracle import attribution as at
+    p = at.variant_probabilities(sub)
+    want = at.attribute(sub, p).reshape(-1)
+    got64 = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), dtype=torch.float64, device="cuda"))
+    assert np.abs(got64.cpu().numpy() - want).max() <= 1e-12
+    p32 = p.astype(np.float32)
+    want32 = at.attribute(sub, p32.astype(np.float64)).reshape(-1)
+    got32 = cutqc.cutqc_attribute(sub, torch.tensor(p32.reshape(-1), device="cuda"))
+    assert np.abs(got32.double().cpu().numpy() - want32).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["qaoa8_k4", "grid4x5_k5", "aqft8_k4"])
+def test_attribute_random_distributions(env, name):
+    torch, cutqc = env
+    from oracle import attribution as at
+    rng = np.random.default_rng(7)
+    for sub in cases.SMALL[name]().subs:
+        shape = (4 ** sub.k_in, 3 ** sub.k_out, 2 ** sub.d)
+        p = rng.random(shape)
+        p /= p.sum(axis=2, keepdims=True)
+        want = at.attribute(sub, p).reshape(-1)
+        got = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), device="cuda"))
+        assert np.abs(got.cpu().numpy() - want).max() <= 1e-12
+
+
+def test_attribute_matches_the_simulator_path(env):
+    """Attributing the oracle's variant distributions on the GPU gives the
+    tensors the GPU simulator produces (its own attribution) for the
+    benchmark circuit's two subcircuits."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    cc = cases.supremacy_4x6()
+    for sub in cc.subs:
+        p = torch.tensor(at.variant_probabilities(sub).reshape(-1), device="cuda")
+        got = cutqc.cutqc_attribute(sub, p)
+        sim = cutqc.cutqc_simulate_subcircuit(sub, torch.float64)
+        assert torch.abs(got - sim).max().item() <= 1e-12
+
+
+def synthetic_sub(d, k_in, k_out, seed):
+    """A subcircuit layout without gates (the attribution only needs the slot
+    and output qubits): random distinct local qubits for the measured slots."""
+    from types import SimpleNamespace
+    rng = np.random.default_rng(seed)
+    perm = [int(q) for q in rng.permutation(d)]
+    meas = perm[:k_out]
+    outs = sorted(perm[k_out:])
+    return SimpleNamespace(d=d, k_in=k_in, k_out=k_out, n_eff=d - k_out,
+                           in_slots=[(q, i) for i, q in enumerate(perm[:k_in])],
+                           out_slots=[(q, i) for i, q in enumerate(meas)],
+                           outputs=[(q, q) for q in outs])
+
+
+@pytest.mark.parametrize("d,k_in,k_out", [(8, 1, 5), (9, 0, 6), (7, 4, 1), (6, 5, 0), (5, 2, 4), (3, 0, 2)])
+def test_attribute_all_kernel_forms(env, d, k_in, k_out):
+    """Slot counts that select each form: k_out > 4 (outcome gather), k_in > 3
+    (single kernel), n_eff < 2, the variant-centred form; random layouts of
+    the measured qubits among the local qubits."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    rng = np.random.default_rng(d * 100 + k_in * 10 + k_out)
+    sub = synthetic_sub(d, k_in, k_out, seed=d + k_in + k_out)
+    p = rng.random((4 ** k_in, 3 ** k_out, 2 ** d))
+    p /= p.sum(axis=2, keepdims=True)
+    want = at.attribute(sub, p).reshape(-1)
+    got = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), device="cuda"))
+    assert np.abs(got.cpu().numpy() - want).max() <= 1e-12
+    got32 = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), dtype=torch.float32, device="cuda"))
+    want32 = at.attribute(sub, p.astype(np.float32).astype(np.float64)).reshape(-1)
+    assert np.abs(got32.double().cpu().numpy() - want32).max() <= 1e-6
+
+
+def test_attribute_into_unaligned_output(env):
+    """An output that is not 16-byte aligned takes the scalar-store form."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    sub = cases.SMALL["qaoa8_k4"]().subs[0]
+    p = at.variant_probabilities(sub)
+    n = (4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff)
+    buf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    out = buf[1:]
+    cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), dtype=torch.float32, device="cuda"), out=out)
+    want = at.attribute(sub, p.astype(np.float32).astype(np.float64)).reshape(-1)
+    assert np.abs(out.double().cpu().numpy() - want).max() <= 1e-6
+    assert buf[0].item() == 0.0
