@@ -17,6 +17,8 @@ Modules
   reconstruct   full-definition sum (Sec. 3.2.3, Sec. 3.3, Sec. 4.2), dynamic
                 definition (Algorithm 1, Sec. 4.3), and the gradient of an
                 expectation value over the reconstructed distribution
+  metrics       the chi^2 loss of Eq. 16, total variation, and inverse-transform
+                sampling of outcomes from a reconstructed distribution
 
 Every function is pinned by a ``-m "not gpu"`` test against something other
 than itself: textbook states, the paper's worked single-cut formulas,

@@ -346,3 +346,75 @@ def test_grad_entry_central_differences():
         tm[c].reshape(tm[c].shape[0] * tm[c].shape[1], -1)[r, x] -= h
         fd = (G @ rc.fd_full(cc.subs, tp, cc.n, cc.n_cuts) - G @ rc.fd_full(cc.subs, tm, cc.n, cc.n_cuts)) / (2 * h)
         assert rc.grad_entry(cc.subs, Ts, cc.n, cc.n_cuts, c, r, x, f) == pytest.approx(fd, abs=1e-8)
+
+
+# ---- Eq. 16 chi^2 loss, total variation, inverse-transform sampling --------
+
+def test_chi_square_closed_forms():
+    from oracle import metrics as mt
+    # identical distributions: 0
+    p = np.random.default_rng(1).random(64)
+    p /= p.sum()
+    assert mt.chi_square(p, p) == 0.0
+    # a point mass against a fair coin: (1 - 1/2)^2 / (3/2) + (0 - 1/2)^2 / (1/2) = 1/6 + 1/2
+    assert mt.chi_square([1.0, 0.0], [0.5, 0.5]) == pytest.approx(2.0 / 3.0, abs=1e-15)
+    # disjoint supports: every term is (a + b)^2 / (a + b) = a + b, so chi^2 = 2
+    assert mt.chi_square([0.5, 0.5, 0, 0], [0, 0, 0.25, 0.75]) == pytest.approx(2.0, abs=1e-15)
+    # zero-weight outcomes on both sides contribute nothing (the reading for a_i + b_i = 0)
+    assert mt.chi_square([1.0, 0.0, 0.0], [0.5, 0.5, 0.0]) == pytest.approx(2.0 / 3.0, abs=1e-15)
+    # symmetric in its arguments
+    q = np.random.default_rng(2).random(64)
+    q /= q.sum()
+    assert mt.chi_square(p, q) == pytest.approx(mt.chi_square(q, p), rel=1e-14)
+
+
+def test_chi_square_small_differences_match_the_expansion():
+    """For b = a + d with small d, (d_i)^2 / (2 a_i + d_i) ~ d_i^2 / (2 a_i):
+    the leading term of the expansion, checked to relative O(|d|/a)."""
+    from oracle import metrics as mt
+    rng = np.random.default_rng(3)
+    a = rng.random(256) + 0.5
+    a /= a.sum()
+    d = 1e-6 * rng.standard_normal(256)
+    d -= d.mean()
+    approx = float(np.sum(d ** 2 / (2 * a)))
+    assert mt.chi_square(a, a + d) == pytest.approx(approx, rel=1e-3)
+
+
+def test_total_variation_closed_forms():
+    from oracle import metrics as mt
+    assert mt.total_variation([0.5, 0.5, 0, 0], [0, 0, 0.25, 0.75]) == pytest.approx(1.0)
+    assert mt.total_variation([1.0, 0.0], [0.5, 0.5]) == pytest.approx(0.5)
+    p = np.full(8, 1 / 8)
+    assert mt.total_variation(p, p) == 0.0
+
+
+def test_sampling_special_cases():
+    from oracle import metrics as mt
+    # a point mass is always drawn
+    p = np.zeros(16)
+    p[11] = 1.0
+    assert (mt.sample(p, [0.0, 0.3, 0.999999]) == 11).all()
+    # uniform over 4: u in [k/4, (k+1)/4) draws k
+    assert list(mt.sample([0.25] * 4, [0.0, 0.2499, 0.25, 0.5, 0.74, 0.999])) == [0, 0, 1, 2, 2, 3]
+    # negative entries (rounding residue) carry no weight and are never drawn
+    q = np.array([0.5, -1e-9, 0.0, 0.5])
+    xs = mt.sample(q, np.linspace(0, 0.999, 200))
+    assert set(xs.tolist()) == {0, 3}
+    # unnormalised weights: drawn in proportion
+    assert list(mt.sample([1.0, 3.0], [0.24, 0.26])) == [0, 1]
+
+
+def test_sampling_frequencies_follow_the_distribution():
+    """Law of large numbers on a seeded stream: 200k draws from a 16-outcome
+    distribution, Pearson statistic below the 0.999 quantile of chi^2 with 15
+    degrees of freedom (37.7)."""
+    from oracle import metrics as mt
+    rng = np.random.default_rng(5)
+    p = rng.random(16) ** 3
+    p /= p.sum()
+    n = 200_000
+    xs = mt.sample(p, rng.random(n))
+    counts = np.bincount(xs, minlength=16)
+    stat = float(np.sum((counts - n * p) ** 2 / (n * p)))
+    assert stat < 37.7
