@@ -15,7 +15,8 @@ weights w_i = max(p_i, 0) (a reconstructed quasi-probability can be slightly
 negative from rounding; negative entries are given no weight), cumulative
 sums C_x = sum_{i <= x} w_i in order, and for each uniform u in [0, 1) the
 smallest x with C_x > u * C_last.  The uniforms are inputs, so both sides
-draw the same outcomes.
+draw the same outcomes.  When no outcome carries weight (C_last = 0) there is
+nothing to draw; every draw is then -1.
 """
 from __future__ import annotations
 
@@ -50,6 +51,8 @@ def cumulative(p) -> np.ndarray:
 def sample(p, u) -> np.ndarray:
     """Outcome index for each uniform u: the smallest x with C_x > u * C_last."""
     C = cumulative(p)
+    if not C[-1] > 0.0:
+        return np.full(np.shape(u), -1, dtype=np.int64)
     t = np.asarray(u, dtype=np.float64) * C[-1]
     x = np.searchsorted(C, t, side="right")
     return np.minimum(x, len(C) - 1).astype(np.int64)

@@ -403,6 +403,8 @@ def test_sampling_special_cases():
     assert set(xs.tolist()) == {0, 3}
     # unnormalised weights: drawn in proportion
     assert list(mt.sample([1.0, 3.0], [0.24, 0.26])) == [0, 1]
+    # nothing carries weight: nothing can be drawn
+    assert list(mt.sample([0.0, -1e-12, 0.0], [0.1, 0.9])) == [-1, -1]
 
 
 def test_sampling_frequencies_follow_the_distribution():
