@@ -260,6 +260,28 @@ CUTQC_API int32_t cutqc_last_algo(void);
  * tensor-core contraction has run on this thread. */
 CUTQC_API int cutqc_last_split(int32_t* nseg, double* bound);
 
+/* The chi^2 loss of Eq. 16 between two distributions of n entries (device,
+ * `dtype`), sum_i (a_i - b_i)^2 / (a_i + b_i), into *chi2, and their total
+ * variation (1/2) sum_i |a_i - b_i| into *tv (both device doubles).  A term
+ * with a_i + b_i = 0 counts 0 (the paper leaves it undefined).  FP32 inputs:
+ * terms in FP32, summed in compensated FP32 then FP64.  The result does not
+ * depend on scheduling.  Uses a small per-device buffer of the library;
+ * calls that overlap on the GPU (several streams) race on it. */
+CUTQC_API int cutqc_distance(const void* a, const void* b, int64_t n, int32_t dtype, double* chi2, double* tv,
+                             void* stream);
+
+/* Draw n_samples outcomes from the distribution p of n entries (device,
+ * `dtype`; for example a full-definition output or dynamic-definition bins) by
+ * inverse transform: weights w_i = max(p_i, 0) (negative entries are rounding
+ * residue), and for each uniform u[k] in [0, 1) (device doubles, supplied by
+ * the caller) the smallest x whose running weight sum exceeds u[k] times the
+ * total.  out: device int64 [n_samples].  An outcome with zero weight is never
+ * drawn; if no outcome has weight every draw is -1.  Uses a per-device
+ * buffer of the library (grows to 16 bytes per 1024 entries); calls that
+ * overlap on the GPU race on it. */
+CUTQC_API int cutqc_sample(const void* p, int64_t n, int32_t dtype, const double* u, int64_t n_samples,
+                           int64_t* out, void* stream);
+
 /* Every kernel that waits (on an mbarrier, a grid barrier or a flag) gives
  * up after a bounded time instead of hanging the GPU, and records that in a
  * per-device status word; its outputs are then invalid.  cutqc_device_status

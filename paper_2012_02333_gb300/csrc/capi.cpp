@@ -204,6 +204,8 @@ struct DeviceState {
   cudaStream_t branch[kBranches] = {};
   cudaEvent_t fork = nullptr, join[kBranches] = {};
   int* status = nullptr;          // device status word written by kernels with bounded waits
+  void* aux = nullptr;            // distance / sampling scratch (zeroed when (re)allocated)
+  size_t aux_bytes = 0;
 };
 static std::map<int, DeviceState> g_dev;
 
@@ -253,6 +255,22 @@ static void check_status(DeviceState& ds) {
   if (v == DEV_TIMEOUT)
     fail(CUTQC_ERR_TIMEOUT, "a bounded device wait ran out; outputs of the calls since the last check are invalid");
   fail(CUTQC_ERR_DEVICE, "a device-side check failed; outputs of the calls since the last check are invalid");
+}
+
+// Scratch of cutqc_distance (a fixed region that must stay zeroed between
+// calls: its kernel resets it) followed by that of cutqc_sample.
+static size_t aux_distance_bytes() { return (distance_scratch_bytes() + 255) / 256 * 256; }
+static char* aux_buffer(DeviceState& ds, size_t sample_bytes) {
+  const size_t need = aux_distance_bytes() + (sample_bytes + 255) / 256 * 256;
+  if (need > ds.aux_bytes) {
+    if (ds.aux) CUTQC_CUDA(cudaFree(ds.aux));
+    ds.aux = nullptr;
+    ds.aux_bytes = 0;
+    CUTQC_CUDA(cudaMalloc(&ds.aux, need));
+    CUTQC_CUDA(cudaMemset(ds.aux, 0, need));
+    ds.aux_bytes = need;
+  }
+  return static_cast<char*>(ds.aux);
 }
 
 static void drop_graphs(DeviceState& ds) {
@@ -1270,6 +1288,9 @@ void cutqc_release(void) {
     if (kv.second.one) cudaFree(kv.second.one);
     if (kv.second.status) cudaFree(kv.second.status);
     kv.second.status = nullptr;
+    if (kv.second.aux) cudaFree(kv.second.aux);
+    kv.second.aux = nullptr;
+    kv.second.aux_bytes = 0;
     kv.second.ws = nullptr;
     kv.second.one = nullptr;
     kv.second.ws_bytes = 0;
@@ -1290,6 +1311,32 @@ int cutqc_last_split(int32_t* nseg, double* bound) {
     check_status(device_state());
     CUTQC_CUDA(cudaMemcpy(nseg, g_last_nseg, sizeof(int32_t), cudaMemcpyDeviceToHost));
     CUTQC_CUDA(cudaMemcpy(bound, g_last_bound, sizeof(double), cudaMemcpyDeviceToHost));
+  });
+}
+
+int cutqc_distance(const void* a, const void* b, int64_t n, int32_t dtype, double* chi2, double* tv,
+                   void* stream) {
+  return guarded([&] {
+    if (!a || !b || !chi2 || !tv) fail(CUTQC_ERR_ARG, "NULL pointer");
+    if (n < 1 || n > (int64_t(1) << 40)) fail(CUTQC_ERR_UNSUPPORTED, "distance needs 1 <= n <= 2^40");
+    if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
+    DeviceState& ds = device_state();
+    char* scratch = aux_buffer(ds, 0);
+    launch_distance(a, b, n, dtype, chi2, tv, scratch, static_cast<cudaStream_t>(stream));
+  });
+}
+
+int cutqc_sample(const void* p, int64_t n, int32_t dtype, const double* u, int64_t n_samples, int64_t* out,
+                 void* stream) {
+  return guarded([&] {
+    if (!p) fail(CUTQC_ERR_ARG, "p is NULL");
+    if (n < 1 || n > (int64_t(1) << 40)) fail(CUTQC_ERR_UNSUPPORTED, "sampling needs 1 <= n <= 2^40");
+    if (n_samples < 0) fail(CUTQC_ERR_ARG, "n_samples < 0");
+    if (n_samples > 0 && (!u || !out)) fail(CUTQC_ERR_ARG, "NULL u or out");
+    if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
+    DeviceState& ds = device_state();
+    char* scratch = aux_buffer(ds, sample_scratch_bytes(n)) + aux_distance_bytes();
+    launch_sample(p, n, dtype, u, n_samples, out, scratch, static_cast<cudaStream_t>(stream));
   });
 }
 

@@ -150,6 +150,16 @@ void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
 void launch_attribute(const void* P, int dtype, int d, int k_in, const int* meas_q, int k_out, const int* out_q,
                       int n_eff, void* tensor, cudaStream_t s);
 
+// k_metrics.cu: Eq. 16 chi^2 and total variation; inverse-transform sampling.
+// Scratch is the caller's (sizes below); the distance scratch must start
+// zeroed and is left zeroed.
+size_t distance_scratch_bytes();
+void launch_distance(const void* a, const void* b, int64_t n, int dtype, double* chi2, double* tv, void* scratch,
+                     cudaStream_t s);
+size_t sample_scratch_bytes(int64_t n);
+void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t m, int64_t* out, void* scratch,
+                   cudaStream_t s);
+
 // k_tc.cu
 // One block, one thread: waits on a device flag that nothing sets, bounded by
 // `limit_us`, then records DEV_TIMEOUT in *status (the bounded-wait path of

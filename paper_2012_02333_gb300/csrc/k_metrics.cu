@@ -1,0 +1,342 @@
+// Distances between distributions (Eq. 16) and sampling from them.
+//
+// k_distance: chi^2 = sum_i (a_i - b_i)^2 / (a_i + b_i) (Eq. 16; a term with
+//   a_i + b_i = 0 counts 0) and the total variation (1/2) sum_i |a_i - b_i|, in
+//   one streaming pass.  FP32 inputs: each term in FP32, summed in compensated
+//   FP32 (TwoSum) per thread and across the block; FP64 inputs in FP64.  Every
+//   block writes its two partial sums; the block that finishes last adds them
+//   in block order in FP64, so the result does not depend on scheduling.
+// k_sample_chunks / k_sample_scan / k_sample_draw: inverse-transform sampling.
+//   Weights w_i = max(p_i, 0) (negative entries are rounding residue and get
+//   no weight).  The weights are cut into chunks of 1024; a warp sums each
+//   chunk (compensated FP32, or FP64); one block forms the exclusive FP64
+//   prefix of the chunk sums and their total; then one warp per draw takes
+//   t = u * total, finds the chunk by binary search over the prefixes, the lane
+//   of 32 weights by a warp scan and the outcome by a scan of the lane's 32
+//   weights: the first index whose running sum exceeds what is left of t.  An
+//   outcome with no weight is never drawn: where rounding leaves t past a
+//   chunk's or lane's end, the last weighted index before it is taken; when no
+//   outcome has weight every draw is -1.
+#include <cuda_runtime.h>
+
+#include <type_traits>
+
+#include "internal.h"
+
+namespace cutqc {
+
+namespace {
+
+struct FF {
+  float s, c;
+};
+__device__ __forceinline__ FF ff_add(FF a, float b) {
+  const float s = a.s + b;
+  const float bb = s - a.s;
+  const float err = (a.s - (s - bb)) + (b - bb);
+  return {s, a.c + err};
+}
+__device__ __forceinline__ FF ff_merge(FF a, FF b) {
+  FF r = ff_add(a, b.s);
+  r.c += b.c;
+  return r;
+}
+__device__ __forceinline__ double ff_value(FF a) { return (double)a.s + (double)a.c; }
+
+constexpr int DIST_BLOCKS = 152 * 8;
+constexpr int CH = 1024;   // weights per chunk
+
+template <typename T>
+struct Acc {
+  using type = typename std::conditional<sizeof(T) == 8, double, FF>::type;
+};
+
+template <typename T>
+__device__ __forceinline__ void dist_term(T a, T b, typename Acc<T>::type& chi, typename Acc<T>::type& tv) {
+  const T d = a - b, s = a + b;
+  const T c = s != T(0) ? d * d / s : T(0);
+  if constexpr (sizeof(T) == 8) {
+    chi += c;
+    tv += fabs(d);
+  } else {
+    chi = ff_add(chi, c);
+    tv = ff_add(tv, fabsf(d));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_distance(const T* __restrict__ a, const T* __restrict__ b, int64_t n,
+                                                  double* __restrict__ part, unsigned* __restrict__ counter,
+                                                  double* __restrict__ chi2, double* __restrict__ tv_out) {
+  using A = typename Acc<T>::type;
+  A chi{}, tv{};
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, nth = (int64_t)gridDim.x * blockDim.x;
+  const bool vec = sizeof(T) == 4 && (n % 4) == 0 && (reinterpret_cast<uintptr_t>(a) & 15) == 0 &&
+                   (reinterpret_cast<uintptr_t>(b) & 15) == 0;
+  if constexpr (sizeof(T) == 4) {
+    if (vec) {
+      const float4* a4 = reinterpret_cast<const float4*>(a);
+      const float4* b4 = reinterpret_cast<const float4*>(b);
+      for (int64_t i = tid; i < n / 4; i += nth) {
+        const float4 x = __ldcs(a4 + i), y = __ldcs(b4 + i);
+        dist_term<float>(x.x, y.x, chi, tv);
+        dist_term<float>(x.y, y.y, chi, tv);
+        dist_term<float>(x.z, y.z, chi, tv);
+        dist_term<float>(x.w, y.w, chi, tv);
+      }
+    }
+  }
+  if (!vec)
+    for (int64_t i = tid; i < n; i += nth) dist_term<T>(__ldcs(a + i), __ldcs(b + i), chi, tv);
+  // block reduction, then the last block adds the block partials in order
+  __shared__ double red[2][8];
+  __shared__ bool last;
+  double cv, tvv;
+  if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      chi += __shfl_xor_sync(0xffffffffu, chi, o);
+      tv += __shfl_xor_sync(0xffffffffu, tv, o);
+    }
+    cv = chi;
+    tvv = tv;
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      chi = ff_merge(chi, FF{__shfl_xor_sync(0xffffffffu, chi.s, o), __shfl_xor_sync(0xffffffffu, chi.c, o)});
+      tv = ff_merge(tv, FF{__shfl_xor_sync(0xffffffffu, tv.s, o), __shfl_xor_sync(0xffffffffu, tv.c, o)});
+    }
+    cv = ff_value(chi);
+    tvv = ff_value(tv);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = cv;
+    red[1][threadIdx.x >> 5] = tvv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double c = 0.0, t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      c += red[0][w];
+      t += red[1][w];
+    }
+    part[2 * blockIdx.x] = c;
+    part[2 * blockIdx.x + 1] = t;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double c = 0.0, t = 0.0;
+    for (unsigned k = 0; k < gridDim.x; ++k) {
+      c += __ldcg(part + 2 * k);
+      t += __ldcg(part + 2 * k + 1);
+    }
+    *chi2 = c;
+    *tv_out = 0.5 * t;
+    *counter = 0u;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ float weight32(T v) {
+  return v > T(0) ? (float)v : 0.0f;
+}
+
+// a warp per chunk of CH weights: L1[c] = sum of the chunk's weights
+template <typename T>
+__global__ void k_sample_chunks(const T* __restrict__ p, int64_t n, double* __restrict__ L1, int64_t nch) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < nch; c += nw) {
+    const int64_t i0 = c * CH;
+    double sum;
+    if constexpr (sizeof(T) == 8) {
+      double acc = 0.0;
+      for (int k = lane; k < CH; k += 32) {
+        const int64_t i = i0 + k;
+        if (i < n) acc += fmax(p[i], 0.0);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      sum = acc;
+    } else {
+      FF acc{};
+      for (int k = lane; k < CH; k += 32) {
+        const int64_t i = i0 + k;
+        if (i < n) acc = ff_add(acc, weight32(p[i]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        acc = ff_merge(acc, FF{__shfl_xor_sync(0xffffffffu, acc.s, o), __shfl_xor_sync(0xffffffffu, acc.c, o)});
+      sum = ff_value(acc);
+    }
+    if (lane == 0) L1[c] = sum;
+  }
+}
+
+// one block of 1024 threads: P1 = exclusive prefix of L1 (FP64), *total
+__global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__ L1, int64_t nch,
+                                                      double* __restrict__ P1, double* __restrict__ total) {
+  __shared__ double seg[1024];
+  const int t = threadIdx.x;
+  const int64_t per = (nch + 1023) / 1024;
+  const int64_t lo = t * per, hi = min(nch, lo + per);
+  double s = 0.0;
+  for (int64_t j = lo; j < hi; ++j) s += L1[j];
+  seg[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    double run = 0.0;
+    for (int k = 0; k < 1024; ++k) {
+      const double v = seg[k];
+      seg[k] = run;
+      run += v;
+    }
+    *total = run;
+  }
+  __syncthreads();
+  double run = seg[t];
+  for (int64_t j = lo; j < hi; ++j) {
+    P1[j] = run;
+    run += L1[j];
+  }
+}
+
+// one warp per draw
+template <typename T>
+__global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* __restrict__ P1,
+                              const double* __restrict__ L1, int64_t nch, const double* __restrict__ total,
+                              const double* __restrict__ u, int64_t m, int64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double tot = *total;
+  for (int64_t k = warp; k < m; k += nw) {
+    if (!(tot > 0.0)) {   // no outcome carries weight
+      if (lane == 0) out[k] = -1;
+      continue;
+    }
+    const double t = u[k] * tot;
+    // chunk: the largest c with P1[c] <= t that carries weight
+    int64_t lo = 0, hi = nch - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (P1[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    int64_t c = lo;
+    while (c > 0 && L1[c] <= 0.0) --c;   // rounding put t past the weighted chunks
+    const double r = t - P1[c];
+    // lane sums of the chunk's 32 runs of 32 weights
+    const int64_t base = c * CH + 32 * lane;
+    FF ls{};
+    double ld = 0.0;
+    for (int i = 0; i < 32; ++i) {
+      const int64_t idx = base + i;
+      if (idx < n) {
+        if constexpr (sizeof(T) == 8)
+          ld += fmax(p[idx], 0.0);
+        else
+          ls = ff_add(ls, weight32(p[idx]));
+      }
+    }
+    const double lsum = sizeof(T) == 8 ? ld : ff_value(ls);
+    double incl = lsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const double excl = incl - lsum;
+    const unsigned over = __ballot_sync(0xffffffffu, incl > r && lsum > 0.0);
+    const unsigned weighted = __ballot_sync(0xffffffffu, lsum > 0.0);
+    const int L = over ? __ffs(over) - 1 : (weighted ? 31 - __clz(weighted) : 0);
+    if (lane == L) {
+      const double r2 = r - excl;
+      int64_t pick = -1, last_w = -1;
+      FF cs{};
+      double cd = 0.0;
+      for (int i = 0; i < 32 && pick < 0; ++i) {
+        const int64_t idx = base + i;
+        if (idx >= n) break;
+        double cum;
+        if constexpr (sizeof(T) == 8) {
+          const double w = fmax(p[idx], 0.0);
+          if (w > 0.0) last_w = idx;
+          cd += w;
+          cum = cd;
+          if (w > 0.0 && cum > r2) pick = idx;
+        } else {
+          const float w = weight32(p[idx]);
+          if (w > 0.0f) last_w = idx;
+          cs = ff_add(cs, w);
+          cum = ff_value(cs);
+          if (w > 0.0f && cum > r2) pick = idx;
+        }
+      }
+      if (pick < 0) pick = last_w >= 0 ? last_w : base;
+      out[k] = pick;
+    }
+  }
+}
+
+unsigned grid_for(int64_t work, int per_block, int cap) {
+  int64_t g = (work + per_block - 1) / per_block;
+  if (g > cap) g = cap;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace
+
+size_t distance_scratch_bytes() { return (size_t)DIST_BLOCKS * 2 * sizeof(double) + 256; }
+
+void launch_distance(const void* a, const void* b, int64_t n, int dtype, double* chi2, double* tv, void* scratch,
+                     cudaStream_t s) {
+  double* part = static_cast<double*>(scratch);
+  unsigned* counter = reinterpret_cast<unsigned*>(static_cast<char*>(scratch) + (size_t)DIST_BLOCKS * 16);
+  const unsigned g = grid_for(n, 256 * 4, DIST_BLOCKS);
+  if (dtype == CUTQC_F64)
+    k_distance<double><<<g, 256, 0, s>>>(static_cast<const double*>(a), static_cast<const double*>(b), n, part,
+                                         counter, chi2, tv);
+  else
+    k_distance<float><<<g, 256, 0, s>>>(static_cast<const float*>(a), static_cast<const float*>(b), n, part,
+                                        counter, chi2, tv);
+  count_launch();
+  check_launch("k_distance");
+}
+
+size_t sample_scratch_bytes(int64_t n) {
+  const int64_t nch = (n + CH - 1) / CH;
+  return (size_t)nch * 2 * sizeof(double) + 256;
+}
+
+void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t m, int64_t* out, void* scratch,
+                   cudaStream_t s) {
+  const int64_t nch = (n + CH - 1) / CH;
+  double* L1 = static_cast<double*>(scratch);
+  double* P1 = L1 + nch;
+  double* total = P1 + nch;
+  const unsigned gc = grid_for(nch * 32, 256, 152 * 16);
+  if (dtype == CUTQC_F64)
+    k_sample_chunks<double><<<gc, 256, 0, s>>>(static_cast<const double*>(p), n, L1, nch);
+  else
+    k_sample_chunks<float><<<gc, 256, 0, s>>>(static_cast<const float*>(p), n, L1, nch);
+  count_launch();
+  check_launch("k_sample_chunks");
+  k_sample_scan<<<1, 1024, 0, s>>>(L1, nch, P1, total);
+  count_launch();
+  check_launch("k_sample_scan");
+  if (m == 0) return;
+  const unsigned gd = grid_for(m * 32, 256, 152 * 16);
+  if (dtype == CUTQC_F64)
+    k_sample_draw<double><<<gd, 256, 0, s>>>(static_cast<const double*>(p), n, P1, L1, nch, total, u, m, out);
+  else
+    k_sample_draw<float><<<gd, 256, 0, s>>>(static_cast<const float*>(p), n, P1, L1, nch, total, u, m, out);
+  count_launch();
+  check_launch("k_sample_draw");
+}
+
+}  // namespace cutqc

@@ -78,6 +78,8 @@ _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
 _lib.cutqc_device_status.argtypes = [C.c_void_p]
+_lib.cutqc_distance.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.cutqc_sample.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.cutqc_attribute.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
                                  C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
 _lib.cutqc_selftest_wait.argtypes = [C.c_int32, C.c_void_p]
@@ -86,7 +88,7 @@ _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
-           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute"):
+           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute", "cutqc_distance", "cutqc_sample"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -143,6 +145,36 @@ def profile_read():
 def _i32(xs: Sequence[int]):
     arr = (C.c_int32 * max(len(xs), 1))(*[int(x) for x in xs])
     return arr
+
+
+def _dist_dtype(t: torch.Tensor) -> int:
+    if not t.is_cuda or not t.is_contiguous() or t.dtype not in (torch.float32, torch.float64):
+        raise ValueError("expected a contiguous CUDA float32 / float64 tensor")
+    return CUTQC_F64 if t.dtype == torch.float64 else CUTQC_F32
+
+
+def cutqc_distance(a: torch.Tensor, b: torch.Tensor, stream=None):
+    """Binding of cutqc_distance: (chi^2 of Eq. 16, total variation) of two
+    distributions as CUDA float64 scalars (no host synchronisation)."""
+    dt = _dist_dtype(a)
+    if _dist_dtype(b) != dt or a.numel() != b.numel():
+        raise ValueError("a and b must have the same dtype and size")
+    out = torch.empty(2, dtype=torch.float64, device=a.device)
+    _check(_lib.cutqc_distance(C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr()), a.numel(), dt,
+                               C.c_void_p(out.data_ptr()), C.c_void_p(out.data_ptr() + 8), _stream_ptr(stream)))
+    return out[0], out[1]
+
+
+def cutqc_sample(p: torch.Tensor, u: torch.Tensor, stream=None) -> torch.Tensor:
+    """Binding of cutqc_sample: one outcome index (int64) per uniform in u
+    (CUDA float64, values in [0, 1))."""
+    dt = _dist_dtype(p)
+    if not u.is_cuda or u.dtype != torch.float64 or not u.is_contiguous():
+        raise ValueError("u must be a contiguous CUDA float64 tensor")
+    out = torch.empty(u.numel(), dtype=torch.int64, device=p.device)
+    _check(_lib.cutqc_sample(C.c_void_p(p.data_ptr()), p.numel(), dt, C.c_void_p(u.data_ptr()), u.numel(),
+                             C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
 
 
 def device_status(stream=None) -> None:

@@ -114,3 +114,15 @@ def test_attribution_argument_errors(capi):
     for args, status in bad:
         assert capi._lib.cutqc_attribute(*args) == status, args
     assert ok_args[1] == 3
+
+
+def test_distance_and_sampling_argument_errors(capi):
+    a, b = C.c_void_p(0x2000), C.c_void_p(0x3000)
+    f = capi._lib
+    assert f.cutqc_distance(a, None, 8, capi.CUTQC_F32, a, b, None) == capi.CUTQC_ERR_ARG
+    assert f.cutqc_distance(a, b, 0, capi.CUTQC_F32, a, b, None) == capi.CUTQC_ERR_UNSUPPORTED
+    assert f.cutqc_distance(a, b, 8, 5, a, b, None) == capi.CUTQC_ERR_ARG
+    assert f.cutqc_sample(None, 8, capi.CUTQC_F32, a, 4, b, None) == capi.CUTQC_ERR_ARG
+    assert f.cutqc_sample(a, 8, capi.CUTQC_F32, None, 4, b, None) == capi.CUTQC_ERR_ARG
+    assert f.cutqc_sample(a, 8, capi.CUTQC_F32, a, -1, b, None) == capi.CUTQC_ERR_ARG
+    assert f.cutqc_sample(a, 1 << 41, capi.CUTQC_F32, a, 4, b, None) == capi.CUTQC_ERR_UNSUPPORTED
