@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
-                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30"],
+                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "metrics_qaoa30"],
                     help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
@@ -449,6 +449,33 @@ def run_other(args):
                  "cc_only": "forward on the FP32 CUDA-core form"}
         units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
         cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
+    elif w == "metrics_qaoa30":
+        # Eq. 16 chi^2 and total variation between the split-precision and the
+        # FP32 CUDA-core reconstructions of QAOA-30 (2^30 entries each), and
+        # 2^20 draws from the first (uniforms from a seeded generator)
+        cc = circuits.qaoa_2cluster(15, 0)
+        ts = cutqc.simulate_tensors(cc, torch.float32, dev)
+        pa, _ = cutqc.reconstruct_fd(cc, ts, algo="auto")
+        pb, _ = cutqc.reconstruct_fd(cc, ts, algo="cc")
+        del ts
+        ms = timed(lambda: cutqc.cutqc_distance(pa, pb))
+        chi, tv = cutqc.cutqc_distance(pa, pb)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        u = torch.rand(1 << 20, dtype=torch.float64, generator=gen, device=dev)
+        ms_s = timed(lambda: cutqc.cutqc_sample(pa, u))
+        bytes_alg = 2 * pa.numel() * 4
+        pk, pk_src = peaks()
+        extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                              "algorithmic_bytes": bytes_alg, "peak_file": pk_src},
+                 "chi2_tc_vs_cc": chi.item(), "tv_tc_vs_cc": tv.item(),
+                 "sample_ms": ms_s, "samples": u.numel(),
+                 "sample_rate_per_s": u.numel() / (ms_s / 1e3)}
+        units, unit, dtype = pa.numel(), "entries/s", "f32 in, compensated f32 sums, f64 total"
+        cfg = {"workload": "metrics_qaoa30_fp32", "n": pa.numel(),
+               "step": "chi^2 (Eq. 16) and total variation of two 2^30-entry distributions; sampling timed beside it"}
+        del pb
     elif w == "attr_qaoa30":
         # attribution of both QAOA-30 subcircuits from seeded synthetic variant
         # distributions (uniform numbers normalised per variant, the shape of

@@ -8,12 +8,14 @@
 //   in block order in FP64, so the result does not depend on scheduling.
 // k_sample_chunks / k_sample_scan / k_sample_draw: inverse-transform sampling.
 //   Weights w_i = max(p_i, 0) (negative entries are rounding residue and get
-//   no weight).  The weights are cut into chunks of 1024; a warp sums each
-//   chunk (compensated FP32, or FP64); one block forms the exclusive FP64
-//   prefix of the chunk sums and their total; then one warp per draw takes
-//   t = u * total, finds the chunk by binary search over the prefixes, the lane
-//   of 32 weights by a warp scan and the outcome by a scan of the lane's 32
-//   weights: the first index whose running sum exceeds what is left of t.  An
+//   no weight).  The weights are cut into chunks of 1024 and the chunks into
+//   tiles of 1024; a warp sums each chunk (compensated FP32, or FP64) and
+//   each tile of chunk sums (FP64); one block scans the tile sums, and a warp
+//   per tile turns them into the exclusive FP64 prefix of every chunk.  One
+//   warp per draw takes t = u * total, finds the chunk by binary search over
+//   the chunk prefixes, the lane of 32 weights by a warp scan and the outcome
+//   by a scan of the lane's 32 weights: the first index whose running sum
+//   exceeds what is left of t.  An
 //   outcome with no weight is never drawn: where rounding leaves t past a
 //   chunk's or lane's end, the last weighted index before it is taken; when no
 //   outcome has weight every draw is -1.
@@ -54,7 +56,11 @@ struct Acc {
 template <typename T>
 __device__ __forceinline__ void dist_term(T a, T b, typename Acc<T>::type& chi, typename Acc<T>::type& tv) {
   const T d = a - b, s = a + b;
-  const T c = s != T(0) ? d * d / s : T(0);
+  T c;
+  if constexpr (sizeof(T) == 8)
+    c = s != 0.0 ? d * d / s : 0.0;
+  else
+    c = s != 0.0f ? __fdividef(d * d, s) : 0.0f;   // within 2 ulp; the term is a summand
   if constexpr (sizeof(T) == 8) {
     chi += c;
     tv += fabs(d);
@@ -77,13 +83,31 @@ __global__ void __launch_bounds__(256) k_distance(const T* __restrict__ a, const
     if (vec) {
       const float4* a4 = reinterpret_cast<const float4*>(a);
       const float4* b4 = reinterpret_cast<const float4*>(b);
-      for (int64_t i = tid; i < n / 4; i += nth) {
+      // two float4 of each input per step into two independent accumulator pairs
+      A chi2_{}, tv2_{};
+      const int64_t n4 = n / 4;
+      int64_t i = tid;
+      for (; i + nth < n4; i += 2 * nth) {
+        const float4 x = __ldcs(a4 + i), y = __ldcs(b4 + i);
+        const float4 x2 = __ldcs(a4 + i + nth), y2 = __ldcs(b4 + i + nth);
+        dist_term<float>(x.x, y.x, chi, tv);
+        dist_term<float>(x2.x, y2.x, chi2_, tv2_);
+        dist_term<float>(x.y, y.y, chi, tv);
+        dist_term<float>(x2.y, y2.y, chi2_, tv2_);
+        dist_term<float>(x.z, y.z, chi, tv);
+        dist_term<float>(x2.z, y2.z, chi2_, tv2_);
+        dist_term<float>(x.w, y.w, chi, tv);
+        dist_term<float>(x2.w, y2.w, chi2_, tv2_);
+      }
+      if (i < n4) {
         const float4 x = __ldcs(a4 + i), y = __ldcs(b4 + i);
         dist_term<float>(x.x, y.x, chi, tv);
         dist_term<float>(x.y, y.y, chi, tv);
         dist_term<float>(x.z, y.z, chi, tv);
         dist_term<float>(x.w, y.w, chi, tv);
       }
+      chi = ff_merge(chi, chi2_);
+      tv = ff_merge(tv, tv2_);
     }
   }
   if (!vec)
@@ -164,9 +188,28 @@ __global__ void k_sample_chunks(const T* __restrict__ p, int64_t n, double* __re
       sum = acc;
     } else {
       FF acc{};
-      for (int k = lane; k < CH; k += 32) {
-        const int64_t i = i0 + k;
-        if (i < n) acc = ff_add(acc, weight32(p[i]));
+      if (i0 + CH <= n && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        // a whole chunk: 8 float4 per lane, two accumulators
+        const float4* p4 = reinterpret_cast<const float4*>(p + i0);
+        FF acc2{};
+#pragma unroll
+        for (int k = 0; k < CH / 128; k += 2) {
+          const float4 q = __ldcs(p4 + k * 32 + lane), q2 = __ldcs(p4 + (k + 1) * 32 + lane);
+          acc = ff_add(acc, weight32(q.x));
+          acc2 = ff_add(acc2, weight32(q2.x));
+          acc = ff_add(acc, weight32(q.y));
+          acc2 = ff_add(acc2, weight32(q2.y));
+          acc = ff_add(acc, weight32(q.z));
+          acc2 = ff_add(acc2, weight32(q2.z));
+          acc = ff_add(acc, weight32(q.w));
+          acc2 = ff_add(acc2, weight32(q2.w));
+        }
+        acc = ff_merge(acc, acc2);
+      } else {
+        for (int k = lane; k < CH; k += 32) {
+          const int64_t i = i0 + k;
+          if (i < n) acc = ff_add(acc, weight32(p[i]));
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1)
@@ -177,15 +220,32 @@ __global__ void k_sample_chunks(const T* __restrict__ p, int64_t n, double* __re
   }
 }
 
-// one block of 1024 threads: P1 = exclusive prefix of L1 (FP64), *total
-__global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__ L1, int64_t nch,
-                                                      double* __restrict__ P1, double* __restrict__ total) {
+// a warp per tile of CH chunk sums: T2[g] = sum of the tile's chunk sums
+__global__ void k_sample_tiles(const double* __restrict__ L1, int64_t nch, double* __restrict__ T2, int64_t nt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < nt; g += nw) {
+    double acc = 0.0;
+    for (int k = lane; k < CH; k += 32) {
+      const int64_t c = g * CH + k;
+      if (c < nch) acc += L1[c];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) T2[g] = acc;
+  }
+}
+
+// one block of 1024 threads: P2 = exclusive prefix of the tile sums (FP64), *total
+__global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__ T2, int64_t nt,
+                                                      double* __restrict__ P2, double* __restrict__ total) {
   __shared__ double seg[1024];
   const int t = threadIdx.x;
-  const int64_t per = (nch + 1023) / 1024;
-  const int64_t lo = t * per, hi = min(nch, lo + per);
+  const int64_t per = (nt + 1023) / 1024;
+  const int64_t lo = t * per, hi = min(nt, lo + per);
   double s = 0.0;
-  for (int64_t j = lo; j < hi; ++j) s += L1[j];
+  for (int64_t j = lo; j < hi; ++j) s += T2[j];
   seg[t] = s;
   __syncthreads();
   if (t == 0) {
@@ -200,8 +260,31 @@ __global__ void __launch_bounds__(1024) k_sample_scan(const double* __restrict__
   __syncthreads();
   double run = seg[t];
   for (int64_t j = lo; j < hi; ++j) {
-    P1[j] = run;
-    run += L1[j];
+    P2[j] = run;
+    run += T2[j];
+  }
+}
+
+// a warp per tile: P1[c] = P2[g] + exclusive prefix of the tile's chunk sums
+__global__ void k_sample_tile_scan(const double* __restrict__ L1, int64_t nch, const double* __restrict__ P2,
+                                   int64_t nt, double* __restrict__ P1) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = warp; g < nt; g += nw) {
+    double carry = P2[g];
+    for (int k0 = 0; k0 < CH; k0 += 32) {
+      const int64_t c = g * CH + k0 + lane;
+      const double v = c < nch ? L1[c] : 0.0;
+      double incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      if (c < nch) P1[c] = carry + (incl - v);
+      carry += __shfl_sync(0xffffffffu, incl, 31);
+    }
   }
 }
 
@@ -309,16 +392,18 @@ void launch_distance(const void* a, const void* b, int64_t n, int dtype, double*
 }
 
 size_t sample_scratch_bytes(int64_t n) {
-  const int64_t nch = (n + CH - 1) / CH;
-  return (size_t)nch * 2 * sizeof(double) + 256;
+  const int64_t nch = (n + CH - 1) / CH, nt = (nch + CH - 1) / CH;
+  return (size_t)(2 * nch + 2 * nt + 1) * sizeof(double) + 256;
 }
 
 void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t m, int64_t* out, void* scratch,
                    cudaStream_t s) {
-  const int64_t nch = (n + CH - 1) / CH;
+  const int64_t nch = (n + CH - 1) / CH, nt = (nch + CH - 1) / CH;
   double* L1 = static_cast<double*>(scratch);
   double* P1 = L1 + nch;
-  double* total = P1 + nch;
+  double* T2 = P1 + nch;
+  double* P2 = T2 + nt;
+  double* total = P2 + nt;
   const unsigned gc = grid_for(nch * 32, 256, 152 * 16);
   if (dtype == CUTQC_F64)
     k_sample_chunks<double><<<gc, 256, 0, s>>>(static_cast<const double*>(p), n, L1, nch);
@@ -326,9 +411,16 @@ void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t
     k_sample_chunks<float><<<gc, 256, 0, s>>>(static_cast<const float*>(p), n, L1, nch);
   count_launch();
   check_launch("k_sample_chunks");
-  k_sample_scan<<<1, 1024, 0, s>>>(L1, nch, P1, total);
+  const unsigned gt = grid_for(nt * 32, 256, 152 * 16);
+  k_sample_tiles<<<gt, 256, 0, s>>>(L1, nch, T2, nt);
+  count_launch();
+  check_launch("k_sample_tiles");
+  k_sample_scan<<<1, 1024, 0, s>>>(T2, nt, P2, total);
   count_launch();
   check_launch("k_sample_scan");
+  k_sample_tile_scan<<<gt, 256, 0, s>>>(L1, nch, P2, nt, P1);
+  count_launch();
+  check_launch("k_sample_tile_scan");
   if (m == 0) return;
   const unsigned gd = grid_for(m * 32, 256, 152 * 16);
   if (dtype == CUTQC_F64)
