@@ -420,3 +420,55 @@ def test_sampling_frequencies_follow_the_distribution():
     counts = np.bincount(xs, minlength=16)
     stat = float(np.sum((counts - n * p) ** 2 / (n * p)))
     assert stat < 37.7
+
+
+# ---- exact cut search (Sec. 4.1, Eqs. 4-15) --------------------------------
+
+def _chain(n):
+    from paper_2012_02333_gb300.circuits import Circuit
+    c = Circuit(n)
+    for q in range(n):
+        c.add("h", q)
+    for q in range(n - 1):
+        c.add("cx", q, q + 1)
+    return c
+
+
+def test_cut_search_worked_chain():
+    """A CNOT chain on 4 qubits: v0 = CX(0,1), v1 = CX(1,2), v2 = CX(2,3);
+    edges v0->v1 (qubit 1) and v1->v2 (qubit 2); w = (2, 1, 1).  With D = 3 the
+    uncut circuit (d = 4) is infeasible; cutting either edge gives K = 1 and
+    subcircuits of f = (2, 2) or (1, 3): L = 4 * 2^4 = 64 both ways, and the
+    first in vertex order is {v0, v1 | v2}."""
+    from oracle import cutsearch as cs
+    c = _chain(4)
+    verts, edges, w = cs.graph(4, c.gates)
+    assert edges == [(0, 1), (1, 2)] and w == [2, 1, 1]
+    r = cs.search(4, c.gates, 3, 2)
+    assert r["L"] == 64 and r["K"] == 1 and r["assign"] == [0, 0, 1]
+    assert r["f"] == [2, 2] and r["d"] == [3, 2]
+    # the other cut of the same cost
+    other = cs.cost([0, 1, 1], edges, w, 2)
+    assert other["L"] == 64 and other["f"] == [1, 3] and other["d"] == [2, 3]
+    # with room for the whole circuit nothing is cut: f = (4, 0), L = 2^4
+    r = cs.search(4, c.gates, 4, 2)
+    assert r["K"] == 0 and r["L"] == 16
+    # too small a device: no assignment satisfies Eq. 9
+    assert cs.search(4, c.gates, 1, 2) is None
+
+
+def test_cut_search_invariants():
+    """For every assignment: sum_c f_c = n (each qubit's final segment is
+    measured in exactly one subcircuit), sum_c rho_c = sum_c O_c = K, and
+    sum_c alpha_c = n; L of the three-subcircuit sum written out by hand."""
+    import itertools
+    from oracle import cutsearch as cs
+    from paper_2012_02333_gb300 import circuits as C
+    circ = C.hwea(5, 3)
+    verts, edges, w = cs.graph(5, circ.gates)
+    for assign in itertools.product(*[range(min(k + 1, 3)) for k in range(len(verts))]):
+        r = cs.cost(assign, edges, w, 3)
+        assert sum(r["f"]) == 5 and sum(r["alpha"]) == 5
+        assert sum(r["rho"]) == sum(r["O"]) == r["K"]
+        f1, f2, f3 = r["f"]
+        assert r["L"] == 4 ** r["K"] * (2 ** (f1 + f2) + 2 ** (f1 + f2 + f3))
