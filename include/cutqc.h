@@ -198,6 +198,26 @@ typedef struct {
   double param;      /* angle for RX/RY/RZ/CP                                 */
 } cutqc_gate;
 
+/* Exact cut search (Sec. 4.1, Eqs. 4-15), on the host.  The circuit's
+ * multi-qubit gates (CZ, CX, CP, in order) are the vertices, the qubit wires
+ * between consecutive multi-qubit gates the edges; single-qubit gates are
+ * ignored.  Among the assignments of vertices to max_subcircuits (= n_C)
+ * subcircuits with vertex k in a subcircuit <= k (Eq. 12) and every
+ * subcircuit's width alpha + rho <= max_width (= D, Eq. 9), finds one of least
+ * reconstruction cost L = 4^K sum_{c=2}^{n_C} prod_{i<=c} 2^{f_i} (Eq. 14; K
+ * cut wires, f_i the outputs of subcircuit i, Eq. 7) by branch and bound; ties
+ * go to the first assignment in vertex order.  Qubits no multi-qubit gate
+ * touches belong to no vertex.  cluster: host int32 with room for one entry
+ * per gate; receives the subcircuit of each multi-qubit gate, in gate order;
+ * *n_vertices the number of them, *n_cuts K, *cost L (exact below 2^53).  The
+ * search visits at most max_nodes nodes; beyond that, or when no assignment
+ * fits the width, it returns CUTQC_ERR_UNSUPPORTED.  The paper solves the
+ * same model with a MIP solver; this exhaustive form is for small circuits.
+ * No GPU work. */
+CUTQC_API int cutqc_cut_search(const cutqc_gate* gates, int32_t n_gates, int32_t n_qubits, int32_t max_width,
+                               int32_t max_subcircuits, int64_t max_nodes, int32_t* cluster,
+                               int32_t* n_vertices, int32_t* n_cuts, double* cost);
+
 /* Attribution of measured variant distributions (Sec. 3.2.2, Eq. 2 and
  * Eq. 3): the tensor T[4^k_in][4^k_out][2^n_eff] of one subcircuit from the
  * output distributions of its 4^k_in x 3^k_out physical variants (Fig. 3),

@@ -383,7 +383,7 @@ def cut_circuit(circ: Circuit, home: Sequence[int], max_cuts: Optional[int] = No
 def build_cut(circ: Circuit, gate_block: Dict[int, int], home: Sequence[int]) -> CutCircuit:
     """Turn a gate -> block assignment into subcircuits, slots and cut ids."""
     wires = _wire_blocks(circ, gate_block, home)
-    n_blocks = max(home) + 1
+    n_blocks = max(max(home), max(gate_block.values(), default=0)) + 1
     # segments per qubit: list of (block, first pos, last pos)
     cut_wires: List[Tuple[int, int]] = []
     seg_of_gate: Dict[Tuple[int, int], Tuple[int, int]] = {}  # (gate, qubit) -> (qubit, seg idx)
@@ -477,6 +477,46 @@ def grid_blocks(rows: int, cols: int, depth: int, seed: int, brows: int, bcols: 
     home = [min(r // rh, brows - 1) * bcols + min(cc // ch, bcols - 1)
             for r in range(rows) for cc in range(cols)]
     return cut_circuit(c, home, max_cuts=max_cuts, max_width=max_width)
+
+
+def cut_from_clusters(circ: Circuit, gate_cluster: Dict[int, int], max_width: Optional[int] = None) -> CutCircuit:
+    """Subcircuits from an assignment of every multi-qubit gate (by gate index)
+    to a subcircuit, as the cut searcher returns it (Sec. 4.1: the cuts are the
+    wires whose consecutive multi-qubit gates lie in different subcircuits).
+    Subcircuits are renumbered in order of first use.  A qubit that no
+    multi-qubit gate touches is outside the search's graph (Sec. 4.1 takes the
+    circuit to be connected); such qubits join the narrowest subcircuit that
+    stays within max_width, else new subcircuits without cuts."""
+    order: Dict[int, int] = {}
+    for gi in sorted(gate_cluster):
+        order.setdefault(gate_cluster[gi], len(order))
+    gb = {gi: order[c] for gi, c in gate_cluster.items()}
+    home = [-1] * circ.n
+    for gi, g in enumerate(circ.gates):
+        if len(g.qubits) > 1:
+            for q in g.qubits:
+                if home[q] < 0:
+                    home[q] = gb[gi]
+    n_blocks = max(len(order), 1)
+    # widths of the connected part: wire segments per block
+    width = [0] * n_blocks
+    for w in _wire_blocks(circ, gb, [max(h, 0) for h in home]):
+        prev = None
+        for _, b in w:
+            if b != prev:
+                width[b] += 1
+                prev = b
+    for q in range(circ.n):
+        if home[q] >= 0:
+            continue
+        b = min(range(n_blocks), key=lambda i: (width[i], i))
+        if max_width is not None and width[b] >= max_width:
+            b = n_blocks
+            n_blocks += 1
+            width.append(0)
+        home[q] = b
+        width[b] += 1
+    return build_cut(circ, gb, home)
 
 
 def chain_blocks(circ: Circuit, n_sub: int, max_cuts: Optional[int] = None,

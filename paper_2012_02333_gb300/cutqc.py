@@ -78,6 +78,9 @@ _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
 _lib.cutqc_device_status.argtypes = [C.c_void_p]
+_lib.cutqc_cut_search.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int64,
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_double)]
 _lib.cutqc_distance.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
 _lib.cutqc_sample.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.cutqc_attribute.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
@@ -88,7 +91,7 @@ _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
-           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute", "cutqc_distance", "cutqc_sample"):
+           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute", "cutqc_distance", "cutqc_sample", "cutqc_cut_search"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -175,6 +178,25 @@ def cutqc_sample(p: torch.Tensor, u: torch.Tensor, stream=None) -> torch.Tensor:
     _check(_lib.cutqc_sample(C.c_void_p(p.data_ptr()), p.numel(), dt, C.c_void_p(u.data_ptr()), u.numel(),
                              C.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def cut_search(circ: circuits.Circuit, max_width: int, max_subcircuits: int, max_nodes: int = 10 ** 8) -> dict:
+    """Binding of cutqc_cut_search: the least-cost cut (Eqs. 4-15) of `circ`
+    for devices of max_width qubits and at most max_subcircuits subcircuits.
+    Returns {"gate_cluster": {gate index: subcircuit}, "assign": [...] per
+    multi-qubit gate in order, "K": cuts, "cost": Eq. 14}."""
+    gates = (cutqc_gate * max(len(circ.gates), 1))()
+    for i, g in enumerate(circ.gates):
+        q1 = g.qubits[1] if len(g.qubits) > 1 else -1
+        gates[i] = cutqc_gate(GATE_OPS[g.name], g.qubits[0], q1, g.params[0] if g.params else 0.0)
+    cl = (C.c_int32 * max(len(circ.gates), 1))()
+    nv, k = C.c_int32(), C.c_int32()
+    cost = C.c_double()
+    _check(_lib.cutqc_cut_search(gates, len(circ.gates), circ.n, max_width, max_subcircuits, max_nodes, cl,
+                                 C.byref(nv), C.byref(k), C.byref(cost)))
+    assign = [int(cl[v]) for v in range(nv.value)]
+    verts = [gi for gi, g in enumerate(circ.gates) if len(g.qubits) > 1]
+    return {"gate_cluster": dict(zip(verts, assign)), "assign": assign, "K": int(k.value), "cost": cost.value}
 
 
 def device_status(stream=None) -> None:

@@ -217,3 +217,26 @@ def test_unregistered_host_output_is_rejected(env):
                                           cutqc._stream_ptr(None))
     assert st == cutqc.CUTQC_ERR_ARG
     assert "pinned" in cutqc._lib.cutqc_last_error().decode()
+
+
+@pytest.mark.parametrize("make,D,nC", [(lambda C: C.hwea(10, 4), 6, 2), (lambda C: C.bv(8, 3), 5, 2),
+                                       (lambda C: C.hwea(9, 5), 4, 3)])
+def test_reconstruction_of_searched_cuts(env, make, D, nC):
+    """End to end from the cut searcher (Sec. 4.1): the least-cost cut of the
+    circuit, its subcircuits' tensors (oracle simulation), the GPU
+    reconstruction in FP64 (CUDA core) and FP32 (automatic form), against the
+    statevector of the uncut circuit (exactness, Sec. 3.2.3)."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    from oracle import statevector as sv
+    from paper_2012_02333_gb300 import circuits as C
+    circ = make(C)
+    r = cutqc.cut_search(circ, D, nC)
+    cc = C.cut_from_clusters(circ, r["gate_cluster"], max_width=D)
+    assert cc.n_cuts == r["K"] and max(s.d for s in cc.subs) <= D
+    T = at.tensors(cc)
+    truth = sv.probabilities(cc.circuit)
+    out64, _ = cutqc.reconstruct_fd(cc, to_dev(torch, T, torch.float64), algo="cc")
+    assert np.abs(out64.cpu().numpy() - truth).max() <= 1e-12
+    out32, _ = cutqc.reconstruct_fd(cc, to_dev(torch, [t.astype(np.float32) for t in T], torch.float32))
+    assert np.abs(out32.double().cpu().numpy() - truth).max() <= TOL32
