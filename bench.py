@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
-                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "metrics_qaoa30"],
+                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "metrics_qaoa30",
+                             "sim_supremacy4x6"],
                     help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
@@ -449,6 +450,38 @@ def run_other(args):
                  "cc_only": "forward on the FP32 CUDA-core form"}
         units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
         cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
+    elif w == "sim_supremacy4x6":
+        # the GPU subcircuit simulator (input preparation, here timed): every
+        # variant of both subcircuits of the 4x6 supremacy workload simulated
+        # in complex FP64, attributed (Eq. 3, Eq. 2) into the FP32 tensors
+        cc = circuits.supremacy_4x6(0)
+        outs = [torch.empty((4 ** s.k_in) * (4 ** s.k_out) * (2 ** s.n_eff), device=dev) for s in cc.subs]
+        n_gate_passes = 0
+        state_bytes = 0
+        pass_bytes = 0
+        for sub in cc.subs:
+            nvar = (4 ** sub.k_in) * (3 ** sub.k_out)
+            st = nvar * (2 ** sub.d) * 16
+            state_bytes += st
+            n_gate_passes += len(sub.gates)
+            pass_bytes += 2 * st * len(sub.gates)
+
+        def sim_step():
+            for sub, o in zip(cc.subs, outs):
+                cutqc.cutqc_simulate_subcircuit(sub, torch.float32, dev, out=o)
+        ms = timed(sim_step)
+        units, unit, dtype = sum(o.numel() for o in outs), "tensor entries/s", "complex f64 state, f32 tensors"
+        pk, pk_src = peaks()
+        extra = {"gates": n_gate_passes, "state_bytes_all_variants": state_bytes,
+                 "roofline": {"bound": "hbm", "achieved": pass_bytes / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": pass_bytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                              "traffic": None, "algorithmic_bytes": pass_bytes, "peak_file": pk_src,
+                              "note": "the states (57 and 25 MB) stay in L2 between gate passes"},
+                 "gate_pass_bytes": "each gate reads and writes the state of every variant (16 B per amplitude)"}
+        cfg = {"workload": "sim_supremacy4x6_fp64_state", "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff]
+                                                                          for s in cc.subs],
+               "step": "simulate every variant of both subcircuits and attribute (input preparation; each call "
+                       "allocates and frees its state buffers)"}
     elif w == "metrics_qaoa30":
         # Eq. 16 chi^2 and total variation between the split-precision and the
         # FP32 CUDA-core reconstructions of QAOA-30 (2^30 entries each), and

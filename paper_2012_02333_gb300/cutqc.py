@@ -365,7 +365,8 @@ def cutqc_reconstruct_dd(problem: Problem, roles: Sequence[int], bins: torch.Ten
     return [int(ti[j]) for j in range(topk)], [float(tv[j]) for j in range(topk)]
 
 
-def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, device=None, stream=None) -> torch.Tensor:
+def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, device=None, stream=None,
+                              out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Binding of cutqc_simulate_subcircuit: the attributed tensor of one
     subcircuit, simulated on the GPU (input preparation)."""
     dev = device or torch.device("cuda", torch.cuda.current_device())
@@ -373,7 +374,11 @@ def cutqc_simulate_subcircuit(sub: circuits.Subcircuit, dtype=torch.float32, dev
     for i, g in enumerate(sub.gates):
         q1 = g.qubits[1] if len(g.qubits) > 1 else -1
         gates[i] = cutqc_gate(GATE_OPS[g.name], g.qubits[0], q1, g.params[0] if g.params else 0.0)
-    out = torch.empty((4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff), dtype=dtype, device=dev)
+    n_out = (4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** sub.n_eff)
+    if out is None:
+        out = torch.empty(n_out, dtype=dtype, device=dev)
+    elif out.numel() != n_out or out.dtype != dtype or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor of 4^k_in*4^k_out*2^n_eff entries in dtype")
     s = stream or torch.cuda.current_stream(dev)
     _check(_lib.cutqc_simulate_subcircuit(
         gates, len(sub.gates), sub.d, _i32([q for q, _ in sub.in_slots]), sub.k_in,
