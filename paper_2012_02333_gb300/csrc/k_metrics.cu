@@ -288,7 +288,17 @@ __global__ void k_sample_tile_scan(const double* __restrict__ L1, int64_t nch, c
   }
 }
 
-// one warp per draw
+// FF compare: a.s + a.c > r.s + r.c, evaluated as (a.s - r.s) + (a.c - r.c) > 0
+// (the leading difference is exact when the two are close)
+__device__ __forceinline__ bool ff_greater(FF a, FF r) { return (a.s - r.s) + (a.c - r.c) > 0.0f; }
+__device__ __forceinline__ FF ff_of(double x) {
+  const float hi = (float)x;
+  return FF{hi, (float)(x - (double)hi)};
+}
+
+// Warps take the draws 32 at a time: each lane first binary-searches the chunk
+// of its own draw (32 searches in flight per warp), then the warp resolves
+// the 32 draws one after the other inside their chunks.
 template <typename T>
 __global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* __restrict__ P1,
                               const double* __restrict__ L1, int64_t nch, const double* __restrict__ total,
@@ -297,71 +307,85 @@ __global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* 
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const double tot = *total;
-  for (int64_t k = warp; k < m; k += nw) {
-    if (!(tot > 0.0)) {   // no outcome carries weight
-      if (lane == 0) out[k] = -1;
-      continue;
-    }
-    const double t = u[k] * tot;
-    // chunk: the largest c with P1[c] <= t that carries weight
-    int64_t lo = 0, hi = nch - 1;
-    while (lo < hi) {
-      const int64_t mid = (lo + hi + 1) >> 1;
-      if (P1[mid] <= t) lo = mid;
-      else hi = mid - 1;
-    }
-    int64_t c = lo;
-    while (c > 0 && L1[c] <= 0.0) --c;   // rounding put t past the weighted chunks
-    const double r = t - P1[c];
-    // lane sums of the chunk's 32 runs of 32 weights
-    const int64_t base = c * CH + 32 * lane;
-    FF ls{};
-    double ld = 0.0;
-    for (int i = 0; i < 32; ++i) {
-      const int64_t idx = base + i;
-      if (idx < n) {
-        if constexpr (sizeof(T) == 8)
-          ld += fmax(p[idx], 0.0);
-        else
-          ls = ff_add(ls, weight32(p[idx]));
+  for (int64_t k0 = warp * 32; k0 < m; k0 += nw * 32) {
+    // this lane's draw: the largest chunk c with P1[c] <= t that carries weight
+    const int64_t kl = k0 + lane;
+    int64_t my_c = 0;
+    double my_r = 0.0;
+    if (kl < m && tot > 0.0) {
+      const double t = u[kl] * tot;
+      int64_t lo = 0, hi = nch - 1;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (P1[mid] <= t) lo = mid;
+        else hi = mid - 1;
       }
+      while (lo > 0 && L1[lo] <= 0.0) --lo;   // rounding put t past the weighted chunks
+      my_c = lo;
+      my_r = t - P1[lo];
     }
-    const double lsum = sizeof(T) == 8 ? ld : ff_value(ls);
-    double incl = lsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const double y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const double excl = incl - lsum;
-    const unsigned over = __ballot_sync(0xffffffffu, incl > r && lsum > 0.0);
-    const unsigned weighted = __ballot_sync(0xffffffffu, lsum > 0.0);
-    const int L = over ? __ffs(over) - 1 : (weighted ? 31 - __clz(weighted) : 0);
-    if (lane == L) {
-      const double r2 = r - excl;
-      int64_t pick = -1, last_w = -1;
-      FF cs{};
-      double cd = 0.0;
-      for (int i = 0; i < 32 && pick < 0; ++i) {
+    const int nd = (int)(m - k0 < 32 ? m - k0 : 32);
+    for (int j = 0; j < nd; ++j) {
+      const int64_t k = k0 + j;
+      if (!(tot > 0.0)) {   // no outcome carries weight
+        if (lane == 0) out[k] = -1;
+        continue;
+      }
+      const int64_t c = __shfl_sync(0xffffffffu, my_c, j);
+      const double r = __shfl_sync(0xffffffffu, my_r, j);
+      // lane sums of the chunk's 32 runs of 32 weights
+      const int64_t base = c * CH + 32 * lane;
+      FF ls{};
+      double ld = 0.0;
+      for (int i = 0; i < 32; ++i) {
         const int64_t idx = base + i;
-        if (idx >= n) break;
-        double cum;
-        if constexpr (sizeof(T) == 8) {
-          const double w = fmax(p[idx], 0.0);
-          if (w > 0.0) last_w = idx;
-          cd += w;
-          cum = cd;
-          if (w > 0.0 && cum > r2) pick = idx;
-        } else {
-          const float w = weight32(p[idx]);
-          if (w > 0.0f) last_w = idx;
-          cs = ff_add(cs, w);
-          cum = ff_value(cs);
-          if (w > 0.0f && cum > r2) pick = idx;
+        if (idx < n) {
+          if constexpr (sizeof(T) == 8)
+            ld += fmax(p[idx], 0.0);
+          else
+            ls = ff_add(ls, weight32(p[idx]));
         }
       }
-      if (pick < 0) pick = last_w >= 0 ? last_w : base;
-      out[k] = pick;
+      const double lsum = sizeof(T) == 8 ? ld : ff_value(ls);
+      double incl = lsum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const double excl = incl - lsum;
+      const unsigned over = __ballot_sync(0xffffffffu, incl > r && lsum > 0.0);
+      const unsigned weighted = __ballot_sync(0xffffffffu, lsum > 0.0);
+      const int L = over ? __ffs(over) - 1 : (weighted ? 31 - __clz(weighted) : 0);
+      if (lane == L) {
+        const double r2 = r - excl;
+        int64_t pick = -1, last_w = -1;
+        if constexpr (sizeof(T) == 8) {
+          double cd = 0.0;
+          for (int i = 0; i < 32 && pick < 0; ++i) {
+            const int64_t idx = base + i;
+            if (idx >= n) break;
+            const double w = fmax(p[idx], 0.0);
+            if (w > 0.0) last_w = idx;
+            cd += w;
+            if (w > 0.0 && cd > r2) pick = idx;
+          }
+        } else {
+          // running sum and remainder both as compensated FP32 pairs: no FP64 per weight
+          const FF rr = ff_of(r2);
+          FF cs{};
+          for (int i = 0; i < 32 && pick < 0; ++i) {
+            const int64_t idx = base + i;
+            if (idx >= n) break;
+            const float w = weight32(p[idx]);
+            if (w > 0.0f) last_w = idx;
+            cs = ff_add(cs, w);
+            if (w > 0.0f && ff_greater(cs, rr)) pick = idx;
+          }
+        }
+        if (pick < 0) pick = last_w >= 0 ? last_w : base;
+        out[k] = pick;
+      }
     }
   }
 }
@@ -422,7 +446,7 @@ void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t
   count_launch();
   check_launch("k_sample_tile_scan");
   if (m == 0) return;
-  const unsigned gd = grid_for(m * 32, 256, 152 * 16);
+  const unsigned gd = grid_for((m + 31) / 32 * 32, 256, 152 * 16);
   if (dtype == CUTQC_F64)
     k_sample_draw<double><<<gd, 256, 0, s>>>(static_cast<const double*>(p), n, P1, L1, nch, total, u, m, out);
   else
