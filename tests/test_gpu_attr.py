@@ -116,3 +116,20 @@ def test_attribute_into_unaligned_output(env):
     want = at.attribute(sub, p.astype(np.float32).astype(np.float64)).reshape(-1)
     assert np.abs(out.double().cpu().numpy() - want).max() <= 1e-6
     assert buf[0].item() == 0.0
+
+
+def test_attribute_benchmark_size(env):
+    """The benchmark's attribution workload itself: both QAOA-30 subcircuits
+    (17 qubits, 2 init + 2 measurement slots) from seeded synthetic variant
+    distributions, every entry against the oracle."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    from paper_2012_02333_gb300 import circuits as C
+    cc = C.qaoa_2cluster(15, 0)
+    rng = np.random.default_rng(21)
+    for sub in cc.subs:
+        p = rng.random(((4 ** sub.k_in) * (3 ** sub.k_out), 2 ** sub.d)).astype(np.float32)
+        p /= p.sum(axis=1, keepdims=True)
+        got = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), device="cuda"))
+        want = at.attribute(sub, p.astype(np.float64).reshape(4 ** sub.k_in, 3 ** sub.k_out, 2 ** sub.d))
+        assert np.abs(got.double().cpu().numpy() - want.reshape(-1)).max() <= 1e-6

@@ -70,11 +70,26 @@ def test_distance_of_reconstruction_to_ground_truth(env):
     assert chi.item() < 1e-6 and tv.item() < 1e-4
 
 
+def blocked_cumulative(p64, block=1024):
+    """The oracle's C_x = sum_{i <= x} max(p_i, 0) with less rounding for large
+    inputs: pairwise block sums, their running sum, and running sums inside
+    each block (a sequential sum over 2^28 values drifts by more than the
+    tolerance of these checks)."""
+    w = np.maximum(p64, 0.0)
+    n = len(w)
+    pad = (-n) % block
+    wb = np.concatenate([w, np.zeros(pad)]).reshape(-1, block)
+    starts = np.concatenate([[0.0], np.cumsum(wb.sum(axis=1))[:-1]])
+    return (starts[:, None] + np.cumsum(wb, axis=1)).reshape(-1)[:n]
+
+
 def check_draws(p64, u, got, tol_rel=1e-11):
     from oracle import metrics as mt
-    C = mt.cumulative(p64)
+    C = mt.cumulative(p64) if len(p64) <= (1 << 21) else blocked_cumulative(p64)
     total = C[-1]
-    want = mt.sample(p64, u)
+    t_all = u * total
+    want = np.minimum(np.searchsorted(C, t_all, side="right"), len(C) - 1) if len(p64) > (1 << 21) \
+        else mt.sample(p64, u)
     t = u * total
     tol = tol_rel * total
     w = np.maximum(p64, 0.0)
@@ -141,3 +156,51 @@ def test_sampling_a_reconstruction(env):
     u = rng.random(100000)
     got = cutqc.cutqc_sample(out, torch.tensor(u, device="cuda")).cpu().numpy()
     check_draws(out.double().cpu().numpy(), u, got)
+
+
+def test_distance_benchmark_size_properties(env):
+    """2^30 entries (the benchmark's size): properties that hold at any size
+    -- chi^2(a, a) = 0, symmetry, chi^2 <= 2 and TV <= 1 for distributions,
+    and the sum over a split of the index range equals the whole (the first
+    2^20 entries checked against the oracle as well)."""
+    torch, cutqc = env
+    from oracle import metrics as mt
+    n = 1 << 30
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    a = torch.rand(n, generator=g, device="cuda")
+    a /= a.sum()
+    b = torch.rand(n, generator=g, device="cuda")
+    b /= b.sum()
+    c0, t0 = cutqc.cutqc_distance(a, a)
+    assert c0.item() == 0.0 and t0.item() == 0.0
+    cab, tab = cutqc.cutqc_distance(a, b)
+    cba, tba = cutqc.cutqc_distance(b, a)
+    assert cab.item() == pytest.approx(cba.item(), rel=1e-6)
+    assert tab.item() == pytest.approx(tba.item(), rel=1e-6)
+    assert 0.0 < cab.item() <= 2.0 and 0.0 < tab.item() <= 1.0
+    h = n // 2
+    c1, t1 = cutqc.cutqc_distance(a[:h], b[:h])
+    c2, t2 = cutqc.cutqc_distance(a[h:], b[h:])
+    assert c1.item() + c2.item() == pytest.approx(cab.item(), rel=1e-6)
+    assert t1.item() + t2.item() == pytest.approx(tab.item(), rel=1e-6)
+    k = 1 << 20
+    ck, tk = cutqc.cutqc_distance(a[:k], b[:k])
+    aa, bb = a[:k].double().cpu().numpy(), b[:k].double().cpu().numpy()
+    assert ck.item() == pytest.approx(mt.chi_square(aa, bb), rel=1e-6)
+    assert tk.item() == pytest.approx(mt.total_variation(aa, bb), rel=1e-6)
+
+
+def test_sampling_2e28_entries(env):
+    """Draws from a 2^28-entry distribution with zero and negative runs, every
+    draw valid against the exact FP64 cumulative sums."""
+    torch, cutqc = env
+    n = 1 << 28
+    g = torch.Generator(device="cuda")
+    g.manual_seed(4)
+    p = torch.rand(n, generator=g, device="cuda") ** 8
+    p[: 1 << 20] = 0.0
+    p[1 << 25: (1 << 25) + 4096] = -1e-9
+    u = np.random.default_rng(5).random(50000)
+    got = cutqc.cutqc_sample(p, torch.tensor(u, device="cuda")).cpu().numpy()
+    check_draws(p.double().cpu().numpy(), u, got)
