@@ -693,7 +693,11 @@ static bool is_host_memory(const void* p) {
 
 static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
-                      cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr) {
+                      cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr,
+                      size_t topk_back_off = SIZE_MAX, int* topk_nlists = nullptr) {
+  // topk_back_off: where in the back region a tensor-core final contraction
+  // may leave its fused top-32 lists (*topk_nlists of them; 0 when it did not)
+  if (topk_nlists) *topk_nlists = 0;
   size_t tc_ws = 0;
   std::vector<Contraction> cs(P.steps.size());
   char* base = nullptr;
@@ -828,6 +832,12 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       g_last_stream = s;
     }
     c.status = status_word(ds);
+    if (final_step && use_tc_final && topk_nlists && topk_back_off != SIZE_MAX) {
+      char* tk = base + need + topk_back_off;
+      c.topk_v = reinterpret_cast<float*>(tk);
+      c.topk_i = reinterpret_cast<int64_t*>(tk + (size_t)152 * 8 * 4 * 32 * 4);
+      c.topk_nlists = topk_nlists;
+    }
     c.out = final_step ? out : static_cast<void*>(base + P.ws_node[st.result]);
     c.out_host = final_step && is_host_memory(out);
     c.sum = final_step ? sum : nullptr;
@@ -1105,6 +1115,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
     }
     char* ddtab = static_cast<char*>(P.ddtab);
     char* front_ptr = nullptr;
+    int fused_lists = 0;
     char* back_ptr = run_plan(
         ds, P, P.dd_front, back,
         [&](char* front) {
@@ -1121,11 +1132,14 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
           }
           return t;
         },
-        bins, nullptr, algo, s);
+        bins, nullptr, algo, s, nullptr, nullptr, topk > 0 ? off_tk : SIZE_MAX, &fused_lists);
     if (topk > 0) {
       float* cv = reinterpret_cast<float*>(back_ptr + off_cv);
       int64_t* ci = reinterpret_cast<int64_t*>(back_ptr + off_ci);
-      launch_topk(bins, P.dtype, nbins, back_ptr + off_tk, cv, ci, s);
+      if (fused_lists > 0)   // the tensor-core contraction kept the candidates while writing the bins
+        launch_topk_lists(back_ptr + off_tk, fused_lists, cv, ci, s);
+      else
+        launch_topk(bins, P.dtype, nbins, back_ptr + off_tk, cv, ci, s);
       DdEvalArgs ea{};
       ea.n_sub = p->n_sub;
       ea.n_cuts = p->n_cuts;

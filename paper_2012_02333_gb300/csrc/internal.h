@@ -108,6 +108,11 @@ struct Contraction {
   double split_tol = 2.5e-7;
   int* status = nullptr;           // device status word (DeviceStatus) of this device
   bool out_host = false;           // `out` is pinned host memory (written over the host link)
+  // tensor-core path only: keep a top-32 of the written values per epilogue
+  // warp (lists of 32 at topk_v / topk_i) and report the number of lists
+  float* topk_v = nullptr;
+  int64_t* topk_i = nullptr;
+  int* topk_nlists = nullptr;
 };
 
 // k_cc.cu
@@ -212,6 +217,8 @@ void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int m
                      void* part, cudaStream_t s);
 size_t topk_workspace_bytes(int64_t n);
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
+// merge nlists lists of 32 (value, index) candidates, laid out like launch_topk's workspace
+void launch_topk_lists(void* ws, int64_t nlists, float* out_v, int64_t* out_i, cudaStream_t s);
 // chunks of the Kronecker terms per candidate in the FP64 re-evaluation (<= 64)
 int dd_eval_chunks(int n_cuts);
 void launch_dd_rerank(const DdEvalArgs& a, int dtype, double* m64, double* part, double* val, cudaStream_t s);

@@ -590,6 +590,16 @@ void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v,
   check_launch("k_topk_final");
 }
 
+void launch_topk_lists(void* ws, int64_t nlists, float* out_v, int64_t* out_i, cudaStream_t s) {
+  const int64_t lists_max = 152 * 8 * 4;
+  if (nlists > lists_max) fail(CUTQC_ERR_UNSUPPORTED, "too many candidate lists");
+  float* cv = static_cast<float*>(ws);
+  int64_t* ci = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + (size_t)lists_max * KC * 4);
+  k_topk_final<<<1, 1024, 0, s>>>(cv, ci, nlists * KC, out_v, out_i);
+  count_launch();
+  check_launch("k_topk_final");
+}
+
 int dd_eval_chunks(int n_cuts) {
   const int64_t nterms = int64_t(1) << (2 * n_cuts);
   int64_t c = nterms / 2048;

@@ -38,6 +38,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -453,6 +454,27 @@ __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, in
   return g;
 }
 
+// (value, index) order of the fused top-32: larger value first, then lower index
+__device__ __forceinline__ bool tk_before(float v1, int64_t i1, float v2, int64_t i2) {
+  return v1 > v2 || (v1 == v2 && i1 < i2);
+}
+// insert into the warp's sorted list (lane j holds the j-th best)
+__device__ __forceinline__ void tk_insert(float& lv, int64_t& li, float v, int64_t idx, int lane) {
+  const unsigned ahead = __ballot_sync(0xffffffffu, tk_before(lv, li, v, idx));
+  const int pos = __popc(ahead);
+  const float uv = __shfl_up_sync(0xffffffffu, lv, 1);
+  const int64_t ui = __shfl_up_sync(0xffffffffu, li, 1);
+  if (pos < 32) {
+    if (lane > pos) {
+      lv = uv;
+      li = ui;
+    } else if (lane == pos) {
+      lv = v;
+      li = idx;
+    }
+  }
+}
+
 struct TcArgs {
   int Kp;
   int M, N;                   // rows of one piece of A' / B' (the piece offset of the TMA row coordinate)
@@ -468,6 +490,8 @@ struct TcArgs {
   int vecB;
   int staged;                 // restage the epilogue through shared memory (large outputs)
   int* status;
+  float* topk_v;              // fused top-32 (dynamic-definition bins): one list of 32 per epilogue warp
+  int64_t* topk_i;
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -607,6 +631,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = 0; t < 4; ++t) dtiny[t] = deposit(a.depB, 1, (uint64_t)t);
     const bool vec = a.vecB >= 4;
     const bool staged = vec && a.staged;
+    // fused top-32 of the written values, ranked by (value, output index)
+    const bool tk = a.topk_v != nullptr;
+    float tk_v = -FLT_MAX;
+    int64_t tk_i = INT64_MAX;
     // Staged stores (outputs larger than L2, where the store stream is
     // DRAM-bound, and outputs in host memory; an output that stays in L2 goes
     // out directly from the registers, 16 bytes per row, which costs less
@@ -681,6 +709,33 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint64_t dc = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
+        if (tk) {
+          // the warp's current 32nd best; a chunk with no value at or above it
+          // (the usual case once the list has filled) costs one vote
+          float thr_v = __shfl_sync(0xffffffffu, tk_v, 31);
+          bool cand = false;
+#pragma unroll
+          for (int j = 0; j < 32; ++j) cand |= v[j] >= thr_v;
+          if (__any_sync(0xffffffffu, cand)) {
+            const uint64_t rowg = gbase + dep_lane + dc;
+            int64_t thr_i = __shfl_sync(0xffffffffu, tk_i, 31);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+              const int64_t idx = (int64_t)(rowg + dlow[j >> 2] + dtiny[j & 3]);
+              unsigned m = __ballot_sync(0xffffffffu, tk_before(v[j], idx, thr_v, thr_i));
+              if (m) {
+                while (m) {
+                  const int src = __ffs(m) - 1;
+                  m &= m - 1;
+                  tk_insert(tk_v, tk_i, __shfl_sync(0xffffffffu, v[j], src), __shfl_sync(0xffffffffu, idx, src),
+                            lane);
+                }
+                thr_v = __shfl_sync(0xffffffffu, tk_v, 31);
+                thr_i = __shfl_sync(0xffffffffu, tk_i, 31);
+              }
+            }
+          }
+        }
         if (staged) {
           float* cbase = a.out + gbase + dc;
 #pragma unroll
@@ -742,6 +797,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
       if (lane == 0) atomicAdd(a.sum, local);
+    }
+    if (tk) {
+      const int64_t list = (int64_t)blockIdx.x * EPI_WARPS + (warp - 2);
+      a.topk_v[list * 32 + lane] = tk_v;
+      a.topk_i[list * 32 + lane] = tk_i;
     }
   }
   __syncwarp();
@@ -939,6 +999,8 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   // restage through shared memory for outputs beyond L2 (128 MiB of FP32) and
   // for outputs in host memory, where whole-line stores matter most
   a.staged = (c.out_host || M * N >= (int64_t(1) << 25)) ? 1 : 0;
+  a.topk_v = c.topk_v;
+  a.topk_i = c.topk_i;
   a.status = status;
   static int sms = 0;
   static bool attr = false;
@@ -956,6 +1018,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   CUTQC_CUDA(launch_pdl(k_tc_gemm, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
   count_launch();
   check_launch("k_tc_gemm");
+  if (c.topk_nlists) *c.topk_nlists = c.topk_v ? grid * EPI_WARPS : 0;
   if (c.profile) prof_end(s, ev);
 }
 
