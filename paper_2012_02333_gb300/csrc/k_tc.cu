@@ -494,6 +494,9 @@ struct TcArgs {
   int64_t* topk_i;
 };
 
+// TK: also keep the fused top-32 (a separate instantiation, so the plain
+// contraction carries none of its code)
+template <bool TK>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
@@ -632,7 +635,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool vec = a.vecB >= 4;
     const bool staged = vec && a.staged;
     // fused top-32 of the written values, ranked by (value, output index)
-    const bool tk = a.topk_v != nullptr;
+    constexpr bool tk = TK;
     float tk_v = -FLT_MAX;
     int64_t tk_i = INT64_MAX;
     // Staged stores (outputs larger than L2, where the store stream is
@@ -709,7 +712,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint64_t dc = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
-        if (tk) {
+        if constexpr (TK) {
           // the warp's current 32nd best; a chunk with no value at or above it
           // (the usual case once the list has filled) costs one vote
           float thr_v = __shfl_sync(0xffffffffu, tk_v, 31);
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
       if (lane == 0) atomicAdd(a.sum, local);
     }
-    if (tk) {
+    if constexpr (TK) {
       const int64_t list = (int64_t)blockIdx.x * EPI_WARPS + (warp - 2);
       a.topk_v[list * 32 + lane] = tk_v;
       a.topk_i[list * 32 + lane] = tk_i;
@@ -1005,7 +1008,8 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   static int sms = 0;
   static bool attr = false;
   if (!attr) {
-    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     int dev = 0;
     CUTQC_CUDA(cudaGetDevice(&dev));
     CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1015,7 +1019,10 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   const int grid = tiles < sms ? tiles : sms;
   cudaEvent_t ev = nullptr;
   if (c.profile) prof_begin(s, &ev);
-  CUTQC_CUDA(launch_pdl(k_tc_gemm, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
+  if (a.topk_v)
+    CUTQC_CUDA(launch_pdl(k_tc_gemm<true>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
+  else
+    CUTQC_CUDA(launch_pdl(k_tc_gemm<false>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
   count_launch();
   check_launch("k_tc_gemm");
   if (c.topk_nlists) *c.topk_nlists = c.topk_v ? grid * EPI_WARPS : 0;
