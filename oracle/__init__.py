@@ -19,6 +19,8 @@ Modules
                 expectation value over the reconstructed distribution
   metrics       the chi^2 loss of Eq. 16, total variation, and inverse-transform
                 sampling of outcomes from a reconstructed distribution
+  cutsearch     exhaustive search of the cut model of Sec. 4.1 (Eqs. 4-15) on
+                tiny circuits: every assignment enumerated, cost by Eq. 14
 
 Every function is pinned by a ``-m "not gpu"`` test against something other
 than itself: textbook states, the paper's worked single-cut formulas,
