@@ -243,7 +243,7 @@ def run_ours(args):
     out = torch.empty(n_out, dtype=torch.float32, device=dev)
     sum_p = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
-    flush_sink = torch.empty(1, dtype=torch.float32, device=dev)
+    flush_sink = torch.empty((), dtype=torch.float32, device=dev)
 
     def flush_l2():
         # evict everything: write 256 MiB, then read it back so the dirty lines
