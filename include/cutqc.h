@@ -31,6 +31,14 @@
  *    cudaStream_t; NULL = the legacy default stream) unless it says
  *    otherwise.  Device pointers must be on the current device.  The caller
  *    keeps inputs alive and unmodified until the stream has passed the call.
+ *  - Alignment: device arrays given to the reconstruction calls (subcircuit
+ *    tensors, out, bins, grad_out, grad_tensor) must be 16-byte aligned, as
+ *    cudaMalloc and PyTorch allocations are (a tensor view at an element
+ *    offset may not be); cutqc_attribute, cutqc_simulate_subcircuit,
+ *    cutqc_distance and cutqc_sample take any element-aligned array; device
+ *    scalars (sum_p, loss_value, chi2, tv) and the u / out arrays of
+ *    cutqc_sample need their natural alignment.  Anything else is rejected
+ *    with CUTQC_ERR_ARG before anything is launched.
  *  - The library owns a per-device workspace and a plan cache (device tables
  *    derived from the problem's structure).  Both grow on demand with
  *    cudaMalloc and persist until cutqc_release().  Calls from several host

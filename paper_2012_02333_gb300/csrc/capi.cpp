@@ -15,6 +15,7 @@
 #include <atomic>
 #include <cmath>
 #include <functional>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -83,6 +84,14 @@ static constexpr int kMaxQubits = 4096;
 
 static size_t dtype_size(int dt) { return dt == CUTQC_F64 ? 8 : 4; }
 
+// Device arrays are read and written with 16-byte (and wider) vector
+// accesses, device scalars with their natural width: a pointer that breaks
+// this would fault on the GPU, so it is rejected here instead.
+static void need_aligned(const void* p, size_t bytes, const char* what) {
+  if (p && reinterpret_cast<uintptr_t>(p) % bytes != 0)
+    fail(CUTQC_ERR_ARG, std::string(what) + " must be " + std::to_string(bytes) + "-byte aligned");
+}
+
 static void validate(const cutqc_problem* p, bool need_tensors) {
   if (!p) fail(CUTQC_ERR_ARG, "problem is NULL");
   if (p->dtype != CUTQC_F32 && p->dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "dtype must be CUTQC_F32 or CUTQC_F64");
@@ -102,6 +111,7 @@ static void validate(const cutqc_problem* p, bool need_tensors) {
     if ((s.k_in && !s.in_cut) || (s.k_out && !s.out_cut) || (s.n_eff && !s.out_qubit))
       fail(CUTQC_ERR_ARG, "NULL slot or output array");
     if (need_tensors && !s.tensor) fail(CUTQC_ERR_ARG, "NULL tensor pointer");
+    if (need_tensors) need_aligned(s.tensor, 16, "a subcircuit tensor");
     for (int j = 0; j < s.k_in; ++j) {
       const int k = s.in_cut[j];
       if (k < 0 || k >= p->n_cuts) fail(CUTQC_ERR_SHAPE, "init slot names a cut id out of range");
@@ -361,7 +371,7 @@ static Step make_step(Plan& P, int ia, int ib, int result, const std::vector<int
     for (int i = 0; i < fB; ++i) vb[i] = uint64_t(1) << (P.n_out - 1 - B.bits[fB - 1 - i]);
     st.out_stride = 0;
     int run = 0;
-    while (run < fB && run < 2 && vb[run] == (uint64_t(1) << run)) ++run;
+    while (run < fB && run < 3 && vb[run] == (uint64_t(1) << run)) ++run;
     st.vecB = 1 << run;
   }
   st.depA = deposit_table(va);
@@ -990,7 +1000,9 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
       validate(&problems[i], true);
       if (problems[i].n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
       if (!out[i]) fail(CUTQC_ERR_ARG, "out[i] is NULL");
+      need_aligned(out[i], 16, "out[i]");
     }
+    need_aligned(sum_p, 8, "sum_p");
     std::vector<void*> dout(n_problems);
     for (int i = 0; i < n_problems; ++i) dout[i] = resolve_out(out[i]);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -1019,6 +1031,9 @@ int cutqc_attribute(const void* variant_probs, int32_t d, int32_t k_in, const in
     if (k_in < 0 || k_out < 0 || n_eff < 0 || k_in + k_out > kMaxCuts) fail(CUTQC_ERR_SHAPE, "bad slot counts");
     if (k_out + n_eff != d) fail(CUTQC_ERR_SHAPE, "every local qubit must be an output or a measured cut qubit");
     if (!variant_probs || !tensor || (k_out && !meas_qubit) || (n_eff && !out_local)) fail(CUTQC_ERR_ARG, "NULL array");
+    // the attribution kernels pick 16-byte or scalar accesses themselves
+    need_aligned(variant_probs, dtype == CUTQC_F64 ? 8 : 4, "variant_probs");
+    need_aligned(tensor, dtype == CUTQC_F64 ? 8 : 4, "tensor");
     if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
     std::vector<int> seen(d, 0), mq(k_out), oq(n_eff);
     for (int j = 0; j < k_out; ++j) {
@@ -1044,6 +1059,7 @@ int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates, int32_t 
     if (k_out + n_eff != d) fail(CUTQC_ERR_SHAPE, "every local qubit must be an output or a measured cut qubit");
     if ((k_in && !init_qubit) || (k_out && !meas_qubit) || (n_eff && !out_local) || !tensor)
       fail(CUTQC_ERR_ARG, "NULL array");
+    need_aligned(tensor, dtype == CUTQC_F64 ? 8 : 4, "tensor");   // written by the attribution kernels
     if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
     std::vector<int> seen(d, 0);
     SimPlan sp;
@@ -1080,6 +1096,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
     validate(problem, true);
     if (!role) fail(CUTQC_ERR_ARG, "role is NULL");
     if (!bins) fail(CUTQC_ERR_ARG, "bins is NULL");
+    need_aligned(bins, 16, "bins");
     if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X6) fail(CUTQC_ERR_ARG, "unknown algo");
     if (topk < 0 || topk > 32) fail(CUTQC_ERR_UNSUPPORTED, "topk must be in 0..32");
     if (topk > 0 && (!top_idx || !top_val)) fail(CUTQC_ERR_ARG, "NULL top_idx / top_val");
@@ -1204,6 +1221,10 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
     if (p->n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs n_qubits <= 34");
     if (p->n_sub != 2) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint supports circuits cut into two subcircuits");
     if (!grad_tensor || !grad_tensor[0] || !grad_tensor[1]) fail(CUTQC_ERR_ARG, "NULL gradient pointer");
+    need_aligned(grad_tensor[0], 16, "grad_tensor[0]");
+    need_aligned(grad_tensor[1], 16, "grad_tensor[1]");
+    need_aligned(grad_out, 16, "grad_out");
+    need_aligned(loss_value, 8, "loss_value");
     const bool maxcut = loss && loss->kind == CUTQC_LOSS_MAXCUT;
     if (loss && loss->kind != CUTQC_LOSS_NONE && !maxcut) fail(CUTQC_ERR_ARG, "unknown loss kind");
     if (!maxcut && !grad_out) fail(CUTQC_ERR_ARG, "need grad_out or a loss");
@@ -1332,6 +1353,10 @@ int cutqc_distance(const void* a, const void* b, int64_t n, int32_t dtype, doubl
                    void* stream) {
   return guarded([&] {
     if (!a || !b || !chi2 || !tv) fail(CUTQC_ERR_ARG, "NULL pointer");
+    need_aligned(a, dtype == CUTQC_F64 ? 8 : 4, "a");
+    need_aligned(b, dtype == CUTQC_F64 ? 8 : 4, "b");
+    need_aligned(chi2, 8, "chi2");
+    need_aligned(tv, 8, "tv");
     if (n < 1 || n > (int64_t(1) << 40)) fail(CUTQC_ERR_UNSUPPORTED, "distance needs 1 <= n <= 2^40");
     if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
     DeviceState& ds = device_state();
@@ -1347,6 +1372,9 @@ int cutqc_sample(const void* p, int64_t n, int32_t dtype, const double* u, int64
     if (n < 1 || n > (int64_t(1) << 40)) fail(CUTQC_ERR_UNSUPPORTED, "sampling needs 1 <= n <= 2^40");
     if (n_samples < 0) fail(CUTQC_ERR_ARG, "n_samples < 0");
     if (n_samples > 0 && (!u || !out)) fail(CUTQC_ERR_ARG, "NULL u or out");
+    need_aligned(p, dtype == CUTQC_F64 ? 8 : 4, "p");
+    need_aligned(u, 8, "u");
+    need_aligned(out, 8, "out");
     if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
     DeviceState& ds = device_state();
     char* scratch = aux_buffer(ds, sample_scratch_bytes(n)) + aux_distance_bytes();

@@ -88,7 +88,7 @@ struct Contraction {
   void* out = nullptr;
   double scale = 1.0;
   double* sum = nullptr;           // device double or null
-  int vecB = 1;                    // consecutive n -> consecutive g run length (1, 2, 4)
+  int vecB = 1;                    // consecutive n -> consecutive g run length (1, 2, 4, 8)
   int dtype = CUTQC_F32;
   const int32_t* nzA = nullptr;    // device row non-zero flags of A (or null)
   const int32_t* nzB = nullptr;

@@ -448,6 +448,14 @@ __device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
                : "memory");
 }
 
+// 32-byte streaming store of 8 consecutive FP32 values (the address must be
+// 32-byte aligned)
+__device__ __forceinline__ void st_cs_v8(float* p, const float* v) {
+  asm volatile("st.global.cs.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+
 __device__ __forceinline__ uint64_t deposit(const uint64_t* __restrict__ tab, int nbytes, uint64_t v) {
   uint64_t g = 0;
   for (int b = 0; b < nbytes; ++b) g += __ldg(tab + b * 256 + ((v >> (8 * b)) & 255));
@@ -487,7 +495,7 @@ struct TcArgs {
   float* out;
   float scale;
   double* sum;
-  int vecB;
+  int vecB;                   // consecutive columns that land on consecutive outputs: 1, 2, 4 or 8
   int staged;                 // restage the epilogue through shared memory (large outputs)
   int* status;
   float* topk_v;              // fused top-32 (dynamic-definition bins): one list of 32 per epilogue warp
@@ -634,6 +642,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int t = 0; t < 4; ++t) dtiny[t] = deposit(a.depB, 1, (uint64_t)t);
     const bool vec = a.vecB >= 4;
     const bool staged = vec && a.staged;
+    // 8 consecutive columns are 8 consecutive outputs (32 bytes, one sector);
+    // with the next output bits on the rows, the 8 lanes of a row group then
+    // write whole lines
+    const bool vec8 = a.vecB >= 8;
     // fused top-32 of the written values, ranked by (value, output index)
     constexpr bool tk = TK;
     float tk_v = -FLT_MAX;
@@ -755,6 +767,10 @@ __global__ void __launch_bounds__(THREADS, 1)
               __stcs(reinterpret_cast<float4*>(pbase + rel[st]), *reinterpret_cast<const float4*>(ebuf + so[st]));
             __syncwarp();
           }
+        } else if (vec8) {
+          float* orow = a.out + gbase + dep_lane + dc;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) st_cs_v8(orow + dlow[2 * j], v + 8 * j);
         } else if (vec) {
           float* orow = a.out + gbase + dep_lane + dc;
 #pragma unroll
@@ -998,7 +1014,9 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   a.out = static_cast<float*>(c.out);
   a.scale = (float)c.scale;
   a.sum = c.sum;
-  a.vecB = c.vecB;
+  // 32-byte stores need a 32-byte aligned output (16 bytes is the minimum the
+  // entry points accept)
+  a.vecB = (c.vecB >= 8 && reinterpret_cast<uintptr_t>(c.out) % 32 != 0) ? 4 : c.vecB;
   // restage through shared memory for outputs beyond L2 (128 MiB of FP32) and
   // for outputs in host memory, where whole-line stores matter most
   a.staged = (c.out_host || M * N >= (int64_t(1) << 25)) ? 1 : 0;

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -67,6 +68,9 @@ void run(void* ctx) {
   const Call& call = *static_cast<const Call*>(ctx);
   if (!call.p) fail(CUTQC_ERR_ARG, "problem is NULL");
   if (!call.out) fail(CUTQC_ERR_ARG, "out is NULL");
+  // 16-byte vector stores (the tensors are checked by the planner)
+  if (reinterpret_cast<uintptr_t>(call.out) % 16) fail(CUTQC_ERR_ARG, "out must be 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(call.sum_p) % 8) fail(CUTQC_ERR_ARG, "sum_p must be 8-byte aligned");
   PairPlanHost h;
   plan_pair_host(call.p, h);
   // scratch layout: rows | compacted rows | count | row flags A, B | row max A, B | deposit tables A, B

@@ -126,3 +126,46 @@ def test_distance_and_sampling_argument_errors(capi):
     assert f.cutqc_sample(a, 8, capi.CUTQC_F32, None, 4, b, None) == capi.CUTQC_ERR_ARG
     assert f.cutqc_sample(a, 8, capi.CUTQC_F32, a, -1, b, None) == capi.CUTQC_ERR_ARG
     assert f.cutqc_sample(a, 1 << 41, capi.CUTQC_F32, a, 4, b, None) == capi.CUTQC_ERR_UNSUPPORTED
+
+
+def test_misaligned_pointers_are_rejected(capi):
+    """Device arrays are accessed with 16-byte vector loads and stores, so a
+    pointer off that grid is an argument error on the host, never a fault."""
+    f, i32, ARG = capi._lib, capi._i32, capi.CUTQC_ERR_ARG
+    # a subcircuit tensor 4 bytes off
+    spec = list(GOOD)
+    p, keep, arr = _problem(capi, spec, 10, 1)
+    arr[1].tensor = C.c_void_p(0x1004)
+    assert _fd(capi, p) == ARG and "16-byte" in capi.last_error()
+    # the full-definition output and its FP64 sum
+    p, keep, arr = _problem(capi, GOOD, 10, 1)
+    out = (C.c_void_p * 1)(C.c_void_p(0x2008))
+    assert f.cutqc_reconstruct_fd(C.byref(p), 1, out, 0, None, None) == ARG
+    out = (C.c_void_p * 1)(C.c_void_p(0x2000))
+    assert f.cutqc_reconstruct_fd(C.byref(p), 1, out, 0, C.c_void_p(0x3004), None) == ARG
+    assert "sum_p" in capi.last_error()
+    assert f.cutqc_reconstruct_fd_noalloc(C.byref(p), C.c_void_p(0x2004), None, None) == ARG
+    # dynamic-definition bins
+    role = (C.c_int8 * 10)(*([0] * 10))
+    assert f.cutqc_reconstruct_dd(C.byref(p), role, C.c_void_p(0x2004), 0, None, None, 0, None) == ARG
+    assert "bins" in capi.last_error()
+    # adjoint gradients
+    grads = (C.c_void_p * 2)(C.c_void_p(0x4000), C.c_void_p(0x5002))
+    assert f.cutqc_reconstruct_backward(C.byref(p), C.c_void_p(0x6000), None, grads, None, None) == ARG
+    # attribution and simulation
+    # (element alignment: these kernels choose vector or scalar accesses)
+    args = [C.c_void_p(0x2002), 3, 1, i32([2]), 1, i32([0, 1]), 2, capi.CUTQC_F32, C.c_void_p(0x3000), None]
+    assert f.cutqc_attribute(*args) == ARG
+    args[0], args[8] = C.c_void_p(0x2000), C.c_void_p(0x3004)
+    args[7] = capi.CUTQC_F64
+    assert f.cutqc_attribute(*args) == ARG
+    g = (capi.cutqc_gate * 1)(capi.cutqc_gate(0, 0, 0, 0.0))
+    st = f.cutqc_simulate_subcircuit(g, 1, 2, None, 0, None, 0, i32([0, 1]), 2, 1, C.c_void_p(0x3002), None)
+    assert st == ARG
+    # distance and sampling take element-aligned arrays, scalars need 8 bytes
+    a, b = C.c_void_p(0x2000), C.c_void_p(0x3000)
+    assert f.cutqc_distance(C.c_void_p(0x2002), b, 8, capi.CUTQC_F32, a, b, None) == ARG
+    assert f.cutqc_distance(a, C.c_void_p(0x3004), 8, capi.CUTQC_F64, a, b, None) == ARG
+    assert f.cutqc_distance(a, b, 8, capi.CUTQC_F32, C.c_void_p(0x2004), b, None) == ARG
+    assert f.cutqc_sample(a, 8, capi.CUTQC_F32, C.c_void_p(0x2004), 4, b, None) == ARG
+    assert f.cutqc_sample(a, 8, capi.CUTQC_F32, a, 4, C.c_void_p(0x3002), None) == ARG

@@ -113,6 +113,31 @@ def sup(env):
     return cc, [T.astype(np.float32) for T in Ts]
 
 
+def test_misaligned_output_is_rejected(env, sup):
+    """A device output one element off the 16-byte grid (a tensor view) is an
+    argument error before anything is launched; the vector stores never see
+    it.  A 16-byte aligned view that is not 32-byte aligned is accepted and
+    gives the same result as a fresh buffer: on the 4x6 workload the
+    tensor-core epilogue writes 8 consecutive outputs per 32-byte store, and
+    falls back to 16-byte stores for that view."""
+    torch, cutqc = env
+    cc, T32 = sup
+    ts = to_dev(torch, T32, torch.float32)
+    ref, _ = cutqc.reconstruct_fd(cc, ts, algo="tc_bf16x3")
+    big = torch.full((2 ** cc.n + 8,), -1.0, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    n0 = cutqc.launch_count()
+    with pytest.raises(cutqc.CutQCError, match="16-byte"):
+        cutqc.reconstruct_fd(cc, ts, algo="tc_bf16x3", out=big[1:1 + 2 ** cc.n])
+    assert cutqc.launch_count() == n0
+    view = big[4:4 + 2 ** cc.n]
+    assert view.data_ptr() % 32 == 16
+    o, _ = cutqc.reconstruct_fd(cc, ts, algo="tc_bf16x3", out=view)
+    torch.cuda.synchronize()
+    assert torch.equal(view, ref)
+    assert torch.all(big[:4] == -1.0) and torch.all(big[4 + 2 ** cc.n:] == -1.0)
+
+
 @pytest.mark.parametrize("algo", ["cc", "auto"])
 def test_supremacy_4x6_full_size_sampled(env, sup, algo):
     """Full size (2^24 outputs, the launch configuration the benchmark times):
