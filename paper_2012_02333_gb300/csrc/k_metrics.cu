@@ -298,21 +298,82 @@ __device__ __forceinline__ FF ff_of(double x) {
 
 // Warps take the draws 32 at a time: each lane first binary-searches the chunk
 // of its own draw (32 searches in flight per warp), then the warp resolves
-// the 32 draws one after the other inside their chunks.
+// the 32 draws one after the other inside their chunks.  A draw's chunk is
+// staged in a padded 32 x 33 shared-memory tile (row q = weights 32q .. 32q +
+// 31): FP32 chunks come in with 16-byte loads (lane l takes weights 4l + 128i
+// .. + 3), partial chunks, FP64 and unaligned inputs with coalesced scalar
+// loads (weight l + 32i); lane q then reads its row without bank conflicts
+// (33-word pitch).  The next draw's chunk is loaded into registers while the
+// current one is resolved.
+constexpr int DRAW_THREADS = 256;
+// warps per block: the tile of one warp is 4.2 KB (FP32) or 8.4 KB (FP64),
+// and a block's static shared memory stays at 33 KB either way
 template <typename T>
-__global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* __restrict__ P1,
-                              const double* __restrict__ L1, int64_t nch, const double* __restrict__ total,
-                              const double* __restrict__ u, int64_t m, int64_t* __restrict__ out) {
+constexpr int draw_warps() {
+  return sizeof(T) == 4 ? DRAW_THREADS / 32 : DRAW_THREADS / 64;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(DRAW_THREADS) k_sample_draw(const T* __restrict__ p, int64_t n,
+                                                              const double* __restrict__ P1,
+                                                              const double* __restrict__ L1, int64_t nch,
+                                                              const double* __restrict__ total,
+                                                              const double* __restrict__ u, int64_t m,
+                                                              int64_t* __restrict__ out, int vec_ok) {
+  __shared__ T tile[draw_warps<T>()][32][33];
   const int lane = threadIdx.x & 31;
+  T(*wb)[33] = tile[threadIdx.x >> 5];
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const double tot = *total;
+  const bool vec4 = sizeof(T) == 4 && vec_ok;
+  // this lane's 32 weights of a chunk, in the load order of its form
+  T v[32];
+  bool vform = false;
+  auto load = [&](int64_t c) {
+    const int64_t base = c * CH;
+    vform = vec4 && base + CH <= n;
+    if (vform) {
+      const float4* q = reinterpret_cast<const float4*>(p + base) + lane;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float4 x = __ldg(q + 32 * i);
+        v[4 * i] = x.x;
+        v[4 * i + 1] = x.y;
+        v[4 * i + 2] = x.z;
+        v[4 * i + 3] = x.w;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const int64_t idx = base + lane + 32 * i;
+        v[i] = idx < n ? __ldg(p + idx) : T(0);
+      }
+    }
+  };
+  auto stage = [&]() {
+    if (vform) {
+      // weight e = 4 lane + 128 i + k goes to row e / 32, column e % 32
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) wb[4 * i + (lane >> 3)][4 * (lane & 7) + k] = v[4 * i + k];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i) wb[i][lane] = v[i];
+    }
+  };
   for (int64_t k0 = warp * 32; k0 < m; k0 += nw * 32) {
+    const int nd = (int)(m - k0 < 32 ? m - k0 : 32);
+    if (!(tot > 0.0)) {   // no outcome carries weight
+      if (lane < nd) out[k0 + lane] = -1;
+      continue;
+    }
     // this lane's draw: the largest chunk c with P1[c] <= t that carries weight
     const int64_t kl = k0 + lane;
     int64_t my_c = 0;
     double my_r = 0.0;
-    if (kl < m && tot > 0.0) {
+    if (kl < m) {
       const double t = u[kl] * tot;
       int64_t lo = 0, hi = nch - 1;
       while (lo < hi) {
@@ -324,27 +385,29 @@ __global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* 
       my_c = lo;
       my_r = t - P1[lo];
     }
-    const int nd = (int)(m - k0 < 32 ? m - k0 : 32);
+    int64_t c_next = __shfl_sync(0xffffffffu, my_c, 0);
+    load(c_next);
     for (int j = 0; j < nd; ++j) {
       const int64_t k = k0 + j;
-      if (!(tot > 0.0)) {   // no outcome carries weight
-        if (lane == 0) out[k] = -1;
-        continue;
-      }
-      const int64_t c = __shfl_sync(0xffffffffu, my_c, j);
+      const int64_t c = c_next;
       const double r = __shfl_sync(0xffffffffu, my_r, j);
-      // lane sums of the chunk's 32 runs of 32 weights
+      __syncwarp();   // the previous draw has finished reading the tile
+      stage();
+      __syncwarp();
+      if (j + 1 < nd) {
+        c_next = __shfl_sync(0xffffffffu, my_c, j + 1);
+        load(c_next);   // in flight while this draw is resolved
+      }
+      // lane sums of the chunk's 32 runs of 32 weights (row `lane` of the tile)
       const int64_t base = c * CH + 32 * lane;
       FF ls{};
       double ld = 0.0;
+#pragma unroll 8
       for (int i = 0; i < 32; ++i) {
-        const int64_t idx = base + i;
-        if (idx < n) {
-          if constexpr (sizeof(T) == 8)
-            ld += fmax(p[idx], 0.0);
-          else
-            ls = ff_add(ls, weight32(p[idx]));
-        }
+        if constexpr (sizeof(T) == 8)
+          ld += fmax(wb[lane][i], 0.0);
+        else
+          ls = ff_add(ls, weight32(wb[lane][i]));
       }
       const double lsum = sizeof(T) == 8 ? ld : ff_value(ls);
       double incl = lsum;
@@ -365,7 +428,7 @@ __global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* 
           for (int i = 0; i < 32 && pick < 0; ++i) {
             const int64_t idx = base + i;
             if (idx >= n) break;
-            const double w = fmax(p[idx], 0.0);
+            const double w = fmax(wb[L][i], 0.0);
             if (w > 0.0) last_w = idx;
             cd += w;
             if (w > 0.0 && cd > r2) pick = idx;
@@ -377,7 +440,7 @@ __global__ void k_sample_draw(const T* __restrict__ p, int64_t n, const double* 
           for (int i = 0; i < 32 && pick < 0; ++i) {
             const int64_t idx = base + i;
             if (idx >= n) break;
-            const float w = weight32(p[idx]);
+            const float w = weight32(wb[L][i]);
             if (w > 0.0f) last_w = idx;
             cs = ff_add(cs, w);
             if (w > 0.0f && ff_greater(cs, rr)) pick = idx;
@@ -446,11 +509,16 @@ void launch_sample(const void* p, int64_t n, int dtype, const double* u, int64_t
   count_launch();
   check_launch("k_sample_tile_scan");
   if (m == 0) return;
-  const unsigned gd = grid_for((m + 31) / 32 * 32, 256, 152 * 16);
-  if (dtype == CUTQC_F64)
-    k_sample_draw<double><<<gd, 256, 0, s>>>(static_cast<const double*>(p), n, P1, L1, nch, total, u, m, out);
-  else
-    k_sample_draw<float><<<gd, 256, 0, s>>>(static_cast<const float*>(p), n, P1, L1, nch, total, u, m, out);
+  const int vec_ok = (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+  if (dtype == CUTQC_F64) {
+    constexpr int bt = 32 * draw_warps<double>();
+    k_sample_draw<double><<<grid_for((m + 31) / 32 * 32, bt, 152 * 16), bt, 0, s>>>(
+        static_cast<const double*>(p), n, P1, L1, nch, total, u, m, out, vec_ok);
+  } else {
+    constexpr int bt = 32 * draw_warps<float>();
+    k_sample_draw<float><<<grid_for((m + 31) / 32 * 32, bt, 152 * 16), bt, 0, s>>>(
+        static_cast<const float*>(p), n, P1, L1, nch, total, u, m, out, vec_ok);
+  }
   count_launch();
   check_launch("k_sample_draw");
 }

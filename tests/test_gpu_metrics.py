@@ -105,6 +105,25 @@ def check_draws(p64, u, got, tol_rel=1e-11):
     assert clear.mean() > 0.99
 
 
+def test_sampling_from_unaligned_view(env):
+    """FP32 weights that are element- but not 16-byte aligned (a view one
+    entry into a buffer): whole chunks then come in by scalar loads instead of
+    16-byte loads; the draws obey the same parity rule."""
+    torch, cutqc = env
+    n = (1 << 16) + 300
+    rng = np.random.default_rng(77)
+    p = rng.random(n) ** 3
+    p[rng.random(n) < 0.3] = 0.0
+    p /= p.sum()
+    buf = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = torch.tensor(p, dtype=torch.float32, device="cuda")
+    view = buf[1:]
+    assert view.data_ptr() % 16 == 4
+    u = rng.random(50000)
+    got = cutqc.cutqc_sample(view, torch.tensor(u, device="cuda")).cpu().numpy()
+    check_draws(view.double().cpu().numpy(), u, got)
+
+
 @pytest.mark.parametrize("n", [1, 5, 1024, 1025, 3000, (1 << 20) + 7])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_sampling_parity(env, n, dtype):
