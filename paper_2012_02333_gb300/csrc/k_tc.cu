@@ -502,11 +502,47 @@ struct TcArgs {
   int64_t* topk_i;
 };
 
+// One work item of a CTA: rows tm*128 .. +127 and columns tn*256 + n0 ..
+// + w - 1 of the output.  CTA b takes the full tiles b, b + G, b + 2G, ...
+// (G CTAs) while whole rounds remain; when the last round has L < G tiles
+// and 2L <= G, those tiles are cut into halves of 128 columns and CTA b < 2L
+// takes half b % 2 of leftover tile b / 2, so no CTA owns a whole extra tile
+// while others idle.  The producer, the MMA issuer and the epilogue walk the
+// same list.
+struct TcItem {
+  int tm, tn, n0, w;
+};
+__device__ __forceinline__ bool tc_item(const TcArgs& a, int i, TcItem& it) {
+  const int G = gridDim.x, b = blockIdx.x;
+  const int ntiles = a.tilesM * a.tilesN;
+  const int R = ntiles / G, L = ntiles - R * G;
+  const int S = (L > 0 && 2 * L <= G) ? 2 : 1;
+  int tile;
+  it.n0 = 0;
+  it.w = BN;
+  if (i < R) {
+    tile = b + i * G;
+  } else if (i == R && b < L * S) {
+    tile = R * G + b / S;
+    if (S == 2) {
+      it.w = BN / 2;
+      it.n0 = (b & 1) * (BN / 2);
+    }
+  } else {
+    return false;
+  }
+  it.tm = tile % a.tilesM;
+  it.tn = tile / a.tilesM;
+  return true;
+}
+
 // TK: also keep the fused top-32 (a separate instantiation, so the plain
-// contraction carries none of its code)
+// contraction carries none of its code).  tmBh: the B operand map with a
+// 128-row box, for half-width items.
 template <bool TK>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmBh, const TcArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGE_AREA);   // 256 bytes of barriers
@@ -549,25 +585,28 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int stages = nseg == 3 ? 4 : 3;
   const uint32_t stage_bytes = (uint32_t)npieces * (A_PIECE + B_PIECE);
   const int nkb = (kc + KS - 1) / KS;                       // 32-wide k steps
-  const int ntiles = a.tilesM * a.tilesN;
 
   if (nkb > 0 && warp == 0) {
     // ---- TMA producer (the warp waits, lane 0 issues): every split piece of
-    // a 32-wide k step of A (128 rows) and B (256 rows) into one stage
+    // a 32-wide k step of A (128 rows) and B (the item's 256 or 128 rows)
+    // into one stage (a half-width B piece fills the first half of its slot)
     int stage = 0;
     uint32_t phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-      const int tm = tile % a.tilesM, tn = tile / a.tilesM;
+    TcItem it;
+    for (int i = 0; ok && tc_item(a, i, it); ++i) {
+      const uint32_t item_bytes = (uint32_t)npieces * (uint32_t)(A_PIECE + it.w * KS * 2);
+      const CUtensorMap* mapB = it.w == BN ? &tmB : &tmBh;
       for (int kb = 0; kb < nkb; ++kb) {
         ok = __all_sync(0xffffffffu, mbar_wait(&empty[stage], phase ^ 1, abort_flag));
         if (!ok) break;
         if (lane == 0) {
           uint8_t* st = smem + stage * stage_bytes;
-          mbar_expect_tx(&full[stage], stage_bytes);
+          mbar_expect_tx(&full[stage], item_bytes);
           for (int pc = 0; pc < npieces; ++pc) {
-            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KS, pc * a.M + tm * BM, &full[stage]);
-            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, &tmB, kb * KS, pc * a.N + tn * BN, &full[stage]);
+            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KS, pc * a.M + it.tm * BM, &full[stage]);
+            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, mapB, kb * KS, pc * a.N + it.tn * BN + it.n0,
+                        &full[stage]);
           }
         }
         __syncwarp();
@@ -580,13 +619,14 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (nkb > 0 && warp == 1) {
     // ---- MMA issuer (the warp waits, lane 0 issues): per stage the nseg
     // products hh, hm, mh (, hl, lh, mm), two K=16 MMAs each
-    const uint32_t idesc = idesc_bf16(BM, BN);
     int stage = 0;
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    TcItem it;
+    for (int i = 0; ok && tc_item(a, i, it); ++i) {
+      const uint32_t idesc = idesc_bf16(BM, it.w);
       ok = __all_sync(0xffffffffu, mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag));
       if (!ok) break;
       tc_fence_after();
@@ -626,7 +666,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int q = warp & 3;
     const int hf = (warp - 2) / 4;
     constexpr int CPW = BN / 32 / (EPI_WARPS / 4);   // 32-column chunks per warp
-    static_assert(CPW % 2 == 0, "chunks go in pairs");
+    static_assert(CPW % 4 == 0, "chunks go in pairs, also in half-width items");
     double local = 0.0;
     // the deposit is additive over disjoint index bits, so a row's output
     // address is dep(row base) + dep(lane) + dep(chunk column base) +
@@ -692,11 +732,11 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint64_t dpass1 = deposit(a.depA, 1, 16ull);   // row bit 4: second pass
     int acc = 0;
     uint32_t acc_phase = 0;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int tm = tile % a.tilesM, tn = tile / a.tilesM;
-      // this thread's row: tm*128 + 32q + lane; columns tn*256 + 32c + j
-      const uint64_t gbase = deposit(a.depA, a.nbA, (uint64_t)tm * BM + 32 * q) +
-                             deposit(a.depB, a.nbB, (uint64_t)tn * BN);
+    TcItem it;
+    for (int i = 0; tc_item(a, i, it); ++i) {
+      // this thread's row: tm*128 + 32q + lane; columns tn*256 + n0 + 32c + j
+      const uint64_t gbase = deposit(a.depA, a.nbA, (uint64_t)it.tm * BM + 32 * q) +
+                             deposit(a.depB, a.nbB, (uint64_t)it.tn * BN + it.n0);
       if (nkb > 0) {
         const bool ok = mbar_wait(&tfull[acc], acc_phase, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
@@ -787,10 +827,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint32_t ra[32], rb[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) ra[j] = rb[j] = 0u;
-      const int c0 = hf * CPW;
+      // chunks of this warp in the item: CPW, or half as many for a half-width item
+      const int cpw = it.w == BN ? CPW : CPW / 2;
+      const int c0 = hf * cpw;
       if (nkb > 0) tmem_ld32_issue(taddr(c0), ra);
 #pragma unroll 1
-      for (int c = c0; c < c0 + CPW; c += 2) {
+      for (int c = c0; c < c0 + cpw; c += 2) {
         if (nkb > 0) {
           tmem_wait32(ra);
           tmem_ld32_issue(taddr(c + 1), rb);
@@ -798,7 +840,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         process(c, ra);
         if (nkb > 0) {
           tmem_wait32(rb);
-          if (c + 2 < c0 + CPW) tmem_ld32_issue(taddr(c + 2), ra);
+          if (c + 2 < c0 + cpw) tmem_ld32_issue(taddr(c + 2), ra);
         }
         process(c + 1, rb);
       }
@@ -999,6 +1041,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   // three pieces of each operand stacked along rows: [piece * rows + row][k]
   const CUtensorMap tmA = make_map(Ab, (uint64_t)M * 3, (uint64_t)Kp, BM);
   const CUtensorMap tmB = make_map(Bb, (uint64_t)N * 3, (uint64_t)Kp, BN);
+  const CUtensorMap tmBh = make_map(Bb, (uint64_t)N * 3, (uint64_t)Kp, BN / 2);
   TcArgs a;
   a.Kp = Kp;
   a.M = (int)M;
@@ -1038,9 +1081,9 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   cudaEvent_t ev = nullptr;
   if (c.profile) prof_begin(s, &ev);
   if (a.topk_v)
-    CUTQC_CUDA(launch_pdl(k_tc_gemm<true>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
+    CUTQC_CUDA(launch_pdl(k_tc_gemm<true>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, tmBh, a));
   else
-    CUTQC_CUDA(launch_pdl(k_tc_gemm<false>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, a));
+    CUTQC_CUDA(launch_pdl(k_tc_gemm<false>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, tmBh, a));
   count_launch();
   check_launch("k_tc_gemm");
   if (c.topk_nlists) *c.topk_nlists = c.topk_v ? grid * EPI_WARPS : 0;
