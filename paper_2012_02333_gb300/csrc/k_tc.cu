@@ -144,10 +144,15 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
     for (int t0 = 0; t0 < a.kmax; t0 += 256) {
       const int t = t0 + tid;
       int keep = 0, r0 = 0, r1 = 0;
+      float mxa = 0.0f, mxb = 0.0f;
       if (t < a.kmax) {
         r0 = (pre && t0 == 0) ? pre_r0 : ra[t];
         r1 = (pre && t0 == 0) ? pre_r1 : rb[t];
-        keep = __ldcg(a.nzA + r0) && __ldcg(a.nzB + r1);
+        // flags and maxima in one round trip (the maxima count only when kept)
+        const int nza = __ldcg(a.nzA + r0), nzb = __ldcg(a.nzB + r1);
+        mxa = __ldcg(a.rmaxA + r0);
+        mxb = __ldcg(a.rmaxB + r1);
+        keep = nza && nzb;
       }
       const unsigned m = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) warp_tot[warp] = __popc(m);
@@ -160,7 +165,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
       if (keep) {
         const int ci = base_s + off + __popc(m & ((1u << lane) - 1u));
         if (ci >= k0 && ci < k0 + 64) rowsel[ci - k0] = which == 0 ? r0 : r1;
-        sacc = fmaf(__ldcg(a.rmaxA + r0), __ldcg(a.rmaxB + r1), sacc);
+        sacc = fmaf(mxa, mxb, sacc);
       }
       __syncthreads();
       if (tid == 0) base_s += tot;
@@ -227,11 +232,15 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
   }
   __nv_bfloat16* out = a.out[which];
   const int npieces = nseg == 3 ? 2 : 3;
-  for (int pc = 0; pc < npieces; ++pc) {
-    const uint4* src = reinterpret_cast<const uint4*>(part[pc]);
-    uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)pc * cols + m0 + ml) * a.Kp + k0 + kq);
-    dst[0] = src[0];
-    dst[1] = src[1];
+  // unrolled over the three possible pieces so `part` stays in registers
+#pragma unroll
+  for (int pc = 0; pc < 3; ++pc) {
+    if (pc < npieces) {
+      const uint4* src = reinterpret_cast<const uint4*>(part[pc]);
+      uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)pc * cols + m0 + ml) * a.Kp + k0 + kq);
+      dst[0] = src[0];
+      dst[1] = src[1];
+    }
   }
 }
 
@@ -252,7 +261,7 @@ struct StatsArgs {
   int64_t rows[2];
   int32_t* nz[2];
   float* rmax[2];
-  unsigned* barrier;   // zeroed before the launch
+  unsigned* barrier;   // zeroed before the launch (its own per problem: batches run concurrently)
   int* status;
   int tilesX, tilesY;
 };
@@ -308,9 +317,13 @@ __global__ void __launch_bounds__(256) k_stats_prep(const PrepArgs a, const Stat
   }
   const int64_t nrows = sa.rows[0] + sa.rows[1];
   for (int64_t r = blockIdx.x; r < nrows; r += gridDim.x) {
-    const int j = r < sa.rows[0] ? 0 : 1;
-    const int64_t rr = j == 0 ? r : r - sa.rows[0];
-    stats_row(a.T[j] + rr * a.cols[j], a.cols[j], sa.nz[j] + rr, sa.rmax[j] + rr);
+    // selects, not a dynamic index into the parameter arrays (which would
+    // copy them to local memory)
+    const bool j0 = r < sa.rows[0];
+    const int64_t rr = j0 ? r : r - sa.rows[0];
+    const int64_t cols = j0 ? a.cols[0] : a.cols[1];
+    stats_row((j0 ? a.T[0] : a.T[1]) + rr * cols, cols, (j0 ? sa.nz[0] : sa.nz[1]) + rr,
+              (j0 ? sa.rmax[0] : sa.rmax[1]) + rr);
   }
   // grid barrier
   __shared__ int pass;
