@@ -13,7 +13,9 @@ none of the method's arithmetic.
 Modules
   statevector   textbook statevector simulation (Sec. 2, Fig. 2a ground truth)
   attribution   subcircuit variants (Fig. 3 / Sec. 3.1) and shot attribution
-                (Eq. 3, Sec. 3.2.2) into Pauli-indexed subcircuit tensors
+                (Eq. 3, Sec. 3.2.2) into Pauli-indexed subcircuit tensors, and
+                the merged tensors of a dynamic-definition recursion taken
+                straight from the variant distributions
   reconstruct   full-definition sum (Sec. 3.2.3, Sec. 3.3, Sec. 4.2), dynamic
                 definition (Algorithm 1, Sec. 4.3), and the gradient of an
                 expectation value over the reconstructed distribution

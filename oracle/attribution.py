@@ -125,6 +125,18 @@ def attribute(sub, p: np.ndarray, snap: float = 2.0 ** -40) -> np.ndarray:
     return T
 
 
+def attribute_merged(sub, p: np.ndarray, roles, snap: float = 2.0 ** -40) -> np.ndarray:
+    """The merged tensor one recursion of Algorithm 1 contracts, taken from the
+    variant distributions: the attributed tensor (Eq. 3 then Eq. 2,
+    `attribute`) merged over the recursion's roles (`reconstruct.merge`:
+    zoomed outputs fixed at their bit, merged outputs summed, active outputs
+    kept in output order).  roles[q] is indexed by global qubit (0 active,
+    1 merged, 2 zoomed at 0, 3 zoomed at 1).  Shape (4^k_in * 4^k_out,
+    2^#active outputs)."""
+    from .reconstruct import merge
+    return merge(sub, attribute(sub, p, snap), roles)
+
+
 def subcircuit_tensor(sub) -> np.ndarray:
     """T_c for one subcircuit, in float64."""
     return attribute(sub, variant_probabilities(sub))

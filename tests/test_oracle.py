@@ -286,6 +286,75 @@ def test_dd_bins_are_brute_force_marginals(name, make):
             assert rec["bins"].sum() == pytest.approx(recs[ri]["bins"][bi], abs=1e-13)
 
 
+def _roles_cycle(cc, pattern):
+    """Roles over the global qubits: the pattern repeated over the qubit order."""
+    return [pattern[q % len(pattern)] for q in range(cc.n)]
+
+
+@pytest.mark.parametrize("pattern", [(0, 1, 2, 3), (1, 0, 1, 3, 0), (1, 1, 1, 2), (0, 0, 0, 0)])
+def test_attribute_merged_is_attribution_of_merged_variants(pattern):
+    """Merging (Algorithm 1) sums over output qubits and fixes zoomed ones,
+    while Eq. 3 and Eq. 2 act only on the cut qubits' outcomes and the init
+    variants, so attributing then merging equals attributing the variant
+    distributions already summed over the merged outputs.  Checked with
+    random, non-physical distributions (nothing cancels by accident) against
+    that second route, built here from plain axis sums and a reduced
+    subcircuit with the merged and zoomed qubits removed."""
+    cc = C.qaoa_2cluster(4, 1)
+    rng = np.random.default_rng(5)
+    roles = _roles_cycle(cc, pattern)
+    for sub in cc.subs:
+        V = (4 ** sub.k_in) * (3 ** sub.k_out)
+        p = rng.random((V, 2 ** sub.d))
+        got = at.attribute_merged(sub, p, roles)
+        role_of = {lq: roles[gq] for lq, gq in sub.outputs}
+        arr = p.reshape([V] + [2] * sub.d)
+        idx = [slice(None)] + [({2: 0, 3: 1}.get(role_of.get(lq), slice(None))) for lq in range(sub.d)]
+        red = arr[tuple(idx)]
+        remaining = [lq for lq in range(sub.d) if role_of.get(lq) not in (2, 3)]
+        red = red.sum(axis=tuple(1 + remaining.index(lq) for lq in remaining if role_of.get(lq) == 1))
+        kept = [lq for lq in remaining if role_of.get(lq) != 1]
+        pos = {lq: i for i, lq in enumerate(kept)}
+        reduced = C.Subcircuit(d=len(kept), gates=[], in_slots=[(0, c) for _, c in sub.in_slots],
+                               out_slots=[(pos[lq], c) for lq, c in sub.out_slots],
+                               outputs=[(pos[lq], gq) for lq, gq in sub.outputs if roles[gq] == 0])
+        want = at.attribute(reduced, red.reshape(V, -1)).reshape(got.shape)
+        assert got.shape == (4 ** (sub.k_in + sub.k_out), 2 ** sum(1 for _, g in sub.outputs if roles[g] == 0))
+        assert np.allclose(got, want, atol=1e-12, rtol=0)
+        assert np.abs(got).max() > 0.1
+
+
+def test_attribute_merged_bins_are_brute_force_marginals():
+    """A recursion's bins contracted from the fused merged tensors of the
+    physical variants equal the uncut circuit's marginal over the merged
+    qubits with the zoomed ones fixed."""
+    cc = C.grid_blocks(3, 4, 8, 1, 1, 2, 6, 9)
+    roles = _roles_cycle(cc, (0, 1, 3, 0, 1, 2))
+    Ms = [at.attribute_merged(s, at.variant_probabilities(s), roles) for s in cc.subs]
+    active = [q for q in range(cc.n) if roles[q] == 0]
+    rank = {q: i for i, q in enumerate(active)}
+    na = len(active)
+    bins = np.zeros(2 ** na)
+    for e in range(4 ** cc.n_cuts):
+        dg = [(e >> (2 * (cc.n_cuts - 1 - k))) & 3 for k in range(cc.n_cuts)]
+        term = np.ones(2 ** na)
+        for s, M in zip(cc.subs, Ms):
+            qs = [g for _, g in s.outputs if roles[g] == 0]
+            vals = M[rc.row_of(s, dg)]
+            for b in range(2 ** na):
+                j = 0
+                for q in qs:
+                    j = 2 * j + ((b >> (na - 1 - rank[q])) & 1)
+                term[b] *= vals[j]
+        bins += term
+    bins *= 2.0 ** -cc.n_cuts
+    ref = sv.probabilities(cc.circuit).reshape([2] * cc.n)
+    ref = ref[tuple(0 if r == 2 else 1 if r == 3 else slice(None) for r in roles)]
+    kept = [r for r in roles if r in (0, 1)]
+    want = ref.sum(axis=tuple(i for i, r in enumerate(kept) if r == 1)).reshape(-1)
+    assert np.allclose(bins, want, atol=1e-13)
+
+
 def test_dd_zoom_roles_reading():
     roles = rc.initial_roles(6, 2)
     assert roles == [0, 0, 1, 1, 1, 1]
