@@ -55,8 +55,8 @@ def parse():
     ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
-                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "metrics_qaoa30",
-                             "sim_supremacy4x6"],
+                    choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "attr_merged_qaoa30",
+                             "metrics_qaoa30", "sim_supremacy4x6"],
                     help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
@@ -509,6 +509,36 @@ def run_other(args):
         cfg = {"workload": "metrics_qaoa30_fp32", "n": pa.numel(),
                "step": "chi^2 (Eq. 16) and total variation of two 2^30-entry distributions; sampling timed beside it"}
         del pb
+    elif w == "attr_merged_qaoa30":
+        # the merged tensors of a first dynamic-definition recursion (20 of 30
+        # qubits active, the rest merged) of both QAOA-30 subcircuits, straight
+        # from seeded synthetic variant distributions
+        cc = circuits.qaoa_2cluster(15, 0)
+        roles = [0 if q < 20 else 1 for q in range(cc.n)]
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(0)
+        probs, outs = [], []
+        for sub in cc.subs:
+            v = torch.rand((4 ** sub.k_in) * (3 ** sub.k_out), 2 ** sub.d, generator=gen, device=dev)
+            probs.append((v / v.sum(dim=1, keepdim=True)).reshape(-1).contiguous())
+            outs.append(cutqc.cutqc_attribute_merged(sub, probs[-1], roles))
+
+        def attr_step():
+            for sub, p, o in zip(cc.subs, probs, outs):
+                cutqc.cutqc_attribute_merged(sub, p, roles, o)
+        ms = timed(attr_step)
+        bytes_alg = sum(p.numel() * 4 + o.numel() * 4 for p, o in zip(probs, outs))
+        pk, pk_src = peaks()
+        extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                              "unit": "GB/s", "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
+                              "traffic": None, "algorithmic_bytes": bytes_alg, "peak_file": pk_src}}
+        units, unit, dtype = sum(p.numel() for p in probs), "variant outcomes/s", "f32 in, compensated f32 sums"
+        cfg = {"workload": "attr_merged_qaoa30_fp32", "roles": "qubits 0-19 active, 20-29 merged",
+               "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
+               "merged_tensor_entries": [o.numel() for o in outs],
+               "inputs": "seeded uniform variant distributions normalised per variant (synthetic shot frequencies)",
+               "step": "merge the variant distributions over the merged outputs, then Eq. 3 and Eq. 2, both "
+                       "subcircuits"}
     elif w == "attr_qaoa30":
         # attribution of both QAOA-30 subcircuits from seeded synthetic variant
         # distributions (uniform numbers normalised per variant, the shape of

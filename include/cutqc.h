@@ -34,8 +34,9 @@
  *  - Alignment: device arrays given to the reconstruction calls (subcircuit
  *    tensors, out, bins, grad_out, grad_tensor) must be 16-byte aligned, as
  *    cudaMalloc and PyTorch allocations are (a tensor view at an element
- *    offset may not be); cutqc_attribute, cutqc_simulate_subcircuit,
- *    cutqc_distance and cutqc_sample take any element-aligned array; device
+ *    offset may not be); cutqc_attribute, cutqc_attribute_merged,
+ *    cutqc_simulate_subcircuit, cutqc_distance and cutqc_sample take any
+ *    element-aligned array; device
  *    scalars (sum_p, loss_value, chi2, tv) and the u / out arrays of
  *    cutqc_sample need their natural alignment.  Anything else is rejected
  *    with CUTQC_ERR_ARG before anything is launched.
@@ -246,6 +247,27 @@ CUTQC_API int cutqc_cut_search(const cutqc_gate* gates, int32_t n_gates, int32_t
 CUTQC_API int cutqc_attribute(const void* variant_probs, int32_t d, int32_t k_in, const int32_t* meas_qubit,
                               int32_t k_out, const int32_t* out_local, int32_t n_eff, int32_t dtype,
                               void* tensor, void* stream);
+
+/* The merged tensor one recursion of the dynamic definition (Sec. 4.3,
+ * Algorithm 1) contracts for one subcircuit, straight from its variants'
+ * measured distributions: [4^k_in][4^k_out][2^a] in `dtype`, a = the number
+ * of active outputs, kept in output order (output 0 most significant).
+ * Arguments as cutqc_attribute, plus role_out[n_eff] (host): the role of each
+ * output in the recursion, 0 active, 1 merged (summed out), 2 zoomed at 0,
+ * 3 zoomed at 1.  Merging sums over output qubits and fixes zoomed ones,
+ * while Eq. 3 and Eq. 2 act only on the measured cut qubits' outcomes and the
+ * init variants, so the library sums the variant distributions over the
+ * merged outputs first (one read of variant_probs) and attributes the merged
+ * distributions: the full 2^n_eff tensor is never formed.  Equals
+ * attributing, then merging, up to rounding.  Uses a per-device buffer of the
+ * library (the merged distributions, 4^k_in * 3^k_out * 2^(k_out + a)
+ * entries); calls that overlap on the GPU race on it.  When nothing is merged
+ * or zoomed this is cutqc_attribute.  Rejected with CUTQC_ERR_UNSUPPORTED
+ * when no measured cut qubit and no active output remains. */
+CUTQC_API int cutqc_attribute_merged(const void* variant_probs, int32_t d, int32_t k_in,
+                                     const int32_t* meas_qubit, int32_t k_out, const int32_t* out_local,
+                                     int32_t n_eff, const int8_t* role_out, int32_t dtype, void* tensor,
+                                     void* stream);
 
 /* Produce one subcircuit's attributed tensor on the GPU (Fig. 3, Eq. 2-3):
  * simulates, in complex FP64, every variant (each init slot in |0>, |1>,

@@ -1049,6 +1049,102 @@ int cutqc_attribute(const void* variant_probs, int32_t d, int32_t k_in, const in
   });
 }
 
+int cutqc_attribute_merged(const void* variant_probs, int32_t d, int32_t k_in, const int32_t* meas_qubit,
+                           int32_t k_out, const int32_t* out_local, int32_t n_eff, const int8_t* role_out,
+                           int32_t dtype, void* tensor, void* stream) {
+  return guarded([&] {
+    if (d < 1 || d > 30) fail(CUTQC_ERR_UNSUPPORTED, "attribution needs 1 <= d <= 30");
+    if (k_in < 0 || k_out < 0 || n_eff < 0 || k_in + k_out > kMaxCuts) fail(CUTQC_ERR_SHAPE, "bad slot counts");
+    if (k_out + n_eff != d) fail(CUTQC_ERR_SHAPE, "every local qubit must be an output or a measured cut qubit");
+    if (!variant_probs || !tensor || (k_out && !meas_qubit) || (n_eff && (!out_local || !role_out)))
+      fail(CUTQC_ERR_ARG, "NULL array");
+    if (dtype != CUTQC_F32 && dtype != CUTQC_F64) fail(CUTQC_ERR_ARG, "bad dtype");
+    const size_t es = dtype == CUTQC_F64 ? 8 : 4;
+    need_aligned(variant_probs, es, "variant_probs");
+    need_aligned(tensor, es, "tensor");
+    // role of each local qubit: 0 kept (a measured cut qubit or an active
+    // output), 1 merged, 2 / 3 zoomed at 0 / 1
+    std::vector<int> seen(d, 0), lrole(d, 0), mq(k_out);
+    for (int j = 0; j < k_out; ++j) {
+      if (meas_qubit[j] < 0 || meas_qubit[j] >= d || seen[meas_qubit[j]]++) fail(CUTQC_ERR_SHAPE, "bad measured qubit");
+      mq[j] = meas_qubit[j];
+    }
+    for (int i = 0; i < n_eff; ++i) {
+      if (out_local[i] < 0 || out_local[i] >= d || seen[out_local[i]]++) fail(CUTQC_ERR_SHAPE, "bad output qubit");
+      if (role_out[i] < 0 || role_out[i] > 3) fail(CUTQC_ERR_ARG, "role_out must be 0, 1, 2 or 3");
+      lrole[out_local[i]] = role_out[i];
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    std::vector<int> kept, oq;
+    int mg = 0;
+    bool zoomed = false;
+    for (int j = 0; j < d; ++j) {
+      if (lrole[j] == 0) kept.push_back(j);
+      if (lrole[j] == 1) ++mg;
+      if (lrole[j] >= 2) zoomed = true;
+    }
+    for (int i = 0; i < n_eff; ++i)
+      if (role_out[i] == 0) oq.push_back(out_local[i]);
+    if (mg == 0 && !zoomed) {   // nothing to merge: plain attribution
+      launch_attribute(variant_probs, dtype, d, k_in, mq.data(), k_out, oq.data(), n_eff, tensor, s);
+      return;
+    }
+    if (kept.empty()) fail(CUTQC_ERR_UNSUPPORTED, "no measured cut qubit or active output left to attribute");
+    // merge the variant distributions over the merged outputs, zoomed ones
+    // fixed, keeping the local qubits of `kept` in order (local qubit j is
+    // bit d-1-j of a distribution's index); Eq. 3 and Eq. 2 act only on the
+    // cut qubits and the init variants, so attributing the merged
+    // distributions gives the merged tensor (Algorithm 1) without forming
+    // the full one
+    std::vector<uint64_t> act_val, mrg_val;
+    uint64_t zoom = 0, mm = 0, am = 0;
+    for (int j = d - 1; j >= 0; --j) {   // least significant index bit first
+      const uint64_t xbit = uint64_t(1) << (d - 1 - j);
+      if (lrole[j] == 0) {
+        act_val.push_back(xbit);
+        am |= xbit;
+      } else if (lrole[j] == 1) {
+        mrg_val.push_back(xbit);
+        mm |= xbit;
+      } else if (lrole[j] == 3) {
+        zoom |= xbit;
+      }
+    }
+    const int a = (int)kept.size();
+    const bool run = mg > 0 && mm == ((uint64_t(1) << mg) - 1);
+    const bool dense = run && am == (((uint64_t(1) << a) - 1) << mg);
+    const size_t tab_act = (size_t)std::max((a + 7) / 8, 1) * 256, tab_mrg = (size_t)std::max((mg + 7) / 8, 1) * 256;
+    int64_t rows = 1;
+    for (int j = 0; j < k_in; ++j) rows *= 4;
+    for (int j = 0; j < k_out; ++j) rows *= 3;
+    const size_t nq = (size_t)rows << a;
+    size_t off = 0;
+    const size_t o_q = off;
+    off = align_up(off + nq * es);
+    const size_t o_mc = off;
+    off = align_up(off + nq * 4);
+    const size_t o_part = off;
+    if (run) off = align_up(off + ((size_t)rows << (a + dd_merge_chunks(rows, a, mg))) * 8);
+    const size_t o_act = off;
+    off = align_up(off + tab_act * 8);
+    const size_t o_mrg = off;
+    off = align_up(off + tab_mrg * 8);
+    DeviceState& ds = device_state();
+    char* w = aux_buffer(ds, off) + aux_distance_bytes();
+    launch_deposit_tables(act_val.data(), a, mrg_val.data(), mg, reinterpret_cast<uint64_t*>(w + o_act),
+                          reinterpret_cast<uint64_t*>(w + o_mrg), s);
+    launch_dd_merge(variant_probs, dtype, rows, d, a, mg, reinterpret_cast<const uint64_t*>(w + o_act),
+                    reinterpret_cast<const uint64_t*>(w + o_mrg), zoom, run, dense, w + o_q,
+                    reinterpret_cast<float*>(w + o_mc), w + o_part, s);
+    // the merged distributions' local qubits are `kept`, in order
+    std::vector<int> pos(d, -1);
+    for (int i = 0; i < a; ++i) pos[kept[i]] = i;
+    for (int& q : mq) q = pos[q];
+    for (int& q : oq) q = pos[q];
+    launch_attribute(w + o_q, dtype, a, k_in, mq.data(), k_out, oq.data(), (int)oq.size(), tensor, s);
+  });
+}
+
 int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates, int32_t d, const int32_t* init_qubit,
                               int32_t k_in, const int32_t* meas_qubit, int32_t k_out, const int32_t* out_local,
                               int32_t n_eff, int32_t dtype, void* tensor, void* stream) {

@@ -212,6 +212,10 @@ struct DdEvalArgs {
 };
 // log2 of the chunks each output's run is split into by the contiguous-run merge (0 = none)
 int dd_merge_chunks(int64_t rows, int a, int mg);
+// the deposit tables of up to 32 index bits each (bit i = the output value of
+// index bit i, least significant first), built on the device: no host copy
+void launch_deposit_tables(const uint64_t* act, int na, const uint64_t* mrg, int nm, uint64_t* tab_act,
+                           uint64_t* tab_mrg, cudaStream_t s);
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
                      const uint64_t* depMrg, uint64_t zoom, bool run, bool dense_bits, void* M, float* MC,
                      void* part, cudaStream_t s);

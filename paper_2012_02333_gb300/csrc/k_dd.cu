@@ -483,7 +483,43 @@ void launch_run(const float* T, int64_t cols, int a, int mg, const uint64_t* dep
                                                                  MC, part, n_out);
 }
 
+// deposit tables built on the device from up to 32 bit values each (passed
+// by value): table[b][v] = sum over set bits j of v of bits[8b + j]; a table
+// for n bits has max(ceil(n / 8), 1) rows of 256
+struct DepBits {
+  uint64_t v[32];
+  int n;
+};
+__global__ void k_deposit_tables(const DepBits A, const DepBits M, uint64_t* __restrict__ ta,
+                                 uint64_t* __restrict__ tm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // (table, byte, v)
+  const int nbA = max((A.n + 7) / 8, 1), nbM = max((M.n + 7) / 8, 1);
+  const bool first = t < nbA * 256;
+  const int i = first ? t : t - nbA * 256;
+  if (!first && i >= nbM * 256) return;
+  const int n = first ? A.n : M.n;
+  const int b = i >> 8, v = i & 255;
+  uint64_t g = 0;
+  for (int j = 0; j < 8; ++j)
+    if (((v >> j) & 1) && 8 * b + j < n) g += first ? A.v[8 * b + j] : M.v[8 * b + j];
+  (first ? ta : tm)[i] = g;
+}
+
 }  // namespace
+
+void launch_deposit_tables(const uint64_t* act, int na, const uint64_t* mrg, int nm, uint64_t* tab_act,
+                           uint64_t* tab_mrg, cudaStream_t s) {
+  if (na < 0 || na > 32 || nm < 0 || nm > 32) fail(CUTQC_ERR_UNSUPPORTED, "deposit tables take at most 32 bits");
+  DepBits A{}, M{};
+  for (int j = 0; j < na; ++j) A.v[j] = act[j];
+  for (int j = 0; j < nm; ++j) M.v[j] = mrg[j];
+  A.n = na;
+  M.n = nm;
+  const int total = (std::max((na + 7) / 8, 1) + std::max((nm + 7) / 8, 1)) * 256;
+  k_deposit_tables<<<(total + 255) / 256, 256, 0, s>>>(A, M, tab_act, tab_mrg);
+  count_launch();
+  check_launch("k_deposit_tables");
+}
 
 int dd_merge_chunks(int64_t rows, int a, int mg) {
   if (mg < 2) return 0;

@@ -85,13 +85,17 @@ _lib.cutqc_distance.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.
 _lib.cutqc_sample.argtypes = [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
 _lib.cutqc_attribute.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
                                  C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
+_lib.cutqc_attribute_merged.argtypes = [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_int32,
+                                        C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int8), C.c_int32,
+                                        C.c_void_p, C.c_void_p]
 _lib.cutqc_selftest_wait.argtypes = [C.c_int32, C.c_void_p]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
 for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
-           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute", "cutqc_distance", "cutqc_sample", "cutqc_cut_search"):
+           "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute",
+           "cutqc_attribute_merged", "cutqc_distance", "cutqc_sample", "cutqc_cut_search"):
     getattr(_lib, _f).restype = C.c_int
 
 
@@ -405,6 +409,32 @@ def cutqc_attribute(sub: circuits.Subcircuit, variant_probs: torch.Tensor, out: 
     _check(_lib.cutqc_attribute(
         C.c_void_p(variant_probs.data_ptr()), sub.d, sub.k_in, _i32([q for q, _ in sub.out_slots]), sub.k_out,
         _i32([q for q, _ in sub.outputs]), sub.n_eff,
+        CUTQC_F64 if variant_probs.dtype == torch.float64 else CUTQC_F32, C.c_void_p(out.data_ptr()),
+        s.cuda_stream))
+    return out
+
+
+def cutqc_attribute_merged(sub: circuits.Subcircuit, variant_probs: torch.Tensor, roles: Sequence[int],
+                           out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Binding of cutqc_attribute_merged: the merged tensor of one recursion of
+    the dynamic definition, [4^k_in * 4^k_out][2^a], straight from the
+    variants' output distributions.  roles[q] over global qubits: 0 active,
+    1 merged, 2 zoomed at 0, 3 zoomed at 1."""
+    n_in = (4 ** sub.k_in) * (3 ** sub.k_out) * (2 ** sub.d)
+    if not variant_probs.is_cuda or not variant_probs.is_contiguous() or variant_probs.numel() != n_in or \
+            variant_probs.dtype not in (torch.float32, torch.float64):
+        raise ValueError("variant_probs must be a contiguous CUDA float tensor of 4^k_in*3^k_out*2^d entries")
+    role_out = [int(roles[g]) for _, g in sub.outputs]
+    a = sum(1 for r in role_out if r == 0)
+    n_out = (4 ** sub.k_in) * (4 ** sub.k_out) * (2 ** a)
+    if out is None:
+        out = torch.empty(n_out, dtype=variant_probs.dtype, device=variant_probs.device)
+    elif out.numel() != n_out or out.dtype != variant_probs.dtype or not out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CUDA tensor of 4^k_in*4^k_out*2^a entries")
+    s = stream or torch.cuda.current_stream(variant_probs.device)
+    _check(_lib.cutqc_attribute_merged(
+        C.c_void_p(variant_probs.data_ptr()), sub.d, sub.k_in, _i32([q for q, _ in sub.out_slots]), sub.k_out,
+        _i32([q for q, _ in sub.outputs]), sub.n_eff, (C.c_int8 * max(1, len(role_out)))(*role_out),
         CUTQC_F64 if variant_probs.dtype == torch.float64 else CUTQC_F32, C.c_void_p(out.data_ptr()),
         s.cuda_stream))
     return out

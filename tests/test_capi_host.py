@@ -169,3 +169,23 @@ def test_misaligned_pointers_are_rejected(capi):
     assert f.cutqc_distance(a, b, 8, capi.CUTQC_F32, C.c_void_p(0x2004), b, None) == ARG
     assert f.cutqc_sample(a, 8, capi.CUTQC_F32, C.c_void_p(0x2004), 4, b, None) == ARG
     assert f.cutqc_sample(a, 8, capi.CUTQC_F32, a, 4, C.c_void_p(0x3002), None) == ARG
+
+
+def test_attribute_merged_argument_errors(capi):
+    p, t = C.c_void_p(0x2000), C.c_void_p(0x3000)
+    i32, f = capi._i32, capi._lib
+    roles = lambda r: (C.c_int8 * len(r))(*r)
+    # 3 local qubits: one measured cut qubit (2) and two outputs (0, 1)
+    base = [p, 3, 1, i32([2]), 1, i32([0, 1]), 2, roles([0, 1]), capi.CUTQC_F32, t, None]
+    for idx, val, status in [
+        (7, roles([0, 4]), capi.CUTQC_ERR_ARG),             # role out of range
+        (7, None, capi.CUTQC_ERR_ARG),                      # no roles for the outputs
+        (5, i32([0, 2]), capi.CUTQC_ERR_SHAPE),             # an output on the measured qubit
+        (1, 31, capi.CUTQC_ERR_UNSUPPORTED),                # d > 30
+    ]:
+        args = list(base)
+        args[idx] = val
+        assert f.cutqc_attribute_merged(*args) == status, (idx, capi.last_error())
+    # nothing left to attribute: no measured cut qubit, every output merged or zoomed
+    st = f.cutqc_attribute_merged(p, 2, 1, None, 0, i32([0, 1]), 2, roles([1, 3]), capi.CUTQC_F32, t, None)
+    assert st == capi.CUTQC_ERR_UNSUPPORTED and "left to attribute" in capi.last_error()

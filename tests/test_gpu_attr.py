@@ -133,3 +133,85 @@ def test_attribute_benchmark_size(env):
         got = cutqc.cutqc_attribute(sub, torch.tensor(p.reshape(-1), device="cuda"))
         want = at.attribute(sub, p.astype(np.float64).reshape(4 ** sub.k_in, 3 ** sub.k_out, 2 ** sub.d))
         assert np.abs(got.double().cpu().numpy() - want.reshape(-1)).max() <= 1e-6
+
+
+# ---- merged tensors of a dynamic-definition recursion from the variants ----
+
+def _synthetic_sub(d, k_in, k_out):
+    """A subcircuit whose measured cut qubits are its first local qubits and
+    whose outputs are the rest, global qubit = local qubit: the roles below
+    then put the merged outputs exactly where each merge form needs them."""
+    from paper_2012_02333_gb300 import circuits as C
+    return C.Subcircuit(d=d, gates=[], in_slots=[(j, j) for j in range(k_in)],
+                        out_slots=[(j, j) for j in range(k_out)], outputs=[(lq, lq) for lq in range(k_out, d)])
+
+
+# roles of outputs 2..11 of a 12-qubit subcircuit with 2 measured cut qubits
+MERGE_FORMS = {
+    "run_dense": [0] * 6 + [1] * 4,            # merged = the lowest 4 index bits, kept bits right above
+    "run_zoomed": [0, 0, 3, 0, 2, 0, 1, 1, 1, 1],
+    "warp": [0, 1, 1, 1, 0, 1, 1, 1, 0, 0],    # 6 merged values, not on the lowest bits
+    "thread": [0, 1, 0, 0, 2, 0, 1, 0, 0, 0],  # 2 merged values
+    "zoom_only": [0, 3, 0, 2, 0, 0, 3, 0, 0, 0],
+    "all_active": [0] * 10,
+}
+
+
+@pytest.mark.parametrize("form", list(MERGE_FORMS))
+def test_attribute_merged_forms(env, form):
+    """Every merge form (contiguous runs, warp and thread per output, zoom
+    only, nothing merged) against the oracle's attribute-then-merge, FP64 and
+    FP32, on seeded random variant distributions."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    sub = _synthetic_sub(12, 2, 2)
+    roles = [0, 0] + MERGE_FORMS[form]
+    rng = np.random.default_rng(31)
+    V = (4 ** sub.k_in) * (3 ** sub.k_out)
+    p = rng.random((V, 2 ** sub.d))
+    p /= p.sum(axis=1, keepdims=True)
+    want = at.attribute_merged(sub, p, roles).reshape(-1)
+    got = cutqc.cutqc_attribute_merged(sub, torch.tensor(p.reshape(-1), device="cuda"), roles)
+    assert got.numel() == want.size
+    assert np.abs(got.cpu().numpy() - want).max() <= 1e-12
+    p32 = p.astype(np.float32)
+    want32 = at.attribute_merged(sub, p32.astype(np.float64), roles).reshape(-1)
+    got32 = cutqc.cutqc_attribute_merged(sub, torch.tensor(p32.reshape(-1), device="cuda"), roles)
+    assert np.abs(got32.double().cpu().numpy() - want32).max() <= 1e-6
+
+
+@pytest.mark.parametrize("name", ["qaoa8_k4", "grid4x5_k5", "hwea10_k1", "aqft8_k4"])
+def test_attribute_merged_simulated_variants(env, name):
+    """Physical variant distributions of the test circuits, roles cycling
+    through active / merged / zoomed over the global qubits."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    cc = cases.SMALL[name]()
+    for pattern in [(0, 1, 2, 3), (1, 0, 1, 3, 0), (1, 1, 0)]:
+        roles = [pattern[q % len(pattern)] for q in range(cc.n)]
+        for sub in cc.subs:
+            if sub.k_out == 0 and not any(roles[g] == 0 for _, g in sub.outputs):
+                continue   # nothing left to attribute (rejected, see the host tests)
+            p = at.variant_probabilities(sub)
+            want = at.attribute_merged(sub, p, roles).reshape(-1)
+            got = cutqc.cutqc_attribute_merged(sub, torch.tensor(p.reshape(-1), dtype=torch.float64,
+                                                                 device="cuda"), roles)
+            assert np.abs(got.cpu().numpy() - want).max() <= 1e-12, (pattern, sub.d)
+
+
+def test_attribute_merged_benchmark_size(env):
+    """Both QAOA-30 subcircuits (17 qubits, 2 + 2 slots) with the roles of a
+    first recursion of 20 active qubits, FP32 synthetic variant distributions,
+    every entry against the oracle."""
+    torch, cutqc = env
+    from oracle import attribution as at
+    from paper_2012_02333_gb300 import circuits as C
+    cc = C.qaoa_2cluster(15, 0)
+    roles = [0 if q < 20 else 1 for q in range(cc.n)]
+    rng = np.random.default_rng(23)
+    for sub in cc.subs:
+        p = rng.random(((4 ** sub.k_in) * (3 ** sub.k_out), 2 ** sub.d)).astype(np.float32)
+        p /= p.sum(axis=1, keepdims=True)
+        got = cutqc.cutqc_attribute_merged(sub, torch.tensor(p.reshape(-1), device="cuda"), roles)
+        want = at.attribute_merged(sub, p.astype(np.float64), roles)
+        assert np.abs(got.double().cpu().numpy() - want.reshape(-1)).max() <= 1e-6
