@@ -69,8 +69,9 @@ __device__ __forceinline__ void store_merged(float* out, float* outc, int64_t o,
 }
 __device__ __forceinline__ void store_merged(double* out, float*, int64_t o, double v) { out[o] = v; }
 
-// Generic merge: a warp owns an output when there are >= 32 merged values;
-// lanes stride the merged index and sum runs of 16 in the tensor's type.
+// Generic merge: a warp owns an output when there are >= 32 merged values
+// (mg >= 5); lanes stride the merged index and sum runs of 16 in the
+// tensor's type.
 template <typename T>
 __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, int mg,
                                 const uint64_t* __restrict__ depAct, int nbA, const uint64_t* __restrict__ depMrg,
@@ -84,14 +85,17 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
   for (int64_t o = warp; o < n_out; o += nwarps) {
     const int64_t row = o >> a;
     const uint64_t xa = (uint64_t)o & ((uint64_t(1) << a) - 1);
-    const T* base = Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom);
+    // the deposit is additive over disjoint index bits: the lane's part
+    // (merged-index bits 0-4) once, the rest once per step and the same for
+    // every lane (one broadcast load instead of a table lookup per value)
+    const T* base = Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom) + dep_tab(depMrg, nbM, (uint64_t)lane);
     Acc acc{};
-    for (int64_t x0 = lane; x0 < nm; x0 += 32 * 16) {
+    for (int64_t x0 = 0; x0 < nm; x0 += 32 * 16) {
       T run = T(0);
 #pragma unroll 4
       for (int r = 0; r < 16; ++r) {
-        const int64_t xm = x0 + 32 * r;
-        if (xm < nm) run += base[dep_tab(depMrg, nbM, (uint64_t)xm)];
+        const int64_t xh = x0 + 32 * r;   // nm is a multiple of 32 (mg >= 5)
+        if (xh < nm) run += base[dep_tab(depMrg, nbM, (uint64_t)xh)];
       }
       if constexpr (sizeof(T) == 4)
         acc = ff_add(acc, FF{run, 0.0f});
