@@ -253,7 +253,11 @@ __global__ void k_attr_outcomes(const T* __restrict__ P, const AttrArgs a, T* __
 // rows b that mb serves (a Z-basis slot serves I, unsigned, and Z, signed;
 // X and Y serve themselves), 4 consecutive x per 16-byte store.  P is read
 // exactly once.  The butterfly's adds are pairwise over at most 16 values.
-template <typename T, int KOUT>
+// CONTIG (FP32, k_out <= 2, aligned): the measured cut qubits are the lowest
+// local bits, in any order, and x bits 0-1 sit right above them, so a
+// thread's 4 * 2^KOUT values are contiguous: 2^KOUT 16-byte loads, each value
+// then picked by its measured-bit offset (a select over 2^KOUT registers).
+template <typename T, int KOUT, bool CONTIG>
 __global__ void k_attr_variants(const T* __restrict__ P, const AttrArgs a, T* __restrict__ Q, int64_t n_grp,
                                 int snap) {
   __shared__ uint64_t tab_x[4][256];
@@ -275,10 +279,36 @@ __global__ void k_attr_variants(const T* __restrict__ P, const AttrArgs a, T* __
     const uint64_t yx = tab_x[0][x & 255] | tab_x[1][(x >> 8) & 255] | tab_x[2][(x >> 16) & 255] | tab_x[3][x >> 24];
     const T* base = P + ((int64_t)rest << a.d) + yx;
     T v[NM][4];
+    if constexpr (CONTIG) {
+      // entry e of the 4 * NM contiguous values is measured offset e % NM
+      // (dm[m] for outcome m) of output x + e / NM
+      T w[4 * NM];
+      const float4* b4 = reinterpret_cast<const float4*>(base);
 #pragma unroll
-    for (int m = 0; m < NM; ++m)
+      for (int j = 0; j < NM; ++j) {
+        const float4 q = __ldg(b4 + j);
+        w[4 * j] = q.x;
+        w[4 * j + 1] = q.y;
+        w[4 * j + 2] = q.z;
+        w[4 * j + 3] = q.w;
+      }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) v[m][k] = __ldg(base + dm[m] + dlow[k]);
+      for (int m = 0; m < NM; ++m) {
+        const int o = (int)dm[m];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          T r = w[NM * k];
+#pragma unroll
+          for (int t = 1; t < NM; ++t) r = o == t ? w[NM * k + t] : r;
+          v[m][k] = r;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < NM; ++m)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[m][k] = __ldg(base + dm[m] + dlow[k]);
+    }
     // butterfly over slot j (m bit j): (u, w) -> (u + w, u - w); afterwards
     // v[p] = sum_m (-1)^{popc(m & p)} v_in[m]
 #pragma unroll
@@ -377,12 +407,27 @@ void launch_two_pass(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
   const bool aligned = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
   if (a.n_eff >= 2 && a.k_out <= 4 && aligned) {
     const int64_t n_grp = (((int64_t(1) << (2 * a.k_in)) * a.pow3_kout) << a.n_eff) / 4;
-    switch (a.k_out) {
-      case 0: k_attr_variants<T, 0><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-      case 1: k_attr_variants<T, 1><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-      case 2: k_attr_variants<T, 2><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-      case 3: k_attr_variants<T, 3><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-      default: k_attr_variants<T, 4><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+    // measured cut qubits on y bits 0 .. k_out-1 (any order), x bits 0-1 right above
+    bool contig = sizeof(T) == 4 && a.k_out <= 2 && (reinterpret_cast<uintptr_t>(P) & 15) == 0 &&
+                  a.out_pos[a.n_eff - 1] == a.k_out && a.out_pos[a.n_eff - 2] == a.k_out + 1;
+    for (int j = 0; j < a.k_out; ++j) contig = contig && a.meas_pos[j] < a.k_out;
+    if constexpr (sizeof(T) == 4) {
+      if (contig) {
+        switch (a.k_out) {
+          case 0: k_attr_variants<T, 0, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+          case 1: k_attr_variants<T, 1, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+          default: k_attr_variants<T, 2, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+        }
+      }
+    }
+    if (!contig) {
+      switch (a.k_out) {
+        case 0: k_attr_variants<T, 0, false><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+        case 1: k_attr_variants<T, 1, false><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+        case 2: k_attr_variants<T, 2, false><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+        case 3: k_attr_variants<T, 3, false><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+        default: k_attr_variants<T, 4, false><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+      }
     }
   } else if (a.n_eff >= 2) {
     // x bits 0 and 1 on y bits 0 and 1: four consecutive x are four consecutive y

@@ -92,8 +92,8 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
     Acc acc{};
     for (int64_t x0 = 0; x0 < nm; x0 += 32 * 16) {
       T run = T(0);
-#pragma unroll 4
-      for (int r = 0; r < 16; ++r) {
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {   // 16 independent loads in flight per lane
         const int64_t xh = x0 + 32 * r;   // nm is a multiple of 32 (mg >= 5)
         if (xh < nm) run += base[dep_tab(depMrg, nbM, (uint64_t)xh)];
       }
