@@ -45,8 +45,9 @@ __global__ void k_sim_init(double2* __restrict__ psi, SimArgs a, int s0, int nb)
   const int64_t tot = dim * nb;
   const double r = 0.70710678118654752440;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int s = s0 + (int)(t / dim);
-    const int64_t y = t % dim;
+    // every extent here is a power of two: shifts and masks, no 64-bit division
+    const int s = s0 + (int)(t >> a.d);
+    const int64_t y = t & (dim - 1);
     int64_t init_mask = 0;
     double2 amp = make_double2(1.0, 0.0);
     for (int j = 0; j < a.k_in; ++j) {
@@ -72,7 +73,7 @@ __global__ void k_gate1(double2* __restrict__ psi, int d, int nb, int bit, doubl
   const int64_t tot = half * nb;
   const int64_t lo = (int64_t(1) << bit) - 1;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = t / half, i = t % half;
+    const int64_t v = t >> (d - 1), i = t & (half - 1);
     const int64_t i0 = ((i & ~lo) << 1) | (i & lo);
     const int64_t i1 = i0 | (int64_t(1) << bit);
     double2* p = psi + (v << d);
@@ -92,8 +93,8 @@ __global__ void k_gate2(double2* __restrict__ psi, int d, int nb, int b0, int b1
   const int64_t tot = quarter * nb;
   const int lo_b = b0 < b1 ? b0 : b1, hi_b = b0 < b1 ? b1 : b0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = t / quarter;
-    int64_t i = t % quarter;
+    const int64_t v = t >> (d - 2);
+    int64_t i = t & (quarter - 1);
     // insert zero bits at lo_b then hi_b
     int64_t m = (int64_t(1) << lo_b) - 1;
     i = ((i & ~m) << 1) | (i & m);
@@ -133,8 +134,8 @@ __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, 
     if (basis[j] == 0) zmask |= 1 << j;
   }
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int sl = (int)(t / nx);
-    const int64_t x = t % nx;
+    const int sl = (int)(t >> a.n_eff);
+    const int64_t x = t & (nx - 1);
     int64_t ybase = 0;
     for (int i = 0; i < a.n_eff; ++i)
       if ((x >> (a.n_eff - 1 - i)) & 1) ybase |= int64_t(1) << a.out_bit[i];
@@ -170,11 +171,12 @@ __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, 
 // variants (|0>, |1>, |+>, |+i>) become the 4 Pauli operators (I, X, Y, Z).
 __global__ void k_attr_init(double* __restrict__ P, int k_in, int j, int64_t inner) {
   // inner = 4^k_out * 2^n_eff; index = ((hi * 4 + digit) * stride + lo)
-  const int64_t stride = (int64_t(1) << (2 * (k_in - 1 - j))) * inner;
+  const int64_t stride = (int64_t(1) << (2 * (k_in - 1 - j))) * inner;   // a power of two
+  const int ls = __ffsll((long long)stride) - 1;
   const int64_t hi_n = int64_t(1) << (2 * j);
   const int64_t tot = hi_n * stride;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t hi = t / stride, lo = t % stride;
+    const int64_t hi = t >> ls, lo = t & (stride - 1);
     double* base = P + hi * 4 * stride + lo;
     const double p0 = base[0], p1 = base[stride], pp = base[2 * stride], pi = base[3 * stride];
     base[0] = p0 + p1;                     // I
