@@ -149,7 +149,21 @@ def test_supremacy_4x6_full_size_sampled(env, sup, algo):
     out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
     got = out.double().cpu().numpy()
     rng = np.random.default_rng(11)
-    xs = sorted(set(int(x) for x in rng.integers(0, 2 ** cc.n, 4096)) | {0, 2 ** cc.n - 1})
+    xs = set(int(x) for x in rng.integers(0, 2 ** cc.n, 4096)) | {0, 2 ** cc.n - 1}
+    # plus 1024 outputs in the last two 256-column tile columns of either side
+    # (whichever subcircuit the contraction puts on N): on this shape the
+    # tensor-core contraction's last round of tiles (columns 3584-4095) is cut
+    # into 128-column halves over more CTAs
+    for sub in cc.subs:
+        qs = sub.out_qubit
+        for _ in range(512):
+            n = int(rng.integers(14 * 256, 2 ** len(qs)))
+            x = int(rng.integers(0, 2 ** cc.n))
+            for i, q in enumerate(qs):   # output i of the subcircuit is bit i of n (output 0 most significant)
+                bit = (n >> (len(qs) - 1 - i)) & 1
+                x = (x & ~(1 << (cc.n - 1 - q))) | (bit << (cc.n - 1 - q))
+            xs.add(x)
+    xs = sorted(xs)
     want = rc.fd_entries(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts, xs)
     err = np.abs(got[xs] - want).max()
     assert err <= TOL32, f"max abs err {err:.3e}"
