@@ -428,8 +428,17 @@ def run_other(args):
         outs = [torch.empty(2 ** cc.n, device=dev) for cc in batch]
         sums = torch.empty(len(batch), dtype=torch.float64, device=dev)
         ms = timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "auto", sums))
+        # HBM roofline of the batch: every output written once, every
+        # subcircuit tensor read once (group builds and operand pieces stay in L2
+        # or are counted as overhead)
+        bytes_alg = sum(o.numel() * 4 for o in outs) + sum(t.numel() * 4 for ts in tss for t in ts)
+        pk, pk_src = peaks()
+        gbs = bytes_alg / (ms / 1e3) / 1e9
         extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "cc", sums)),
-                 "cc_only": "every instance on the FP32 CUDA-core form, same graph replay"}
+                 "cc_only": "every instance on the FP32 CUDA-core form, same graph replay",
+                 "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                              "frac": gbs / pk["hbm_gbs"], "traffic": None, "algorithmic_bytes": bytes_alg,
+                              "peak_file": pk_src}}
         units, unit, dtype = sum(2 ** cc.n for cc in batch), "probs/s", "f32 (per instance cc or bf16x3/x6)"
         cfg = {"workload": "batch64_hwea_aqft_bv_fd_fp32", "instances": len(batch),
                "n_qubits": [cc.n for cc in batch], "n_cuts": [cc.n_cuts for cc in batch],
