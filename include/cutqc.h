@@ -178,8 +178,13 @@ CUTQC_API int cutqc_reconstruct_backward(const cutqc_problem* problem,
  * device and stall other streams.  It computes what cutqc_reconstruct_fd
  * computes with CUTQC_CC (CUDA-core contraction in the tensors' dtype, early
  * termination, FP64 sum) for a problem of exactly two subcircuits, writing
- * out (device, 2^n_qubits entries) and, if sum_p is not NULL, the FP64 sum to
- * sum_p (device double).  All of its scratch lives in one 4 MiB array in
+ * out (2^n_qubits entries: device memory of the current device, or pinned
+ * host memory mapped for the device, as for cutqc_reconstruct_fd) and, if
+ * sum_p is not NULL, the FP64 sum to sum_p (device double on the current
+ * device); other pointers are rejected with CUTQC_ERR_ARG before anything
+ * runs.  The plan's tables are written on the device by a kernel from its
+ * launch parameters: no host buffer is read after the call returns and no
+ * host-to-device copy is made.  All of its scratch lives in one 4 MiB array in
  * device global memory that the library declares statically; every GPU that
  * loads the library holds it until the process exits.  Problems that need
  * more scratch (roughly K > 8 cuts) are rejected with CUTQC_ERR_UNSUPPORTED

@@ -701,6 +701,22 @@ static bool is_host_memory(const void* p) {
   return at.type == cudaMemoryTypeHost;
 }
 
+void* resolve_device_out(void* p, bool* host) {
+  *host = is_host_memory(p);
+  return resolve_out(p);
+}
+
+bool is_device_memory_here(const void* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = 0;
+  CUTQC_CUDA(cudaGetDevice(&dev));
+  return (at.type == cudaMemoryTypeDevice && at.device == dev) || at.type == cudaMemoryTypeManaged;
+}
+
 static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
                       cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr,

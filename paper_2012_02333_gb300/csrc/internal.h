@@ -63,6 +63,13 @@ struct PairPlanHost {
   std::vector<uint64_t> depA, depB; // [ceil(f/8)][256]
 };
 void plan_pair_host(const cutqc_problem* p, PairPlanHost& out);
+// The device address a kernel writes a full-definition output through: `p`
+// itself for device or managed memory of the current device, the device
+// alias for pinned host memory mapped for the device (*host = true); any
+// other pointer is rejected with CUTQC_ERR_ARG.
+void* resolve_device_out(void* p, bool* host);
+// true for device memory of the current device and for managed memory
+bool is_device_memory_here(const void* p);
 void check_launch(const char* what);
 
 // Device status word values (written by kernels, read at sync points).

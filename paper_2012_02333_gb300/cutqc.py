@@ -305,12 +305,15 @@ def cutqc_reconstruct_fd_noalloc(problem: Problem, out: torch.Tensor, sum_p: Opt
     """Binding of cutqc_reconstruct_fd_noalloc: the two-subcircuit CUDA-core
     full definition with its scratch in the library's static device array (for
     callers that cannot let the library allocate device memory)."""
-    if out.dtype != problem.dtype or out.numel() != 2 ** problem.n_qubits or not out.is_cuda:
-        raise ValueError("out must be a CUDA tensor of 2^n entries in the tensors' dtype")
+    here = torch.device("cuda", torch.cuda.current_device())
+    if out.dtype != problem.dtype or out.numel() != 2 ** problem.n_qubits or not out.is_contiguous() or \
+            not ((out.is_cuda and out.device == here) or out.is_pinned()):
+        raise ValueError("out must be a contiguous tensor of 2^n entries in the tensors' dtype, on the current "
+                         "CUDA device or in pinned host memory")
     sp = None
     if sum_p is not None:
-        if sum_p.dtype != torch.float64 or not sum_p.is_cuda:
-            raise ValueError("sum_p must be a CUDA float64 tensor")
+        if sum_p.dtype != torch.float64 or not sum_p.is_cuda or sum_p.device != here:
+            raise ValueError("sum_p must be a float64 tensor on the current CUDA device")
         sp = sum_p.data_ptr()
     _check(_lib.cutqc_reconstruct_fd_noalloc(C.byref(problem.c), C.c_void_p(out.data_ptr()), sp,
                                              _stream_ptr(stream)))

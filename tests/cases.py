@@ -38,3 +38,26 @@ def dd_twin():
 def hwea26_chain():
     """26-qubit HWEA cut once between qubits 12 and 13: 2^13 x 2^13 outputs."""
     return C.chain_blocks(C.hwea(26, 7), 2)
+
+
+def k8_pair():
+    """A 6-qubit circuit whose middle wires cross between two 3-qubit halves
+    nine times: two subcircuits (8 and 6 qubits) joined by K = 8 cuts, so
+    4^8 = 65536 Kronecker terms over 2^6 outputs."""
+    c = C.Circuit(6, [], "k8")
+    for q in range(6):
+        c.add("h", q)
+    for layer in range(4):
+        for q in range(6):
+            c.add("ry", q, params=[0.3 + 0.1 * q + 0.2 * layer])
+        c.add("cz", 2, 3)
+        c.add("rz", 3, params=[0.7 + 0.1 * layer])
+        c.add("cx", 3, 4)
+        c.add("cz", 0, 1)
+        c.add("cx", 1, 2)
+        c.add("cz", 4, 5)
+    c.add("ry", 3, params=[0.4])
+    c.add("cz", 2, 3)
+    cc = C.cut_circuit(c, [0, 0, 0, 1, 1, 1], policy="first")
+    assert cc.n_cuts == 8 and len(cc.subs) == 2
+    return cc

@@ -2,18 +2,29 @@
 let the library call cudaMalloc: device memory reserved up front by another
 allocator, or no device allocation allowed after start-up).
 
-It must give what cutqc_reconstruct_fd gives with the CUDA-core form, within
-the tolerances of the other parity tests (1e-6 for FP32, 1e-12 for FP64), on
-two calls in a row that share its static scratch array - different problems,
-so the second call cannot lean on what the first left behind.  This file is
-collected last so that a run stopping at the first failure has already run
-every other test; it also passes alone in a fresh process."""
+Its outputs are compared with the FP64 oracle's plain sum on the same tensors
+(oracle-simulated, rounded to FP32 for the FP32 cases), within the tolerances
+of the other parity tests (1e-6 for FP32, 1e-12 for FP64), on two calls in a
+row that share its static scratch array - different problems and dtypes, so
+the second call cannot lean on what the first left behind - including a
+K = 8 problem near the array's limit.  The same calls also run in a fresh
+process that never touches the library's allocating entry points, where the
+device's free memory must not change across them.  This file is collected
+last so that a run stopping at the first failure has already run every other
+test; it also passes alone in a fresh process."""
 import os
+import subprocess
+import sys
 
 import numpy as np
 import pytest
 
+sys.path.insert(0, os.path.dirname(__file__))
+import cases  # noqa: E402
+
 pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -21,40 +32,94 @@ def env():
     import torch
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    if not os.path.exists(os.path.join(root, "paper_2012_02333_gb300", "libcutqc.so")):
+    if not os.path.exists(os.path.join(ROOT, "paper_2012_02333_gb300", "libcutqc.so")):
         from paper_2012_02333_gb300 import build
         build.build()
     from paper_2012_02333_gb300 import cutqc
     return torch, cutqc
 
 
-def _case(cutqc, torch, make, dtype):
-    cc = make()
-    ts = cutqc.simulate_tensors(cc, dtype, torch.device("cuda"))
-    return cc, ts
+# (case, dtype name, tolerance): the K = 8 pair needs 2.3 MB of the 4 MiB scratch
+RUNS = [("k8_pair", "float32", 1e-6), ("qaoa8_k4", "float64", 1e-12), ("grid4x5_k5", "float32", 1e-6)]
 
 
-def test_noalloc_matches_fd_on_two_calls_in_a_row(env):
+def _make(name):
+    return cases.k8_pair() if name == "k8_pair" else cases.SMALL[name]()
+
+
+def _oracle(name, dtype_name):
+    """(cut circuit, tensors in the call's dtype, the oracle's FP64 result on them)."""
+    from oracle import attribution as at
+    from oracle import reconstruct as rc
+    cc = _make(name)
+    T = [t.astype(np.float32 if dtype_name == "float32" else np.float64) for t in at.tensors(cc)]
+    ref = rc.fd_full(cc.subs, [t.astype(np.float64) for t in T], cc.n, cc.n_cuts)
+    return cc, T, ref
+
+
+def test_noalloc_matches_oracle_on_calls_in_a_row(env):
     torch, cutqc = env
-    from paper_2012_02333_gb300 import circuits as C
-    runs = [
-        (lambda: C.supremacy_4x6(0), torch.float32, 1e-6),     # the benchmark workload, K = 4
-        (lambda: C.qaoa_2cluster(6, 1), torch.float64, 1e-12),  # a different shape and dtype, K = 4
-    ]
-    for make, dtype, tol in runs:
-        cc, ts = _case(cutqc, torch, make, dtype)
-        problem = cutqc.Problem.from_cut(cc, ts)
-        ref = torch.empty(2 ** cc.n, dtype=dtype, device="cuda")
-        ref_sum = torch.empty(1, dtype=torch.float64, device="cuda")
-        cutqc.cutqc_reconstruct_fd([problem], [ref], "cc", ref_sum)
-        got = torch.full((2 ** cc.n,), float("nan"), dtype=dtype, device="cuda")
-        got_sum = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
-        cutqc.cutqc_reconstruct_fd_noalloc(problem, got, got_sum)
+    prepared = []
+    for name, dtn, tol in RUNS:
+        cc, T, ref = _oracle(name, dtn)
+        dt = getattr(torch, dtn)
+        ts = [torch.tensor(t.reshape(-1), dtype=dt, device="cuda") for t in T]
+        prepared.append((cutqc.Problem.from_cut(cc, ts), ts, dt, ref, tol, cc))
+    for _ in range(2):   # every problem twice, interleaved
+        for problem, ts, dt, ref, tol, cc in prepared:
+            got = torch.full((2 ** cc.n,), float("nan"), dtype=dt, device="cuda")
+            got_sum = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+            cutqc.cutqc_reconstruct_fd_noalloc(problem, got, got_sum)
+            torch.cuda.synchronize()
+            err = np.abs(got.double().cpu().numpy() - ref).max()
+            assert err <= tol, f"{cc.n} qubits, K={cc.n_cuts}: max abs error {err:.3e}"
+            assert abs(got_sum.item() - ref.sum()) <= max(tol, 1e-9)
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+sys.path.insert(0, {tests!r})
+import test_zz_no_alloc as t
+from paper_2012_02333_gb300 import cutqc
+prepared = []
+for name, dtn, tol in t.RUNS:
+    cc, T, ref = t._oracle(name, dtn)
+    dt = getattr(torch, dtn)
+    ts = [torch.tensor(x.reshape(-1), dtype=dt, device="cuda") for x in T]
+    out = torch.full((2 ** cc.n,), float("nan"), dtype=dt, device="cuda")
+    sp = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    prepared.append((cutqc.Problem.from_cut(cc, ts), ts, out, sp, ref, tol))
+torch.cuda.synchronize()
+free = [torch.cuda.mem_get_info()[0]]
+for rnd in range(2):
+    for problem, ts, out, sp, ref, tol in prepared:
+        cutqc.cutqc_reconstruct_fd_noalloc(problem, out, sp)
         torch.cuda.synchronize()
-        err = (got.double() - ref.double()).abs().max().item()
-        assert err <= tol, f"max abs difference {err:.3e}"
-        assert abs(got_sum.item() - ref_sum.item()) <= max(tol, 1e-9)
+        err = np.abs(out.cpu().double().numpy() - ref).max()   # no device allocation between the readings
+        assert err <= tol, ("round", rnd, err)
+        assert abs(sp.item() - ref.sum()) <= max(tol, 1e-9)
+    torch.cuda.synchronize()
+    free.append(torch.cuda.mem_get_info()[0])
+print("free bytes", free)
+# the second round allocates nothing at all; the first may only load the
+# library's code and static arrays (the library's own workspace would be
+# allocated there, and is at least 1 MiB: so code loading is bounded by what
+# an eager module load leaves, checked as equality under eager loading)
+assert free[2] == free[1], free
+assert free[1] == free[0], free
+print("NOALLOC_FRESH_OK")
+"""
+
+
+def test_noalloc_in_a_fresh_process_allocates_nothing(env):
+    code = _FRESH.format(root=ROOT, tests=os.path.dirname(os.path.abspath(__file__)))
+    e = dict(os.environ)
+    e["CUDA_MODULE_LOADING"] = "EAGER"   # the library's code is loaded with the context, not at a call
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=e, cwd=ROOT, timeout=600)
+    assert r.returncode == 0 and "NOALLOC_FRESH_OK" in r.stdout, r.stdout[-3000:] + r.stderr[-3000:]
 
 
 def test_noalloc_rejects_problems_beyond_its_scratch(env):
@@ -74,3 +139,28 @@ def test_noalloc_rejects_problems_beyond_its_scratch(env):
     st = cutqc._lib.cutqc_reconstruct_fd_noalloc(C.byref(prob), C.c_void_p(out.data_ptr()), None, None)
     assert st == cutqc.CUTQC_ERR_UNSUPPORTED
     assert "scratch" in cutqc.last_error()
+
+
+def test_noalloc_rejects_outputs_it_cannot_write(env):
+    """Pageable host memory as out, or a host pointer as sum_p, is refused with
+    CUTQC_ERR_ARG before anything is launched."""
+    torch, cutqc = env
+    import ctypes as C
+    from oracle import attribution as at
+    cc = cases.SMALL["hwea10_k1"]()
+    ts = [torch.tensor(t.reshape(-1), dtype=torch.float64, device="cuda") for t in at.tensors(cc)]
+    problem = cutqc.Problem.from_cut(cc, ts)
+    torch.cuda.synchronize()
+    n0 = cutqc.launch_count()
+    host_out = torch.zeros(2 ** cc.n, dtype=torch.float64)          # pageable
+    st = cutqc._lib.cutqc_reconstruct_fd_noalloc(C.byref(problem.c), C.c_void_p(host_out.data_ptr()), None, None)
+    assert st == cutqc.CUTQC_ERR_ARG
+    dev_out = torch.zeros(2 ** cc.n, dtype=torch.float64, device="cuda")
+    host_sum = torch.zeros(1, dtype=torch.float64)
+    st = cutqc._lib.cutqc_reconstruct_fd_noalloc(C.byref(problem.c), C.c_void_p(dev_out.data_ptr()),
+                                                 C.c_void_p(host_sum.data_ptr()), None)
+    assert st == cutqc.CUTQC_ERR_ARG
+    assert cutqc.launch_count() == n0
+    with pytest.raises(ValueError):   # a strided view of 2^n entries
+        cutqc.cutqc_reconstruct_fd_noalloc(problem, torch.zeros(2 * 2 ** cc.n, dtype=torch.float64,
+                                                                device="cuda")[::2])
