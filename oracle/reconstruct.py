@@ -162,20 +162,30 @@ def zoom_roles(parent_roles, bin_index: int, n_active: int) -> List[int]:
 
 
 def dd_run(subs, tensors, n_qubits: int, n_cuts: int, n_active: int,
-           recursions: int, strategy: str = "bfs"):
+           recursions: int, strategy: str = "bfs", follow=None, follow_tol: float = 0.0):
     """Algorithm 1.  Each recursion after the first zooms into one bin taken
     from the list of all bins so far: "bfs" takes the heaviest bin over all
     recursions that has not been zoomed yet and still has merged qubits; "dfs"
     takes the heaviest bin of the latest recursion.  Ties go to the earlier
     recursion, then the lower bin index.  Returns a list of dicts with the
-    roles, the bins and the (recursion, bin) that was zoomed into."""
+    roles, the bins and the (recursion, bin) that was zoomed into.
+
+    Near ties (the paper ranks bins but says nothing about values that differ
+    only by rounding): `follow` may list, per recursion, the (recursion, bin)
+    another implementation zoomed into.  Where that bin is eligible and its
+    value is within `follow_tol` of the heaviest eligible value, it is taken
+    instead and the recursion's dict says so ("followed": True), so a run can
+    keep comparing after a choice that rounding alone decided; any other
+    choice is ignored."""
     out = []
     expanded = set()
     roles = initial_roles(n_qubits, n_active)
     parent = None
     for r in range(recursions):
+        followed = False
         if r > 0:
             best = None
+            eligible = {}
             cands = range(len(out)) if strategy == "bfs" else [len(out) - 1]
             for ri in cands:
                 rec = out[ri]
@@ -184,16 +194,58 @@ def dd_run(subs, tensors, n_qubits: int, n_cuts: int, n_active: int,
                 for bi, v in enumerate(rec["bins"]):
                     if (ri, bi) in expanded:
                         continue
+                    eligible[(ri, bi)] = v
                     if best is None or v > best[0]:
                         best = (v, ri, bi)
             if best is None:
                 break
             _, ri, bi = best
+            if follow is not None and r < len(follow) and follow[r] is not None:
+                want = tuple(follow[r])
+                if want != (ri, bi) and want in eligible and eligible[want] >= best[0] - follow_tol:
+                    ri, bi = want
+                    followed = True
             expanded.add((ri, bi))
             roles = zoom_roles(out[ri]["roles"], bi, n_active)
             parent = (ri, bi)
         bins = dd_bins(subs, tensors, n_qubits, n_cuts, roles)
-        out.append({"roles": roles, "bins": bins, "parent": parent})
+        out.append({"roles": roles, "bins": bins, "parent": parent, "followed": followed})
+    return out
+
+
+def dd_entries(subs, slab, n_qubits: int, n_cuts: int, roles, bins) -> np.ndarray:
+    """Selected bins of one DD recursion by the plain sum over merged tensors
+    (Algorithm 1), for sizes where neither the merged tensors nor the bins
+    can be formed whole.  slab(c, a) yields the entries of subcircuit c's
+    tensor whose active outputs read `a` (bits in output order, the first
+    active output most significant) and whose zoomed outputs read their fixed
+    bits: pieces (first row, array [rows of the piece][any number of the
+    merged outputs' entries]) covering every row and every merged entry once.
+    The merged value of a row is the sum over its merged entries; a bin is
+    2^-K sum_e prod_c (merged value of subcircuit c at row e|c and its active
+    bits of the bin).  Bin index as dd_bins."""
+    K = n_cuts
+    active = [q for q in range(n_qubits) if roles[q] == 0]
+    rank = {q: i for i, q in enumerate(active)}
+    na = len(active)
+    rows = np.array([[row_of(s, _digits(e, K)) for s in subs] for e in range(4 ** K)], dtype=np.int64)
+    merged = {}
+    out = np.empty(len(bins))
+    for i, b in enumerate(bins):
+        acc = np.ones(4 ** K)
+        for c, s in enumerate(subs):
+            a = 0
+            for q in s.out_qubit:
+                if roles[q] == 0:
+                    a = 2 * a + ((int(b) >> (na - 1 - rank[q])) & 1)
+            if (c, a) not in merged:
+                m = np.zeros(4 ** s.k_in * 4 ** s.k_out)
+                for r0, piece in slab(c, a):
+                    piece = np.asarray(piece)
+                    m[r0:r0 + piece.shape[0]] += piece.sum(axis=1, dtype=np.float64)
+                merged[(c, a)] = m
+            acc = acc * merged[(c, a)][rows[:, c]]
+        out[i] = acc.sum() * 2.0 ** -K
     return out
 
 

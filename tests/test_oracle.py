@@ -286,6 +286,78 @@ def test_dd_bins_are_brute_force_marginals(name, make):
             assert rec["bins"].sum() == pytest.approx(recs[ri]["bins"][bi], abs=1e-13)
 
 
+def _slab_of(cc, Ts, roles):
+    """slab(c, a) for dd_entries over host tensors: the entries of subcircuit
+    c's rows whose active outputs read `a` and zoomed outputs their fixed
+    bits, handed over in two row pieces, each split into two column pieces
+    in reverse column order (the oracle must not depend on how they come)."""
+    def slab(c, a):
+        s = cc.subs[c]
+        T = Ts[c].reshape(4 ** s.k_in * 4 ** s.k_out, -1)
+        act = [i for i, q in enumerate(s.out_qubit) if roles[q] == 0]
+        cols = []
+        for x in range(2 ** s.n_eff):
+            ok = True
+            for i, q in enumerate(s.out_qubit):
+                bit = (x >> (s.n_eff - 1 - i)) & 1
+                r = roles[q]
+                if (r == 2 and bit) or (r == 3 and not bit):
+                    ok = False
+                elif r == 0 and bit != (a >> (len(act) - 1 - act.index(i))) & 1:
+                    ok = False
+            if ok:
+                cols.append(x)
+        cols = cols[::-1]
+        h, w = T.shape[0] // 2, len(cols) // 2
+        for r0, r1 in ((0, h), (h, T.shape[0])):
+            for part in (cols[:w], cols[w:]):
+                yield r0, T[r0:r1][:, part] if part else np.zeros((r1 - r0, 0))
+    return slab
+
+
+@pytest.mark.parametrize("name,make", CASES[1:5], ids=[c[0] for c in CASES[1:5]])
+def test_dd_entries_are_brute_force_marginals(name, make):
+    """Selected bins from merged slabs (the form used where the merged tensors
+    cannot be formed whole) equal the uncut circuit's marginals, for every bin
+    of several recursions."""
+    cc = make()
+    Ts = at.tensors(cc)
+    ref = sv.probabilities(cc.circuit).reshape([2] * cc.n)
+    recs = rc.dd_run(cc.subs, Ts, cc.n, cc.n_cuts, 3, 4, "bfs")
+    for rec in recs:
+        roles = rec["roles"]
+        idx = tuple(0 if r == 2 else 1 if r == 3 else slice(None) for r in roles)
+        sub = ref[idx]
+        kept = [r for r in roles if r in (0, 1)]
+        merged_axes = tuple(i for i, r in enumerate(kept) if r == 1)
+        want = sub.sum(axis=merged_axes).reshape(-1) if merged_axes else sub.reshape(-1)
+        bins = list(range(len(want)))
+        got = rc.dd_entries(cc.subs, _slab_of(cc, Ts, roles), cc.n, cc.n_cuts, roles, bins)
+        assert np.allclose(got, want, atol=1e-13)
+
+
+def test_dd_run_follows_only_near_ties():
+    """The follow option of dd_run takes another run's zoom choice only when
+    that bin is eligible and within the given distance of the heaviest one."""
+    cc = CASES[2][1]()
+    Ts = at.tensors(cc)
+    plain = rc.dd_run(cc.subs, Ts, cc.n, cc.n_cuts, 3, 3, "bfs")
+    same = rc.dd_run(cc.subs, Ts, cc.n, cc.n_cuts, 3, 3, "bfs", follow=[r["parent"] for r in plain], follow_tol=1.0)
+    assert [r["roles"] for r in same] == [r["roles"] for r in plain]
+    assert not any(r["followed"] for r in same)
+    b = plain[0]["bins"]
+    order = sorted(range(len(b)), key=lambda i: (-b[i], i))
+    best, second = order[0], order[1]
+    assert plain[1]["parent"] == (0, best)
+    gap = b[best] - b[second]
+    assert gap > 0
+    far = rc.dd_run(cc.subs, Ts, cc.n, cc.n_cuts, 3, 2, "bfs", follow=[None, (0, second)], follow_tol=gap / 2)
+    assert far[1]["parent"] == (0, best) and not far[1]["followed"]
+    near = rc.dd_run(cc.subs, Ts, cc.n, cc.n_cuts, 3, 2, "bfs", follow=[None, (0, second)], follow_tol=gap * 2)
+    assert near[1]["parent"] == (0, second) and near[1]["followed"]
+    assert near[1]["bins"].sum() == pytest.approx(b[second], abs=1e-13)
+
+
 def _roles_cycle(cc, pattern):
     """Roles over the global qubits: the pattern repeated over the qubit order."""
     return [pattern[q % len(pattern)] for q in range(cc.n)]
