@@ -16,9 +16,15 @@ CUDA events on its stream; the max over ranks is reported.  With --gpus N
 under torchrun every rank reconstructs its own replica (weak scaling, no
 collective on the data path).
 
---impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the paper's Sec. 5.2 method: a subset of the Kronecker terms,
-scaled by the term count).
+Each line reports the median step time (best and mean beside it), a
+back-to-back steady-state timing with no flush, the dominant kernel's
+roofline fraction, and, on rank 0 at N = 1, the FP64 oracle timed on the host
+cores on the same input tensors (cpu_baseline) with the error of the timed
+output against it (error_vs_oracle).  With --gpus N outside torchrun the
+script starts the N ranks itself.
+
+--impl reference times the FP64 CPU oracle on the workload: every step is the
+plain sum over all 256 Kronecker terms for all 2^24 outputs.
 """
 from __future__ import annotations
 
@@ -68,6 +74,18 @@ def peaks():
         return p, "measured"
     except Exception:
         return dict(FALLBACK_PEAKS), "fallback"
+
+
+def tc_peak(pk, pk_src, algo):
+    """Tensor peak for the split form that ran: the measured BF16 burst peak,
+    or for TF32 the measured TF32 peak if the peaks file has one, else the
+    BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    from paper_2012_02333_gb300 import cutqc
+    if algo == getattr(cutqc, "CUTQC_TC_TF32X3", -1):
+        if "tf32_tflops" in pk:
+            return pk["tf32_tflops"], f"{pk_src} tf32"
+        return pk["bf16_tflops"] * 1.1 / 2.25, f"{pk_src} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+    return pk["bf16_tflops"], f"{pk_src} bf16 burst"
 
 
 def workload():
@@ -167,42 +185,124 @@ def job_value(n_out_per_rank, world, ms):
     return world * n_out_per_rank / (ms / 1e3)
 
 
-def oracle_sample_rate(cc, n_terms: int, T64=None):
-    """Oracle FP64 plain sum over `n_terms` of the 4^K Kronecker terms for all
-    2^n outputs, scaled by the term count (the paper's Sec. 5.2 method).
-    Returns (probs/s, seconds of the sample, the sample description)."""
-    from oracle import attribution as at
+def step_ms(ts):
+    """Median, best and mean of per-step times (ms); the median is the figure
+    the line reports."""
+    return {"median": statistics.median(ts), "best": min(ts), "mean": statistics.mean(ts)}
+
+
+def error_stats(got, want, what):
+    """Max-abs and total-variation error of a result against the oracle's."""
+    import numpy as np
+    d = np.asarray(got, np.float64) - np.asarray(want, np.float64)
+    return {"max_abs_err": float(np.abs(d).max()), "tv": float(0.5 * np.abs(d).sum()),
+            "entries_compared": int(d.size), "compared": what, "tol": 1e-6,
+            "within_tol": bool(np.abs(d).max() <= 1e-6)}
+
+
+def product_bins(rng, cc, roles, n_bins):
+    """About n_bins distinct bin indices of a dynamic-definition recursion,
+    drawn from a product of small per-subcircuit sets of active-output values,
+    so each subcircuit's merged tensor is needed at only a few active values."""
+    active = [q for q in range(cc.n) if roles[q] == 0]
+    rank = {q: i for i, q in enumerate(active)}
+    na = len(active)
+    per = []
+    for s in cc.subs:
+        qs = [q for q in s.out_qubit if roles[q] == 0]
+        per.append((qs, rng.choice(2 ** len(qs), size=min(2 ** len(qs), 32), replace=False) if qs else [0]))
+    combos = set()
+    tries = 0
+    while len(combos) < n_bins and tries < 20 * n_bins:
+        tries += 1
+        b = 0
+        for qs, vals in per:
+            a = int(vals[rng.integers(len(vals))])
+            for j, q in enumerate(qs):
+                b |= ((a >> (len(qs) - 1 - j)) & 1) << (na - 1 - rank[q])
+        combos.add(b)
+    return sorted(combos)
+
+
+def device_slab(torch, cc, ts, roles):
+    """slab(c, a) for the oracle's selected-bin sum (dd_entries): gathers, on
+    the device, the tensor entries of subcircuit c whose active outputs read
+    `a` and zoomed outputs their fixed bits, and hands them to the host in row
+    pieces of at most 512 MiB (data movement only; the sums are the oracle's)."""
+    def slab(c, a):
+        s = cc.subs[c]
+        T = ts[c].view(4 ** s.k_in * 4 ** s.k_out, 2 ** s.n_eff)
+        base = 0
+        act = [i for i, q in enumerate(s.out_qubit) if roles[q] == 0]
+        mrg = [i for i, q in enumerate(s.out_qubit) if roles[q] == 1]
+        for j, i in enumerate(act):
+            base |= ((a >> (len(act) - 1 - j)) & 1) << (s.n_eff - 1 - i)
+        for i, q in enumerate(s.out_qubit):
+            if roles[q] == 3:
+                base |= 1 << (s.n_eff - 1 - i)
+        m = torch.arange(2 ** len(mrg), device=T.device, dtype=torch.int64)
+        cols = torch.full_like(m, base)
+        for j, i in enumerate(mrg):
+            cols |= ((m >> (len(mrg) - 1 - j)) & 1) << (s.n_eff - 1 - i)
+        step = max(1, (1 << 27) // cols.numel())
+        for r0 in range(0, T.shape[0], step):
+            yield r0, T[r0:r0 + step].index_select(1, cols).cpu().numpy()
+    return slab
+
+
+def oracle_fd_leg(cc, host64, got_fn, n_sample=None, rng=None):
+    """The cpu_baseline leg of a full-definition workload: the FP64 oracle's
+    plain sum on the workload's own tensors, timed on the host cores, and the
+    error of the GPU result against it.  With n_sample set, the oracle
+    evaluates that many sampled outputs one by one (all 4^K terms each)
+    instead of all 2^n.  got_fn(xs or None) returns the GPU result (all, or at
+    xs) as a numpy array."""
+    import numpy as np
     from oracle import reconstruct as rc
-    if T64 is None:
-        T64 = [T.astype("float32").astype("float64") for T in at.tensors(cc)]
-    total = 4 ** cc.n_cuts
-    terms = list(range(0, total, max(1, total // n_terms)))[:n_terms]
     t0 = time.perf_counter()
-    rc.fd_full(cc.subs, T64, cc.n, cc.n_cuts, terms=terms)
+    if n_sample is None:
+        want = rc.fd_full(cc.subs, host64, cc.n, cc.n_cuts)
+        xs = None
+    else:
+        xs = sorted(set(int(x) for x in rng.integers(0, 2 ** cc.n, n_sample)))
+        want = rc.fd_entries(cc.subs, host64, cc.n, cc.n_cuts, xs)
     dt = time.perf_counter() - t0
-    scaled = dt * total / len(terms)
-    return 2 ** cc.n / scaled, dt, (f"{len(terms)} of {total} Kronecker terms over all 2^{cc.n} outputs, "
-                                    f"FP64 numpy oracle, time scaled by {total}/{len(terms)}"), T64
+    n_units = 2 ** cc.n if xs is None else len(xs)
+    what = (f"all 2^{cc.n} outputs" if xs is None else f"{len(xs)} sampled outputs of 2^{cc.n}")
+    cpu = {"value": n_units / dt, "unit": "probs/s", "cores": 1, "kind": "oracle",
+           "sample": f"{what}, every one of the 4^{cc.n_cuts} Kronecker terms, FP64 numpy oracle (no scaling)",
+           "sample_seconds": dt, "host_cpus": os.cpu_count()}
+    return cpu, error_stats(got_fn(xs), want, what + " vs the FP64 oracle on the same input tensors"), want
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle as it stands, timed on the host
+    cores.  One step = the oracle's plain sum over all 256 Kronecker terms for
+    all 2^24 outputs of the benchmark workload (nothing scaled)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import numpy as np
+    from oracle import attribution as at
+    from oracle import reconstruct as rc
     cc = workload()
+    T64 = [T.astype(np.float32).astype(np.float64) for T in at.tensors(cc)]
     W, K = args.warmup, args.steps
-    T64 = None
     times = []
-    desc = ""
     for i in range(W + K):
-        rate, dt, desc, T64 = oracle_sample_rate(cc, 4, T64)
+        t0 = time.perf_counter()
+        rc.fd_full(cc.subs, T64, cc.n, cc.n_cuts)
+        dt = time.perf_counter() - t0
         if i >= W:
-            times.append(2 ** cc.n / rate)
-    ms = 1e3 * statistics.mean(times)
+            times.append(1e3 * dt)
+    st = step_ms(times)
+    ms = st["median"]
     value = 2 ** cc.n / (ms / 1e3)
+    desc = (f"all 2^{cc.n} outputs of the workload, every one of the {4 ** cc.n_cuts} Kronecker terms, FP64 numpy "
+            f"oracle on the oracle-simulated tensors rounded to FP32")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": K, "warmup": W, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": K, "warmup": W, "ms_per_step": ms, "ms_best": st["best"], "ms_mean": st["mean"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": cc.n, "n_cuts": cc.n_cuts},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -273,23 +373,37 @@ def run_ours(args):
         b.record(stream)
     torch.cuda.synchronize()
     launches = cutqc.launch_count() - l0
+    # steady state: the same steps back to back with no flush in between, so
+    # each step also pays for writing the previous step's output back to HBM
+    sa, sb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sa.record(stream)
+    for _ in range(args.steps):
+        step()
+    sb.record(stream)
+    torch.cuda.synchronize()
     barrier(world)
     clocks = clk.stop()
-    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    st = step_ms([a.elapsed_time(b) for a, b in evs])
+    ms_steady = max_over_ranks(sa.elapsed_time(sb) / args.steps, world)
     # the dominant kernel alone: the same steps again with its launches
     # bracketed by events on its stream (this separates it from the kernels
-    # before it, which otherwise overlap its start)
+    # before it, which otherwise overlap its start), flushed and back to back
     cutqc.profile_read()        # discard
     cutqc.profile(True)
     for _ in range(args.steps):
         flush_l2()
         step()
     torch.cuda.synchronize()
-    cutqc.profile(False)
     n_main, main_ms = cutqc.profile_read()
-    ms = max_over_ranks(ms, world)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    cutqc.profile(False)
+    n_main2, main_ms2 = cutqc.profile_read()
+    ms = max_over_ranks(st["median"], world)
     value = job_value(n_out, world, ms)
     kern_ms = main_ms / max(n_main, 1)
+    kern_ms_steady = main_ms2 / max(n_main2, 1)
 
     # end to end through the public API: pinned host tensors in, probabilities out
     out_host = torch.empty(n_out, dtype=torch.float32).pin_memory()
@@ -307,7 +421,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e = max_over_ranks(statistics.mean(e2e_ms), world)
+    e2e = max_over_ranks(statistics.median(e2e_ms), world)
     h2d = sum(t.numel() * t.element_size() for t in host)
     d2h = n_out * 4 + 8
 
@@ -315,43 +429,57 @@ def run_ours(args):
     used_tc = cutqc.last_algo() != cutqc.CUTQC_CC
     flops1 = 2.0 * k_eff * n_out
     bytes_alg = n_out * 4 + sum(t.numel() * 4 for t in tensors)
-    t_s = kern_ms / 1e3
-    hbm = {"bytes_per_launch": bytes_alg, "achieved_gbs": bytes_alg / t_s / 1e9, "peak_gbs": pk["hbm_gbs"],
-           "frac": bytes_alg / t_s / 1e9 / pk["hbm_gbs"], "t_roof_us": bytes_alg / (pk["hbm_gbs"] * 1e9) * 1e6}
-    if used_tc:
-        s, split_S = cutqc.last_split()
-        peak_t = pk["bf16_tflops"]
-        comp = {"flops_per_launch": s * flops1, "split_products": s, "split_bound_S": split_S,
-                "achieved_tflops": s * flops1 / t_s / 1e12, "peak_tflops": peak_t,
-                "frac": s * flops1 / t_s / 1e12 / peak_t, "peak_source": f"{pk_src} bf16 burst",
-                "frac_single_product": flops1 / t_s / 1e12 / peak_t,
-                "t_roof_us": s * flops1 / (peak_t * 1e12) * 1e6}
-        dtype = f"bf16x{s}-f32acc"
-        cbound = "tensor"
-    else:
-        comp = {"flops_per_launch": flops1, "achieved_tflops": flops1 / t_s / 1e12, "peak_tflops": FP32_ALU_TFLOPS,
-                "frac": flops1 / t_s / 1e12 / FP32_ALU_TFLOPS,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "t_roof_us": flops1 / (FP32_ALU_TFLOPS * 1e12) * 1e6}
-        dtype = "f32"
-        cbound = "alu"
-    if comp["t_roof_us"] >= hbm["t_roof_us"]:
-        roof = {"bound": cbound, "achieved": comp["achieved_tflops"], "peak": comp["peak_tflops"],
-                "unit": "TFLOP/s", "frac": comp["frac"]}
-    else:
-        roof = {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm["peak_gbs"], "unit": "GB/s",
-                "frac": hbm["frac"]}
+
+    def roof_of(kms):
+        t_s = kms / 1e3
+        hbm = {"bytes_per_launch": bytes_alg, "achieved_gbs": bytes_alg / t_s / 1e9, "peak_gbs": pk["hbm_gbs"],
+               "frac": bytes_alg / t_s / 1e9 / pk["hbm_gbs"], "t_roof_us": bytes_alg / (pk["hbm_gbs"] * 1e9) * 1e6}
+        if used_tc:
+            s, split_S = cutqc.last_split()
+            peak_t, src = tc_peak(pk, pk_src, cutqc.last_algo())
+            comp = {"flops_per_launch": s * flops1, "split_products": s, "split_bound_S": split_S,
+                    "achieved_tflops": s * flops1 / t_s / 1e12, "peak_tflops": peak_t,
+                    "frac": s * flops1 / t_s / 1e12 / peak_t, "peak_source": src,
+                    "frac_single_product": flops1 / t_s / 1e12 / peak_t,
+                    "t_roof_us": s * flops1 / (peak_t * 1e12) * 1e6}
+            cbound = "tensor"
+        else:
+            comp = {"flops_per_launch": flops1, "achieved_tflops": flops1 / t_s / 1e12,
+                    "peak_tflops": FP32_ALU_TFLOPS, "frac": flops1 / t_s / 1e12 / FP32_ALU_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "t_roof_us": flops1 / (FP32_ALU_TFLOPS * 1e12) * 1e6}
+            cbound = "alu"
+        if comp["t_roof_us"] >= hbm["t_roof_us"]:
+            r = {"bound": cbound, "achieved": comp["achieved_tflops"], "peak": comp["peak_tflops"],
+                 "unit": "TFLOP/s", "frac": comp["frac"]}
+        else:
+            r = {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm["peak_gbs"], "unit": "GB/s",
+                 "frac": hbm["frac"]}
+        r.update({"t_roof_us": max(comp["t_roof_us"], hbm["t_roof_us"]), "compute": comp, "hbm": hbm})
+        return r
+    # the reported fraction is the lower of the two regimes: flushed L2 (inputs
+    # from HBM, the output absorbed by L2) and back to back (the previous
+    # output's write-back inside the launch)
+    r_fl, r_st = roof_of(kern_ms), roof_of(kern_ms_steady)
+    roof = dict(r_fl if r_fl["frac"] <= r_st["frac"] else r_st)
+    roof["regime"] = "flushed" if r_fl["frac"] <= r_st["frac"] else "back_to_back"
     traffic = None
     if used_tc:
         import hashlib
         src = os.path.join(ROOT, "paper_2012_02333_gb300", "csrc", "k_tc.cu")
         if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == TRAFFIC_TC["sha256_16"]:
             traffic = TRAFFIC_TC["bytes"]
-    roof.update({"traffic": traffic, "kernel_ms": kern_ms, "peak_file": pk_src,
-                 "t_roof_us": max(comp["t_roof_us"], hbm["t_roof_us"]), "compute": comp, "hbm": hbm})
+    roof.update({"traffic": traffic, "kernel_ms": kern_ms if roof["regime"] == "flushed" else kern_ms_steady,
+                 "kernel_ms_flushed": kern_ms, "kernel_ms_back_to_back": kern_ms_steady,
+                 "frac_flushed": r_fl["frac"], "frac_back_to_back": r_st["frac"], "peak_file": pk_src})
 
+    dtype = {cutqc.CUTQC_CC: "f32"}.get(cutqc.last_algo(), None)
+    if dtype is None:
+        s, _ = cutqc.last_split()
+        dtype = ("tf32" if cutqc.last_algo() == getattr(cutqc, "CUTQC_TC_TF32X3", -1) else "bf16") + f"x{s}-f32acc"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "ms_best": st["best"], "ms_mean": st["mean"],
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_qubits": cc.n, "n_cuts": cc.n_cuts,
                        "kronecker_terms": 4 ** cc.n_cuts, "nonzero_terms": k_eff,
@@ -359,6 +487,8 @@ def run_ours(args):
                        "algo": args.algo, "inputs": "FP32 tensors from the GPU subcircuit simulator, seed 0",
                        "l2": "flushed before every timed step: 256 MiB written then read back (outside the timed region)",
                        "parallelism": f"replicas x{world}"},
+            "steady_state": {"ms_per_step": ms_steady, "value": job_value(n_out, world, ms_steady),
+                             "l2": "no flush: steps back to back, each pays the previous output's write-back"},
             "roofline": roof,
             "e2e": {"value": world * n_out / (e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "ms_per_step": e2e,
@@ -366,9 +496,12 @@ def run_ours(args):
                             "contraction straight into pinned host memory, FP64 sum copied back"},
             "gpu_launches": launches, "clocks": clocks}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, dt, desc, _ = oracle_sample_rate(cc, 96)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc,
-                                "sample_seconds": dt, "host_cpus": os.cpu_count()}
+        host64 = [t.numpy().astype(np.float64) for t in host]
+        cpu, err, want = oracle_fd_leg(cc, host64, lambda xs: out.double().cpu().numpy())
+        err["sum_p"] = float(sum_p.item())
+        err["sum_p_minus_oracle_sum"] = float(sum_p.item() - want.sum())
+        line["cpu_baseline"] = cpu
+        line["error_vs_oracle"] = err
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -395,7 +528,11 @@ def run_other(args):
         flush.fill_(1.0)
         torch.sum(flush, dim=0, out=sink)
 
-    def timed(step):
+    stats = {}
+
+    def timed(step, key="main"):
+        """Median step time (ms) over args.steps flushed steps; median, best and
+        mean are kept under `key`."""
         for _ in range(max(args.warmup, 3)):
             flush_l2()
             step()
@@ -409,8 +546,12 @@ def run_other(args):
             b.record(stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
-        return max_over_ranks(statistics.mean(ts), world)
+        stats[key] = step_ms(ts)
+        return max_over_ranks(stats[key]["median"], world)
 
+    import numpy as np
+    rng = np.random.default_rng(2012)
+    check = rank == 0 and world == 1 and not args.no_cpu_baseline
     extra = {}
     w = args.workload
     if w == "hwea10":
@@ -419,6 +560,9 @@ def run_other(args):
         problem = cutqc.Problem.from_cut(cc, ts)
         out = torch.empty(2 ** cc.n, dtype=torch.float64, device=dev)
         ms = timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc"))
+        if check:
+            cpu, err, _ = oracle_fd_leg(cc, [t.cpu().numpy() for t in ts], lambda xs: out.cpu().numpy())
+            extra.update({"cpu_baseline": cpu, "error_vs_oracle": err})
         units, unit, dtype = 2 ** cc.n, "probs/s", "f64"
         cfg = {"workload": "hwea10_K1_fd_fp64", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
     elif w == "batch64":
@@ -434,11 +578,31 @@ def run_other(args):
         bytes_alg = sum(o.numel() * 4 for o in outs) + sum(t.numel() * 4 for ts in tss for t in ts)
         pk, pk_src = peaks()
         gbs = bytes_alg / (ms / 1e3) / 1e9
-        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "cc", sums)),
+        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "cc", sums), "cc"),
                  "cc_only": "every instance on the FP32 CUDA-core form, same graph replay",
                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                               "frac": gbs / pk["hbm_gbs"], "traffic": None, "algorithmic_bytes": bytes_alg,
                               "peak_file": pk_src}}
+        if check:
+            # 64 sampled outputs of every instance, each by all of its 4^K terms,
+            # against the automatic form's outputs (the timed line's)
+            cutqc.cutqc_reconstruct_fd(problems, outs, "auto", sums)
+            cpu_s, n_cpu, gots = 0.0, 0, []
+            for cc, t, o in zip(batch, tss, outs):
+                cpu, err, want = oracle_fd_leg(
+                    cc, [x.double().cpu().numpy() for x in t],
+                    lambda xs, o=o: o[torch.tensor(xs, device=dev)].double().cpu().numpy(), 64, rng)
+                cpu_s += cpu["sample_seconds"]
+                n_cpu += err["entries_compared"]
+                gots.append(err["max_abs_err"])
+            extra["cpu_baseline"] = {"value": n_cpu / cpu_s, "unit": "probs/s", "cores": 1, "kind": "oracle",
+                                     "sample": "64 sampled outputs of each of the 64 instances, every one of "
+                                               "its 4^K Kronecker terms, FP64 numpy oracle (no scaling)",
+                                     "sample_seconds": cpu_s}
+            extra["error_vs_oracle"] = {"max_abs_err": max(gots), "entries_compared": n_cpu, "tol": 1e-6,
+                                        "within_tol": max(gots) <= 1e-6,
+                                        "compared": "64 sampled outputs per instance vs the FP64 oracle on the "
+                                                    "same input tensors"}
         units, unit, dtype = sum(2 ** cc.n for cc in batch), "probs/s", "f32 (per instance cc or bf16x3/x6)"
         cfg = {"workload": "batch64_hwea_aqft_bv_fd_fp32", "instances": len(batch),
                "n_qubits": [cc.n for cc in batch], "n_cuts": [cc.n_cuts for cc in batch],
@@ -452,11 +616,18 @@ def run_other(args):
         ms = timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp))
         grads = [torch.empty_like(t) for t in ts]
         loss = torch.empty(1, dtype=torch.float64, device=dev)
-        ms_bwd = timed(lambda: cutqc.cutqc_reconstruct_backward(problem, grads, edges=cc.edges, loss_value=loss))
+        ms_bwd = timed(lambda: cutqc.cutqc_reconstruct_backward(problem, grads, edges=cc.edges, loss_value=loss),
+                       "bwd")
         extra = {"adjoint_ms": ms_bwd, "adjoint": "MaxCut loss and dL/dT of both subcircuits",
                  "expected_cut": float(loss.item()),
-                 "cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc", sp)),
+                 "cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc", sp), "cc"),
                  "cc_only": "forward on the FP32 CUDA-core form"}
+        if check:
+            cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp)
+            cpu, err, _ = oracle_fd_leg(cc, [t.double().cpu().numpy() for t in ts],
+                                        lambda xs: out[torch.tensor(xs, device=dev)].double().cpu().numpy(),
+                                        4096, rng)
+            extra.update({"cpu_baseline": cpu, "error_vs_oracle": err})
         units, unit, dtype = 2 ** cc.n, "probs/s", "bf16x3/x6-f32acc"
         cfg = {"workload": "qaoa30_maxcut_K4_fd_fp32", "n_qubits": cc.n, "n_cuts": cc.n_cuts}
     elif w == "sim_supremacy4x6":
@@ -505,7 +676,7 @@ def run_other(args):
         gen = torch.Generator(device=dev)
         gen.manual_seed(0)
         u = torch.rand(1 << 20, dtype=torch.float64, generator=gen, device=dev)
-        ms_s = timed(lambda: cutqc.cutqc_sample(pa, u))
+        ms_s = timed(lambda: cutqc.cutqc_sample(pa, u), "sample")
         bytes_alg = 2 * pa.numel() * 4
         pk, pk_src = peaks()
         extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
@@ -541,6 +712,18 @@ def run_other(args):
         extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
                               "unit": "GB/s", "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
                               "traffic": None, "algorithmic_bytes": bytes_alg, "peak_file": pk_src}}
+        if check:
+            from oracle import attribution as at
+            t0 = time.perf_counter()
+            wants = [at.attribute_merged(sub, p.double().cpu().numpy().reshape((4 ** sub.k_in) * (3 ** sub.k_out), -1),
+                                         roles) for sub, p in zip(cc.subs, probs)]
+            dt = time.perf_counter() - t0
+            extra["cpu_baseline"] = {"value": sum(p.numel() for p in probs) / dt, "unit": "variant outcomes/s",
+                                     "cores": 1, "kind": "oracle", "sample_seconds": dt,
+                                     "sample": "both subcircuits' merged tensors in full, FP64 numpy oracle"}
+            extra["error_vs_oracle"] = error_stats(
+                np.concatenate([o.double().cpu().numpy() for o in outs]),
+                np.concatenate([w.reshape(-1) for w in wants]), "every merged tensor entry vs the FP64 oracle")
         units, unit, dtype = sum(p.numel() for p in probs), "variant outcomes/s", "f32 in, compensated f32 sums"
         cfg = {"workload": "attr_merged_qaoa30_fp32", "roles": "qubits 0-19 active, 20-29 merged",
                "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
@@ -570,6 +753,18 @@ def run_other(args):
         extra = {"roofline": {"bound": "hbm", "achieved": bytes_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
                               "unit": "GB/s", "frac": bytes_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
                               "traffic": None, "algorithmic_bytes": bytes_alg, "peak_file": pk_src}}
+        if check:
+            from oracle import attribution as at
+            t0 = time.perf_counter()
+            wants = [at.attribute(sub, p.double().cpu().numpy().reshape((4 ** sub.k_in) * (3 ** sub.k_out), -1))
+                     for sub, p in zip(cc.subs, probs)]
+            dt = time.perf_counter() - t0
+            extra["cpu_baseline"] = {"value": sum(o.numel() for o in outs) / dt, "unit": "tensor entries/s",
+                                     "cores": 1, "kind": "oracle", "sample_seconds": dt,
+                                     "sample": "both subcircuits' tensors in full, FP64 numpy oracle (Eq. 3, Eq. 2)"}
+            extra["error_vs_oracle"] = error_stats(
+                np.concatenate([o.double().cpu().numpy() for o in outs]),
+                np.concatenate([w.reshape(-1) for w in wants]), "every tensor entry vs the FP64 oracle")
         units, unit, dtype = sum(o.numel() for o in outs), "tensor entries/s", "f32 in, compensated f32 sums"
         cfg = {"workload": "attr_qaoa30_fp32", "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
                "inputs": "seeded uniform variant distributions normalised per variant (synthetic shot frequencies)",
@@ -581,8 +776,27 @@ def run_other(args):
         roles = dd.initial_roles(cc.n, 30)
         bins = torch.empty(2 ** 30, device=dev)
         ms = timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto"))
-        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "cc")),
+        extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "cc"), "cc"),
                  "cc_only": "one recursion with the final contraction on the FP32 CUDA-core form"}
+        if check:
+            from oracle import reconstruct as rc
+            top = cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto")
+            xs = product_bins(rng, cc, roles, 1024)
+            slab = device_slab(torch, cc, ts, roles)
+            t0 = time.perf_counter()
+            cache = {}
+            want_top = rc.dd_entries(cc.subs, slab, cc.n, cc.n_cuts, roles, top[0], cache)
+            want = rc.dd_entries(cc.subs, slab, cc.n, cc.n_cuts, roles, xs, cache)
+            dt = time.perf_counter() - t0
+            err = error_stats(bins[torch.tensor(xs, device=dev)].double().cpu().numpy(), want,
+                              f"{len(xs)} sampled bins of 2^30 vs the FP64 oracle's sum over merged tensors")
+            err["top32_fp64_max_abs_err"] = float(np.abs(np.array(top[1]) - want_top).max())
+            err["top1_matches_oracle"] = bool(top[0][int(np.argmax(want_top))] == top[0][0])
+            extra.update({"error_vs_oracle": err,
+                          "cpu_baseline": {"value": (len(xs) + len(top[0])) / dt, "unit": "bins/s", "cores": 1,
+                                           "kind": "oracle", "sample_seconds": dt,
+                                           "sample": "the recursion's top-32 and 1024 sampled bins by the plain FP64 "
+                                                     "sum over merged tensors (merging read from the device)"}})
         del bins
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -596,7 +810,8 @@ def run_other(args):
                "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff] for s in cc.subs],
                "step": "one recursion: merge, contraction into 2^30 bins, top-32 with FP64 re-ranking"}
     line = {"metric": METRIC, "value": world * units / (ms / 1e3), "unit": unit, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "ms_best": stats["main"]["best"],
+            "ms_mean": stats["main"]["mean"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": cfg}
     line.update(extra)
     if rank == 0:
@@ -606,8 +821,22 @@ def run_other(args):
         dist.destroy_process_group()
 
 
+def launch_ranks(n):
+    """--gpus N outside torchrun: start N ranks of this command on this node
+    (one process per GPU, rendezvous on 127.0.0.1) and return their status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(launch_ranks(args.gpus))
     if args.impl == "reference":
         run_reference(args)
     elif args.workload != "supremacy_4x6":

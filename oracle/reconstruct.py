@@ -213,7 +213,7 @@ def dd_run(subs, tensors, n_qubits: int, n_cuts: int, n_active: int,
     return out
 
 
-def dd_entries(subs, slab, n_qubits: int, n_cuts: int, roles, bins) -> np.ndarray:
+def dd_entries(subs, slab, n_qubits: int, n_cuts: int, roles, bins, cache=None) -> np.ndarray:
     """Selected bins of one DD recursion by the plain sum over merged tensors
     (Algorithm 1), for sizes where neither the merged tensors nor the bins
     can be formed whole.  slab(c, a) yields the entries of subcircuit c's
@@ -223,13 +223,15 @@ def dd_entries(subs, slab, n_qubits: int, n_cuts: int, roles, bins) -> np.ndarra
     merged outputs' entries]) covering every row and every merged entry once.
     The merged value of a row is the sum over its merged entries; a bin is
     2^-K sum_e prod_c (merged value of subcircuit c at row e|c and its active
-    bits of the bin).  Bin index as dd_bins."""
+    bits of the bin).  Bin index as dd_bins.  `cache` (a dict, optional)
+    keeps merged values between calls, keyed by the subcircuit, the roles of
+    its outputs and `a`."""
     K = n_cuts
     active = [q for q in range(n_qubits) if roles[q] == 0]
     rank = {q: i for i, q in enumerate(active)}
     na = len(active)
     rows = np.array([[row_of(s, _digits(e, K)) for s in subs] for e in range(4 ** K)], dtype=np.int64)
-    merged = {}
+    merged = {} if cache is None else cache
     out = np.empty(len(bins))
     for i, b in enumerate(bins):
         acc = np.ones(4 ** K)
@@ -238,13 +240,14 @@ def dd_entries(subs, slab, n_qubits: int, n_cuts: int, roles, bins) -> np.ndarra
             for q in s.out_qubit:
                 if roles[q] == 0:
                     a = 2 * a + ((int(b) >> (na - 1 - rank[q])) & 1)
-            if (c, a) not in merged:
+            key = (c, tuple(roles[q] for q in s.out_qubit), a)
+            if key not in merged:
                 m = np.zeros(4 ** s.k_in * 4 ** s.k_out)
                 for r0, piece in slab(c, a):
                     piece = np.asarray(piece)
                     m[r0:r0 + piece.shape[0]] += piece.sum(axis=1, dtype=np.float64)
-                merged[(c, a)] = m
-            acc = acc * merged[(c, a)][rows[:, c]]
+                merged[key] = m
+            acc = acc * merged[key][rows[:, c]]
         out[i] = acc.sum() * 2.0 ** -K
     return out
 

@@ -14,6 +14,9 @@ from test_gpu_fd import env, oracle_case, to_dev  # noqa: E402,F401
 
 pytestmark = pytest.mark.gpu
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+# the library ranks candidates by values recomputed in FP64 from the same
+# tensors as the oracle: two bins closer than this are a tie decided by rounding
+TIE_TOL = 1e-12
 
 
 def check_run(env, cc, T, dtype_np, algo, n_active, recursions, strategy, tol):
@@ -43,6 +46,14 @@ def check_run(env, cc, T, dtype_np, algo, n_active, recursions, strategy, tol):
             # the zoomed bin's probability is split exactly across the child bins
             parent_val = rc.dd_bins(cc.subs, T64, cc.n, cc.n_cuts, st.recursions[pr].roles)[pb]
             assert want.sum() == pytest.approx(parent_val, abs=1e-12)
+    # the whole zoom sequence is Algorithm 1's as the oracle runs it; a choice
+    # may differ only where the oracle's two candidates are within rounding of
+    # each other (reading R8), and then the oracle follows it
+    orc = rc.dd_run(cc.subs, T64, cc.n, cc.n_cuts, n_active, recursions, strategy,
+                    follow=[r.parent for r in st.recursions], follow_tol=TIE_TOL)
+    assert len(orc) == len(st.recursions)
+    assert [r["roles"] for r in orc] == [r.roles for r in st.recursions]
+    assert [r["parent"] for r in orc] == [r.parent for r in st.recursions]
     return st
 
 
@@ -108,12 +119,14 @@ def test_dd_twin_of_80_qubit_workload(env):
 def test_dd_80q_full_size(env):
     """The 80-qubit workload itself: an 8x10 supremacy-style grid of depth 10
     cut into 2x2 blocks (4 subcircuits of <= 25 qubits, K = 8), FP32 tensors
-    from the GPU simulator, 30 active qubits (2^30 bins) and 10 BFS recursions.
-    Its tensors come from the CUDA path, so the oracle cannot take them;
-    checked by properties that hold at any size: recursion 1's bins sum to 1
-    (the uncut circuit preserves trace), every zoomed recursion's bins sum to
-    the parent bin's FP64 value, no bin is below -1e-6, and the FP64-ranked top
-    values agree with the stored bins."""
+    from the GPU simulator (the configuration's input preparation), 30 active
+    qubits (2^30 bins) and 10 BFS recursions.  Checked by properties of the
+    physical circuit that hold at any size: recursion 1's bins sum to 1 (the
+    uncut circuit preserves trace), every zoomed recursion's bins sum to the
+    parent bin's FP64 value, no bin is below -1e-6, and the FP64-ranked top
+    values agree with the stored bins.  The oracle comparison at this size
+    runs on seeded synthetic tensors of the same shapes (the next test), so
+    that no value it trusts comes from the library."""
     torch, cutqc = env
     from paper_2012_02333_gb300 import circuits as C
     from paper_2012_02333_gb300 import dd
@@ -159,3 +172,89 @@ def test_dd_skinny_contraction(env, n_active, dtype_np, algo, tol):
     products (the skinny CUDA-core form, both operand orders)."""
     cc, T = oracle_case("hwea22_s2", cases.hwea22_chain)
     check_run(env, cc, T, dtype_np, algo, n_active, 3, "bfs", tol)
+
+
+def _synthetic_tensors(torch, cc, seed):
+    """Seeded synthetic FP32 tensors of the workload's shapes, shaped like
+    attributed tensors: the all-identity row a positive weight profile w
+    (exponential, normalised to 2^(slots/2)), every other row w times a
+    uniform sign-and-size factor in [-1/2, 1/2] (bounded by the identity row,
+    as Pauli expectations are), so the bins form a landscape of mass about 1
+    with signed corrections."""
+    ts = []
+    for c, s in enumerate(cc.subs):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(1000 * seed + c)
+        rows, cols = 4 ** (s.k_in + s.k_out), 2 ** s.n_eff
+        w = torch.empty(cols, device="cuda").exponential_(generator=g)
+        w *= 2.0 ** ((s.k_in + s.k_out) / 2) / w.sum()
+        t = torch.rand(rows, cols, device="cuda", generator=g)
+        t.sub_(0.5)
+        t[0].fill_(1.0)
+        t.mul_(w)
+        ts.append(t.view(-1))
+    return ts
+
+
+def test_dd_80q_full_size_against_oracle(env):
+    """The 80-qubit dynamic-definition launch configuration (8x10 grid cut into
+    2x2 blocks, K = 8, 4 subcircuits of up to 2^20 outputs and 4^6 rows, 30
+    active qubits, 10 BFS recursions) on seeded synthetic tensors of those
+    shapes, against the oracle in every recursion: each returned top-32
+    candidate's FP64 value and 1024 sampled bins (drawn so each subcircuit's
+    merged tensor is needed at few active values) by the plain FP64 sum over
+    merged tensors; every zoom choice is the heaviest eligible candidate by the
+    oracle's values unless the two are within rounding (reading R8); and no
+    stored bin outside a top list beats its last entry."""
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    from paper_2012_02333_gb300 import circuits as C
+    from paper_2012_02333_gb300 import dd
+    cc = C.grid_blocks(8, 10, 10, 0, 2, 2, 8, 25)
+    from bench import device_slab, product_bins
+    ts = _synthetic_tensors(torch, cc, 80)
+    st = dd.run(cc, ts, 30, 10, "bfs")
+    assert len(st.recursions) == 10
+    rng = np.random.default_rng(80)
+    cache = {}
+    orc_top = []
+    worst = 0.0
+    for ri, rec in enumerate(st.recursions):
+        slab = device_slab(torch, cc, ts, rec.roles)
+        idx = [i for i, _ in rec.top if i >= 0]
+        vals = np.array([v for i, v in rec.top if i >= 0])
+        want_top = rc.dd_entries(cc.subs, slab, cc.n, cc.n_cuts, rec.roles, idx, cache)
+        assert np.abs(vals - want_top).max() <= TIE_TOL, (ri, np.abs(vals - want_top).max())
+        orc_top.append(dict(zip(idx, want_top)))
+        xs = product_bins(rng, cc, rec.roles, 1024)
+        assert len(xs) >= 1000
+        want = rc.dd_entries(cc.subs, slab, cc.n, cc.n_cuts, rec.roles, xs, cache)
+        got = rec.bins[torch.tensor(xs, device="cuda")].double().cpu().numpy()
+        err = np.abs(got - want).max()
+        worst = max(worst, err)
+        assert err <= 1e-6, (ri, err, np.abs(want).max())
+        # the stored bins outside the top list do not beat its last entry
+        rest = rec.bins.clone()
+        rest[torch.tensor(idx, device="cuda")] = -float("inf")
+        assert rest.max().item() <= vals[-1] + 2e-6
+        del rest
+    # zoom choices: the heaviest unexpanded candidate over earlier recursions
+    # by the oracle's values (ties: earlier recursion, then lower bin)
+    expanded = set()
+    for r in range(1, len(st.recursions)):
+        best = None
+        for pr in range(r):
+            if 1 not in st.recursions[pr].roles:
+                continue
+            for bi, v in sorted(orc_top[pr].items()):
+                if (pr, bi) in expanded:
+                    continue
+                if best is None or v > best[0]:
+                    best = (v, pr, bi)
+        got = st.recursions[r].parent
+        if got != (best[1], best[2]):
+            assert orc_top[got[0]][got[1]] >= best[0] - TIE_TOL, (r, got, best)
+        expanded.add(got)
+    print(f"80-qubit DD: max abs error of the sampled bins {worst:.3e}")
+    del st, ts
+    torch.cuda.empty_cache()
