@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3"])
+    ap.add_argument("--algo", default="auto", choices=["auto", "cc", "tc_bf16x3", "tc_bf16x6", "tc_tf32x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
                     choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "attr_merged_qaoa30",

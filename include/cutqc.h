@@ -92,6 +92,13 @@ typedef enum { CUTQC_F64 = 0, CUTQC_F32 = 1 } cutqc_dtype;
  *  CUTQC_TC_BF16X6 as above with a third piece l = bf16(x - h - m) and the
  *                  six products hh, hm, mh, hl, lh, mm: FP32-level accuracy
  *                  at twice the tensor work.
+ *  CUTQC_TC_TF32X3 tcgen05 tensor cores, FP32 tensors only: each operand x
+ *                  split into hi = tf32(x), lo = tf32(x - hi) (round to
+ *                  nearest; Ootomo and Yokota's split with TF32 pieces); the
+ *                  products hi*hi + hi*lo + lo*hi accumulate in FP32 in
+ *                  tensor memory.  Error per product <= ~3 * 2^-22 |a||b|, at
+ *                  half the BF16 tensor rate and 4/3 of the BF16 x3 operand
+ *                  bytes.  Never chosen by CUTQC_AUTO.
  *  CUTQC_AUTO      FP64 tensors: CUTQC_CC.  FP32 tensors: the tensor-core
  *                  path when the shape allows it (else CUTQC_CC), with the
  *                  number of products chosen on the device per call from
@@ -102,7 +109,8 @@ typedef enum {
   CUTQC_AUTO = 0,
   CUTQC_CC = 1,
   CUTQC_TC_BF16X3 = 2,
-  CUTQC_TC_BF16X6 = 3
+  CUTQC_TC_BF16X6 = 3,
+  CUTQC_TC_TF32X3 = 4
 } cutqc_algo;
 
 /* One subcircuit (host struct; `tensor` is a device pointer). */
@@ -137,6 +145,20 @@ typedef struct {
 CUTQC_API int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems,
                          void* const* out, int32_t algo, double* sum_p,
                          void* stream);
+
+/* One slab of a full definition (Sec. 4.2, whose parallel processing has no
+ * data dependency between output entries): the 2^(n_qubits - slab_bits)
+ * probabilities whose slab_bits most significant output bits (qubits
+ * 0 .. slab_bits-1) read slab_index, written to out in output order (out[j] =
+ * p(slab_index * 2^(n_qubits - slab_bits) + j)).  G ranks that each compute
+ * slab r of slab_bits = log2(G) together produce the whole distribution, and
+ * the FP64 partial sums they write to sum_p (device double, or NULL) add up
+ * to sum_x p(x): an 8-byte all-reduce is the only exchange.  Computed as a
+ * recursion of the dynamic definition whose zoomed qubits are the slab's (no
+ * merged qubits).  out as in cutqc_reconstruct_fd; algo as there.  No host
+ * synchronisation.  0 <= slab_bits < n_qubits, else CUTQC_ERR_ARG. */
+CUTQC_API int cutqc_reconstruct_fd_slab(const cutqc_problem* problem, int32_t slab_bits, int64_t slab_index,
+                                        void* out, int32_t algo, double* sum_p, void* stream);
 
 /* Dynamic definition, one recursion (Sec. 4.3, Algorithm 1).
  * role[q] (host, n_qubits entries): 0 active, 1 merged, 2 zoomed at 0,

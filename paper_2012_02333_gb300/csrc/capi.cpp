@@ -740,7 +740,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   if (algo == CUTQC_AUTO && P.tuned == CUTQC_CC) algo = CUTQC_CC;
   int final_algo = algo;
   if (final_algo == CUTQC_AUTO) final_algo = (P.dtype == CUTQC_F32) ? CUTQC_TC_BF16X3 : CUTQC_CC;
-  const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6;
+  const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6 || final_algo == CUTQC_TC_TF32X3;
   if (tc_algo && P.dtype != CUTQC_F32) fail(CUTQC_ERR_ARG, "the tensor-core forms need FP32 tensors");
   for (size_t i = 0; i < P.steps.size(); ++i) {
     Contraction& c = cs[i];
@@ -828,7 +828,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       cj.scale = c.scale;
       cj.bound = reinterpret_cast<double*>(base + st.ws_bound);
       cj.nseg = reinterpret_cast<int32_t*>(base + st.ws_nseg);
-      cj.nseg_fixed = algo == CUTQC_TC_BF16X3 ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+      cj.nseg_fixed = (algo == CUTQC_TC_BF16X3 || algo == CUTQC_TC_TF32X3) ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
       cj.sum_zero = sum;
       cj.counter = reinterpret_cast<unsigned*>(base + st.ws_counter);
       CUTQC_CUDA(cudaMemsetAsync(cj.counter, 0, sizeof(unsigned), s));
@@ -852,7 +852,8 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       c.rmaxB = reinterpret_cast<const float*>(base + P.ws_rmax[st.b]);
       c.bound = reinterpret_cast<double*>(base + st.ws_bound);
       c.nseg = reinterpret_cast<int32_t*>(base + st.ws_nseg);
-      c.nseg_fixed = algo == CUTQC_TC_BF16X3 ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+      c.nseg_fixed = (algo == CUTQC_TC_BF16X3 || algo == CUTQC_TC_TF32X3) ? 3 : (algo == CUTQC_TC_BF16X6 ? 6 : 0);
+      c.tf32 = algo == CUTQC_TC_TF32X3;
       g_last_nseg = c.nseg;
       g_last_bound = c.bound;
       g_last_stream = s;
@@ -1000,6 +1001,27 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
   ds.graphs[gk] = e;
 }
 
+// The pre-step of a dynamic-definition plan: merge every subcircuit's tensor
+// over its merged outputs with the zoomed outputs fixed (Algorithm 1), into
+// the front region of the workspace; returns the merged tensors.
+static std::function<std::vector<const void*>(char*)> dd_merge_pre(const Plan& P, const cutqc_problem* p,
+                                                                   cudaStream_t s, char** front_out) {
+  return [&P, p, s, front_out](char* front) {
+    if (front_out) *front_out = front;
+    char* ddtab = static_cast<char*>(P.ddtab);
+    std::vector<const void*> t(p->n_sub);
+    for (int c = 0; c < p->n_sub; ++c) {
+      const DdSubPlan& d = P.dd[c];
+      launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
+                      reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
+                      reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run, d.dense,
+                      front + d.ws_merged, reinterpret_cast<float*>(front + d.ws_mc), front + d.ws_part, s);
+      t[c] = front + d.ws_merged;
+    }
+    return t;
+  };
+}
+
 }  // namespace cutqc
 
 using namespace cutqc;
@@ -1011,7 +1033,7 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
   return guarded([&] {
     if (!problems || n_problems < 1) fail(CUTQC_ERR_ARG, "need n_problems >= 1 problems");
     if (!out) fail(CUTQC_ERR_ARG, "out is NULL");
-    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X6) fail(CUTQC_ERR_ARG, "unknown algo");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_TF32X3) fail(CUTQC_ERR_ARG, "unknown algo");
     for (int i = 0; i < n_problems; ++i) {
       validate(&problems[i], true);
       if (problems[i].n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
@@ -1037,6 +1059,30 @@ int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems, void
       return;
     }
     run_batch(ds, problems, n_problems, dout.data(), algo, sum_p, s);
+  });
+}
+
+int cutqc_reconstruct_fd_slab(const cutqc_problem* problem, int32_t slab_bits, int64_t slab_index, void* out,
+                              int32_t algo, double* sum_p, void* stream) {
+  return guarded([&] {
+    validate(problem, true);
+    const cutqc_problem* p = problem;
+    if (p->n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "full definition needs n_qubits <= 34");
+    if (slab_bits < 0 || slab_bits >= p->n_qubits) fail(CUTQC_ERR_ARG, "slab_bits must be in 0 .. n_qubits - 1");
+    if (slab_index < 0 || slab_index >= (int64_t(1) << slab_bits)) fail(CUTQC_ERR_ARG, "slab_index out of range");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_TF32X3) fail(CUTQC_ERR_ARG, "unknown algo");
+    if (!out) fail(CUTQC_ERR_ARG, "out is NULL");
+    need_aligned(out, 16, "out");
+    need_aligned(sum_p, 8, "sum_p");
+    void* dout = resolve_out(out);
+    // qubits 0 .. slab_bits-1 (the most significant output bits) fixed at the
+    // slab's bits, the rest active: the recursion's bins are the slab
+    std::vector<int8_t> role(p->n_qubits, 0);
+    for (int q = 0; q < slab_bits; ++q) role[q] = (int8_t)(((slab_index >> (slab_bits - 1 - q)) & 1) ? 3 : 2);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DeviceState& ds = device_state();
+    Plan& P = get_plan(ds, fd_key(p, 1, role.data(), 0), [&](Plan& P) { build_dd_plan(P, p, role.data()); });
+    run_plan(ds, P, P.dd_front, 0, dd_merge_pre(P, p, s, nullptr), dout, sum_p, algo, s);
   });
 }
 
@@ -1209,7 +1255,7 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
     if (!role) fail(CUTQC_ERR_ARG, "role is NULL");
     if (!bins) fail(CUTQC_ERR_ARG, "bins is NULL");
     need_aligned(bins, 16, "bins");
-    if (algo < CUTQC_AUTO || algo > CUTQC_TC_BF16X6) fail(CUTQC_ERR_ARG, "unknown algo");
+    if (algo < CUTQC_AUTO || algo > CUTQC_TC_TF32X3) fail(CUTQC_ERR_ARG, "unknown algo");
     if (topk < 0 || topk > 32) fail(CUTQC_ERR_UNSUPPORTED, "topk must be in 0..32");
     if (topk > 0 && (!top_idx || !top_val)) fail(CUTQC_ERR_ARG, "NULL top_idx / top_val");
     int na = 0;
@@ -1245,23 +1291,8 @@ int cutqc_reconstruct_dd(const cutqc_problem* problem, const int8_t* role, void*
     char* ddtab = static_cast<char*>(P.ddtab);
     char* front_ptr = nullptr;
     int fused_lists = 0;
-    char* back_ptr = run_plan(
-        ds, P, P.dd_front, back,
-        [&](char* front) {
-          front_ptr = front;
-          std::vector<const void*> t(p->n_sub);
-          for (int c = 0; c < p->n_sub; ++c) {
-            const DdSubPlan& d = P.dd[c];
-            launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
-                            reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
-                            reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run, d.dense,
-                            front + d.ws_merged, reinterpret_cast<float*>(front + d.ws_mc), front + d.ws_part,
-                            s);
-            t[c] = front + d.ws_merged;
-          }
-          return t;
-        },
-        bins, nullptr, algo, s, nullptr, nullptr, topk > 0 ? off_tk : SIZE_MAX, &fused_lists);
+    char* back_ptr = run_plan(ds, P, P.dd_front, back, dd_merge_pre(P, p, s, &front_ptr), bins, nullptr, algo, s,
+                              nullptr, nullptr, topk > 0 ? off_tk : SIZE_MAX, &fused_lists);
     if (topk > 0) {
       float* cv = reinterpret_cast<float*>(back_ptr + off_cv);
       int64_t* ci = reinterpret_cast<int64_t*>(back_ptr + off_ci);

@@ -113,6 +113,7 @@ struct Contraction {
   bool compacted = false;          // crow / kcount / nseg / bound already written (row statistics did it)
   int nseg_fixed = 0;
   double split_tol = 2.5e-7;
+  bool tf32 = false;               // tensor-core path: TF32 x3 pieces instead of bf16
   int* status = nullptr;           // device status word (DeviceStatus) of this device
   bool out_host = false;           // `out` is pinned host memory (written over the host link)
   // tensor-core path only: keep a top-32 of the written values per epilogue

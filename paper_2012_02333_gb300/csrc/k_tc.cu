@@ -32,6 +32,16 @@
 //              accumulator while the MMA fills the other.
 // Every wait on an mbarrier is bounded (2 s); on timeout the kernel raises an
 // abort flag, records a status word, lets in-flight copies land and frees TMEM.
+//
+// TF32 x3 (the same kernels, instantiated with TF32 = true): the split of
+// Ootomo and Yokota (2022) with TF32 pieces, x_hi = rna_tf32(x) and
+// x_lo = rna_tf32(x - x_hi), both kept in FP32 containers with the low 13
+// mantissa bits zero, and the products hi*hi + hi*lo + lo*hi with
+// tcgen05.mma kind::tf32 (K = 8).  TF32 has FP32's exponent range, so no
+// scaling of the lo piece is needed; the dropped lo*lo term and the rounding
+// of the lo piece bound the error per product by about 3 * 2^-22 |a||b|.  A
+// stage then holds 16 k of each piece: 64-byte rows, the same shared-memory
+// geometry as the BF16 stages.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -104,8 +114,16 @@ struct PrepArgs {
   int32_t* nseg;
   double* bound;
   double* sum_zero;
-  __nv_bfloat16* out[2];      // A', B': [piece][cols][Kp]
+  void* out[2];               // A', B': [piece][cols][Kp] (bf16, or FP32 containers of TF32 pieces)
 };
+
+// round to the nearest TF32 value (ties away from zero), kept in an FP32
+// container with the low 13 mantissa bits zero
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
 
 // out[piece][m][k] = piece of T[row(k)][m] for the k-th kept term (0 for
 // kcount <= k < Kp): pieces h and m for the x3 form, h, m and l for x6; each
@@ -121,6 +139,7 @@ struct PrepArgs {
 // read through L2 (__ldcg), never through a stale L1 line.
 // pre_r0 / pre_r1: this thread's row pair t = threadIdx.x, read before the
 // call (pre = true), for the first pass of the fused scan
+template <bool TF32>
 __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const int by, const bool pre = false,
                                           const int pre_r0 = 0, const int pre_r1 = 0) {
   __syncthreads();   // the shared arrays may still be read by the previous tile
@@ -218,6 +237,25 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
   }
   __syncthreads();
   const int ml = tid / 4, kq = (tid % 4) * 16;
+  if constexpr (TF32) {
+    __align__(16) float part[2][16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const float v = s[kq + j][ml];
+      const float h = tf32_rna(v);
+      part[0][j] = h;
+      part[1][j] = tf32_rna(v - h);   // v - h is exact in FP32
+    }
+    float* out = static_cast<float*>(a.out[which]);
+#pragma unroll
+    for (int pc = 0; pc < 2; ++pc) {
+      const uint4* src = reinterpret_cast<const uint4*>(part[pc]);
+      uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)pc * cols + m0 + ml) * a.Kp + k0 + kq);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dst[q] = src[q];
+    }
+    return;
+  }
   __align__(16) __nv_bfloat16 part[3][16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) {
@@ -230,7 +268,7 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
     part[1][j] = mid;
     part[2][j] = __float2bfloat16_rn(r2);
   }
-  __nv_bfloat16* out = a.out[which];
+  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.out[which]);
   const int npieces = nseg == 3 ? 2 : 3;
   // unrolled over the three possible pieces so `part` stays in registers
 #pragma unroll
@@ -244,10 +282,11 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
   }
 }
 
+template <bool TF32>
 __global__ void __launch_bounds__(256) k_prep(const PrepArgs a) {
   CUTQC_PDL_WAIT();     // row statistics come from the previous kernel
   CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
-  prep_tile(a, blockIdx.x, blockIdx.y);
+  prep_tile<TF32>(a, blockIdx.x, blockIdx.y);
 }
 
 // ---- row statistics + compaction + operand preparation in one launch -----
@@ -307,6 +346,7 @@ __device__ __forceinline__ void stats_row(const float* __restrict__ row, int64_t
   }
 }
 
+template <bool TF32>
 __global__ void __launch_bounds__(256) k_stats_prep(const PrepArgs a, const StatsArgs sa) {
   CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
   // the first 256 row pairs of the compaction are plan data: read them now
@@ -347,7 +387,7 @@ __global__ void __launch_bounds__(256) k_stats_prep(const PrepArgs a, const Stat
   __syncthreads();
   if (!pass) return;
   for (int t = blockIdx.x; t < sa.tilesX * sa.tilesY; t += gridDim.x)
-    prep_tile(a, t % sa.tilesX, t / sa.tilesX, true, pre_r0, pre_r1);
+    prep_tile<TF32>(a, t % sa.tilesX, t / sa.tilesX, true, pre_r0, pre_r1);
 }
 
 // ------------------------------------------------------------ PTX helpers
@@ -411,10 +451,21 @@ __device__ __forceinline__ uint64_t sw64_desc(const void* p) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
+// instruction descriptor: kind::tf32, TF32 x TF32 -> FP32, both K-major
+__host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
@@ -552,10 +603,12 @@ __device__ __forceinline__ bool tc_item(const TcArgs& a, int i, TcItem& it) {
 // TK: also keep the fused top-32 (a separate instantiation, so the plain
 // contraction carries none of its code).  tmBh: the B operand map with a
 // 128-row box, for half-width items.
-template <bool TK>
+template <bool TK, bool TF32>
 __global__ void __launch_bounds__(THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmBh, const TcArgs a) {
+  // k per stage: 32 bf16 or 16 TF32 values, 64 bytes of every piece row
+  constexpr int KSS = TF32 ? KS / 2 : KS;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGE_AREA);   // 256 bytes of barriers
@@ -594,10 +647,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int kc = *a.kcount;
   const int nseg = *a.nseg;
-  const int npieces = nseg == 3 ? 2 : 3;                    // h, m (x3) or h, m, l (x6)
-  const int stages = nseg == 3 ? 4 : 3;
+  const int npieces = (TF32 || nseg == 3) ? 2 : 3;          // h, m (x3) or h, m, l (x6); TF32: hi, lo
+  const int stages = (TF32 || nseg == 3) ? 4 : 3;
   const uint32_t stage_bytes = (uint32_t)npieces * (A_PIECE + B_PIECE);
-  const int nkb = (kc + KS - 1) / KS;                       // 32-wide k steps
+  const int nkb = (kc + KSS - 1) / KSS;                     // k steps of one stage
 
   if (nkb > 0 && warp == 0) {
     // ---- TMA producer (the warp waits, lane 0 issues): every split piece of
@@ -608,7 +661,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     TcItem it;
     for (int i = 0; ok && tc_item(a, i, it); ++i) {
-      const uint32_t item_bytes = (uint32_t)npieces * (uint32_t)(A_PIECE + it.w * KS * 2);
+      const uint32_t item_bytes = (uint32_t)npieces * (uint32_t)(A_PIECE + it.w * 64);   // 64-byte piece rows
       const CUtensorMap* mapB = it.w == BN ? &tmB : &tmBh;
       for (int kb = 0; kb < nkb; ++kb) {
         ok = __all_sync(0xffffffffu, mbar_wait(&empty[stage], phase ^ 1, abort_flag));
@@ -617,8 +670,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* st = smem + stage * stage_bytes;
           mbar_expect_tx(&full[stage], item_bytes);
           for (int pc = 0; pc < npieces; ++pc) {
-            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KS, pc * a.M + it.tm * BM, &full[stage]);
-            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, mapB, kb * KS, pc * a.N + it.tn * BN + it.n0,
+            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KSS, pc * a.M + it.tm * BM, &full[stage]);
+            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, mapB, kb * KSS, pc * a.N + it.tn * BN + it.n0,
                         &full[stage]);
           }
         }
@@ -639,7 +692,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     TcItem it;
     for (int i = 0; ok && tc_item(a, i, it); ++i) {
-      const uint32_t idesc = idesc_bf16(BM, it.w);
+      const uint32_t idesc = TF32 ? idesc_tf32(BM, it.w) : idesc_bf16(BM, it.w);
       ok = __all_sync(0xffffffffu, mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag));
       if (!ok) break;
       tc_fence_after();
@@ -653,9 +706,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int sg = 0; sg < nseg; ++sg) {
             const uint64_t ad = sw64_desc(st + kPartA[sg] * A_PIECE);
             const uint64_t bd = sw64_desc(st + npieces * A_PIECE + kPartB[sg] * B_PIECE);
+            // two MMAs per product and stage (K = 16 bf16 or 8 TF32: 32 bytes each)
 #pragma unroll
-            for (int k = 0; k < KS / 16; ++k)
-              mma_bf16(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+            for (int k = 0; k < 2; ++k) {
+              if constexpr (TF32)
+                mma_tf32(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+              else
+                mma_bf16(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+            }
           }
           mma_commit(&empty[stage]);
         }
@@ -927,13 +985,16 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-CUtensorMap make_map(const void* base, uint64_t rows, uint64_t inner, uint32_t box_rows) {
+// rows of 64 bytes per box: 32 bf16 or 16 FP32 (TF32) elements
+CUtensorMap make_map(const void* base, uint64_t rows, uint64_t inner, uint32_t box_rows, bool tf32) {
   CUtensorMap m;
+  const uint64_t es = tf32 ? 4 : 2;
   const cuuint64_t dims[2] = {inner, rows};
-  const cuuint64_t strides[1] = {inner * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)KS, box_rows};
+  const cuuint64_t strides[1] = {inner * es};
+  const cuuint32_t box[2] = {(cuuint32_t)(64 / es), box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+  CUresult r = encode_fn()(&m, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                           const_cast<void*>(base), dims, strides, box,
                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) fail(CUTQC_ERR_CUDA, "cuTensorMapEncodeTiled failed");
@@ -959,7 +1020,8 @@ bool tc_supported(const Contraction& c) {
 size_t tc_workspace_bytes(const Contraction& c) {
   const size_t Kp = kpad(c);
   const size_t M = size_t(1) << c.fA, N = size_t(1) << c.fB;
-  return align256(M * 3 * Kp * 2) + align256(N * 3 * Kp * 2) + 256;
+  // per (row, k): 3 bf16 pieces (6 bytes) or 2 TF32 pieces in FP32 containers (8 bytes)
+  return align256(M * Kp * 8) + align256(N * Kp * 8) + 256;
 }
 
 void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s, const TcFusedStats* fused) {
@@ -967,9 +1029,10 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   if (ws_bytes < tc_workspace_bytes(c)) fail(CUTQC_ERR_OOM, "tensor-core workspace too small");
   const int Kp = kpad(c);
   const int64_t M = int64_t(1) << c.fA, N = int64_t(1) << c.fB;
+  const bool tf32 = c.tf32;
   char* w = static_cast<char*>(ws);
-  auto* Ab = reinterpret_cast<__nv_bfloat16*>(w);
-  auto* Bb = reinterpret_cast<__nv_bfloat16*>(w + align256((size_t)M * 3 * Kp * 2));
+  void* Ab = w;
+  void* Bb = w + align256((size_t)M * Kp * 8);
   int* status = c.status;
   if (!status) fail(CUTQC_ERR_ARG, "tensor-core path needs the device status word");
   if (!c.nseg || !c.bound) fail(CUTQC_ERR_ARG, "tensor-core path needs the split count");
@@ -990,7 +1053,7 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   pa.rmaxB = c.rmaxB;
   pa.scale = c.scale;
   pa.split_tol = c.split_tol;
-  pa.nseg_fixed = c.nseg_fixed;
+  pa.nseg_fixed = tf32 ? 3 : c.nseg_fixed;
   pa.kcount = c.kcount;
   pa.nseg = c.nseg;
   pa.bound = c.bound;
@@ -1015,17 +1078,18 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
     sa.status = status;
     sa.tilesX = (int)((M + N) / 64);
     sa.tilesY = Kp / 64;
-    static int coop_blocks = 0;   // resident blocks per SM
+    static int coop_blocks[2] = {0, 0};   // resident blocks per SM (bf16, TF32 instantiation)
     static int coop_sms = 0;
-    if (!coop_blocks) {
+    if (!coop_blocks[tf32]) {
       int dev = 0;
       CUTQC_CUDA(cudaGetDevice(&dev));
       CUTQC_CUDA(cudaDeviceGetAttribute(&coop_sms, cudaDevAttrMultiProcessorCount, dev));
-      CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&coop_blocks, k_stats_prep, 256, 0));
-      if (coop_blocks < 1) fail(CUTQC_ERR_CUDA, "operand preparation cannot be resident");
+      CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+          &coop_blocks[tf32], tf32 ? k_stats_prep<true> : k_stats_prep<false>, 256, 0));
+      if (coop_blocks[tf32] < 1) fail(CUTQC_ERR_CUDA, "operand preparation cannot be resident");
     }
     const int64_t want = std::max<int64_t>(sa.rows[0] + sa.rows[1], (int64_t)sa.tilesX * sa.tilesY);
-    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)coop_blocks * coop_sms);
+    const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)coop_blocks[tf32] * coop_sms);
     CUTQC_CUDA(cudaMemsetAsync(fused->barrier, 0, sizeof(unsigned), s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -1037,7 +1101,10 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_stats_prep, pa, sa));
+    if (tf32)
+      CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_stats_prep<true>, pa, sa));
+    else
+      CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_stats_prep<false>, pa, sa));
     count_launch();
     check_launch("k_stats_prep");
   } else {
@@ -1046,15 +1113,21 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
       cc.sum_zero = c.sum;
       launch_compact(cc, s);
     }
-    CUTQC_CUDA(launch_pdl(k_prep, dim3((unsigned)((M + N) / 64), (unsigned)(Kp / 64)), dim3(256), 0, s, pa));
+    const dim3 pg((unsigned)((M + N) / 64), (unsigned)(Kp / 64));
+    if (tf32)
+      CUTQC_CUDA(launch_pdl(k_prep<true>, pg, dim3(256), 0, s, pa));
+    else
+      CUTQC_CUDA(launch_pdl(k_prep<false>, pg, dim3(256), 0, s, pa));
     count_launch();
     check_launch("k_prep");
   }
 
-  // three pieces of each operand stacked along rows: [piece * rows + row][k]
-  const CUtensorMap tmA = make_map(Ab, (uint64_t)M * 3, (uint64_t)Kp, BM);
-  const CUtensorMap tmB = make_map(Bb, (uint64_t)N * 3, (uint64_t)Kp, BN);
-  const CUtensorMap tmBh = make_map(Bb, (uint64_t)N * 3, (uint64_t)Kp, BN / 2);
+  // the pieces of each operand stacked along rows: [piece * rows + row][k]
+  // (three bf16 pieces, or two TF32 pieces)
+  const uint64_t np = tf32 ? 2 : 3;
+  const CUtensorMap tmA = make_map(Ab, (uint64_t)M * np, (uint64_t)Kp, BM, tf32);
+  const CUtensorMap tmB = make_map(Bb, (uint64_t)N * np, (uint64_t)Kp, BN, tf32);
+  const CUtensorMap tmBh = make_map(Bb, (uint64_t)N * np, (uint64_t)Kp, BN / 2, tf32);
   TcArgs a;
   a.Kp = Kp;
   a.M = (int)M;
@@ -1082,8 +1155,14 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   static int sms = 0;
   static bool attr = false;
   if (!attr) {
-    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES));
+    CUTQC_CUDA(cudaFuncSetAttribute(k_tc_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SMEM_BYTES));
     int dev = 0;
     CUTQC_CUDA(cudaGetDevice(&dev));
     CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1093,10 +1172,9 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   const int grid = tiles < sms ? tiles : sms;
   cudaEvent_t ev = nullptr;
   if (c.profile) prof_begin(s, &ev);
-  if (a.topk_v)
-    CUTQC_CUDA(launch_pdl(k_tc_gemm<true>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, tmBh, a));
-  else
-    CUTQC_CUDA(launch_pdl(k_tc_gemm<false>, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, tmBh, a));
+  auto* kern = a.topk_v ? (tf32 ? k_tc_gemm<true, true> : k_tc_gemm<true, false>)
+                        : (tf32 ? k_tc_gemm<false, true> : k_tc_gemm<false, false>);
+  CUTQC_CUDA(launch_pdl(kern, dim3(grid), dim3(THREADS), SMEM_BYTES, s, tmA, tmB, tmBh, a));
   count_launch();
   check_launch("k_tc_gemm");
   if (c.topk_nlists) *c.topk_nlists = c.topk_v ? grid * EPI_WARPS : 0;

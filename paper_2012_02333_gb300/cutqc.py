@@ -37,7 +37,9 @@ CUTQC_AUTO = 0
 CUTQC_CC = 1
 CUTQC_TC_BF16X3 = 2
 CUTQC_TC_BF16X6 = 3
-ALGOS = {"auto": CUTQC_AUTO, "cc": CUTQC_CC, "tc_bf16x3": CUTQC_TC_BF16X3, "tc_bf16x6": CUTQC_TC_BF16X6}
+CUTQC_TC_TF32X3 = 4
+ALGOS = {"auto": CUTQC_AUTO, "cc": CUTQC_CC, "tc_bf16x3": CUTQC_TC_BF16X3, "tc_bf16x6": CUTQC_TC_BF16X6,
+         "tc_tf32x3": CUTQC_TC_TF32X3}
 CUTQC_LOSS_NONE = 0
 CUTQC_LOSS_MAXCUT = 1
 
@@ -74,6 +76,8 @@ _lib.cutqc_simulate_subcircuit.argtypes = [C.POINTER(cutqc_gate), C.c_int32, C.c
                                            C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int32),
                                            C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]
 _lib.cutqc_reconstruct_fd_noalloc.argtypes = [C.POINTER(cutqc_problem), C.c_void_p, C.c_void_p, C.c_void_p]
+_lib.cutqc_reconstruct_fd_slab.argtypes = [C.POINTER(cutqc_problem), C.c_int32, C.c_int64, C.c_void_p, C.c_int32,
+                                           C.c_void_p, C.c_void_p]
 _lib.cutqc_profile.argtypes = [C.c_int32]
 _lib.cutqc_last_split.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double)]
 _lib.cutqc_profile_read.argtypes = [C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -92,7 +96,7 @@ _lib.cutqc_selftest_wait.argtypes = [C.c_int32, C.c_void_p]
 _lib.cutqc_last_error.restype = C.c_char_p
 _lib.cutqc_launch_count.restype = C.c_int64
 _lib.cutqc_last_algo.restype = C.c_int32
-for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
+for _f in ("cutqc_reconstruct_fd", "cutqc_reconstruct_fd_slab", "cutqc_reconstruct_dd", "cutqc_reconstruct_backward",
            "cutqc_simulate_subcircuit", "cutqc_profile", "cutqc_profile_read", "cutqc_last_split",
            "cutqc_reconstruct_fd_noalloc", "cutqc_device_status", "cutqc_selftest_wait", "cutqc_attribute",
            "cutqc_attribute_merged", "cutqc_distance", "cutqc_sample", "cutqc_cut_search"):
@@ -275,6 +279,22 @@ def cutqc_reconstruct_fd(problems: Sequence[Problem], outs: Sequence[torch.Tenso
             raise ValueError("sum_p must be a CUDA float64 tensor of n_problems entries")
         sp = sum_p.data_ptr()
     _check(_lib.cutqc_reconstruct_fd(parr, n, optr, ALGOS[algo], sp, _stream_ptr(stream)))
+
+
+def cutqc_reconstruct_fd_slab(problem: Problem, slab_bits: int, slab_index: int, out: torch.Tensor,
+                              algo: str = "auto", sum_p: Optional[torch.Tensor] = None, stream=None) -> None:
+    """Binding of cutqc_reconstruct_fd_slab: the 2^(n - slab_bits) outputs whose
+    slab_bits most significant bits read slab_index, and their FP64 sum."""
+    if out.dtype != problem.dtype or out.numel() != 2 ** (problem.n_qubits - slab_bits) or \
+            not out.is_contiguous() or not (out.is_cuda or out.is_pinned()):
+        raise ValueError("out must be a contiguous CUDA or pinned tensor of 2^(n - slab_bits) entries")
+    sp = None
+    if sum_p is not None:
+        if sum_p.dtype != torch.float64 or not sum_p.is_cuda:
+            raise ValueError("sum_p must be a CUDA float64 tensor")
+        sp = sum_p.data_ptr()
+    _check(_lib.cutqc_reconstruct_fd_slab(C.byref(problem.c), int(slab_bits), int(slab_index),
+                                          C.c_void_p(out.data_ptr()), ALGOS[algo], sp, _stream_ptr(stream)))
 
 
 def reconstruct_fd(cc: circuits.CutCircuit, tensors: Sequence[torch.Tensor], algo: str = "auto",

@@ -71,11 +71,12 @@ def test_dd_fp32_auto(env, name, strategy):
     check_run(env, cc, T, np.float32, "auto", na, 6, strategy, 1e-6)
 
 
-def test_dd_active_covering_tensor_core_shapes(env):
+@pytest.mark.parametrize("algo", ["auto", "tc_tf32x3"])
+def test_dd_active_covering_tensor_core_shapes(env, algo):
     """Enough active qubits that the final contraction takes the tensor-core
     path (2^8 x 2^8 bins) with merged and zoomed qubits interleaved."""
     cc, T = oracle_case("grid4x5_k5", cases.SMALL["grid4x5_k5"])
-    check_run(env, cc, T, np.float32, "auto", 16, 3, "bfs", 1e-6)
+    check_run(env, cc, T, np.float32, algo, 16, 3, "bfs", 1e-6)
 
 
 def test_figure7_bv_on_gpu(env):

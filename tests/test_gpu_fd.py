@@ -141,7 +141,7 @@ def test_misaligned_output_is_rejected(env, sup):
 _sup_ref = {}
 
 
-@pytest.mark.parametrize("algo", ["cc", "auto", "tc_bf16x3"])
+@pytest.mark.parametrize("algo", ["cc", "auto", "tc_bf16x3", "tc_tf32x3"])
 def test_supremacy_4x6_full_size(env, sup, algo):
     """Full size (2^24 outputs, the launch configuration the benchmark times):
     every output against the oracle's plain FP64 sum over all 256 Kronecker
@@ -180,12 +180,12 @@ def test_supremacy_4x6_full_size(env, sup, algo):
         k_eff += pl1 > 0
     total *= 2.0 ** -cc.n_cuts
     s_l1 *= 2.0 ** -cc.n_cuts
-    tol = (3 * 2.0 ** -18 + k_eff * 2.0 ** -23) * s_l1 + 1e-9
+    tol = (3 * 2.0 ** -18 + k_eff * 2.0 ** -23) * s_l1 + 1e-9   # covers every split form
     assert abs(float(sp.item()) - total) <= tol, (float(sp.item()) - total, tol)
     assert abs(float(sp.item()) - 1.0) <= tol + 1e-6    # trace preservation of the uncut circuit
 
 
-@pytest.mark.parametrize("algo", ["tc_bf16x3", "tc_bf16x6"])
+@pytest.mark.parametrize("algo", ["tc_bf16x3", "tc_bf16x6", "tc_tf32x3"])
 def test_large_output_sampled(env, algo):
     """2^26 outputs (256 MiB of FP32, larger than L2): a 26-qubit HWEA chain
     cut once into two 13-qubit halves.  At this size the tensor-core epilogue

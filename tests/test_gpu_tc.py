@@ -3,8 +3,9 @@ oracle (run on the same FP32 tensors).
 
 BF16 x6 must meet 1e-6 max abs error everywhere; BF16 x3 must stay within its
 a-priori bound 3 * 2^-18 * S + 1e-7 with S = 2^-K sum_e max|A_e| max|B_e|
-(the bound the library's automatic choice uses); the automatic form must meet
-1e-6 everywhere."""
+(the bound the library's automatic choice uses); TF32 x3 within
+3 * 2^-22 * S + 1e-7 and 1e-6; the automatic form must meet 1e-6
+everywhere."""
 import os
 import sys
 
@@ -84,3 +85,28 @@ def test_tc_and_cc_agree_on_repeat(env):
     c, _ = cutqc.reconstruct_fd(cc, ts, algo="cc")
     assert torch.equal(a, b)
     assert (a.double() - c.double()).abs().max().item() <= 1e-6
+
+
+@pytest.mark.parametrize("name", TC_CASES)
+def test_tc_tf32x3_within_bound_and_1e6(env, name):
+    """TF32 x3 (hi = tf32(x), lo = tf32(x - hi), products hh + hl + lh): the
+    dropped lo*lo term and the rounding of lo bound the error per product by
+    about 3 * 2^-22 |a||b|."""
+    torch, cutqc = env
+    cc, T32, ref, got, s, used = run(env, name, "tc_tf32x3")
+    assert used == cutqc.CUTQC_TC_TF32X3
+    bound = 3 * 2.0 ** -22 * split_bound(cc, T32) + 1e-7
+    err = np.abs(got - ref).max()
+    assert err <= min(bound, 1e-6), f"err {err:.3e} > bound {bound:.3e}"
+    assert s == pytest.approx(ref.sum(), abs=1e-6)
+    nseg, _ = cutqc.last_split()
+    assert nseg == 3
+
+
+def test_tc_tf32x3_more_accurate_than_bf16x3(env):
+    """On the same shape TF32 x3 is at least as accurate as BF16 x3 (its
+    dropped terms are 16 times smaller)."""
+    torch, cutqc = env
+    _, _, ref, g3, _, _ = run(env, "grid4x5_k5", "tc_bf16x3")
+    _, _, _, gt, _, _ = run(env, "grid4x5_k5", "tc_tf32x3")
+    assert np.abs(gt - ref).max() <= np.abs(g3 - ref).max() + 1e-12
