@@ -381,16 +381,17 @@ static Step make_step(Plan& P, int ia, int ib, int result, const std::vector<int
 
 // Plan a problem whose nodes are given (original subcircuits, or merged DD
 // tensors) with output positions already in the nodes' bits.
-static void plan_contractions(Plan& P, int ncuts) {
-  std::vector<int> live;
-  for (size_t i = 0; i < P.nodes.size(); ++i) live.push_back((int)i);
+// One greedy merge among the live nodes: the connected pair whose merged
+// tensor is smallest (ties: lowest indices; an unconnected pair only when no
+// pair shares a cut), appended as a batched group-build step.
+static void merge_best_pair(Plan& P, std::vector<int>& live, int ncuts) {
   auto shared = [&](int i, int j) {
     int s = 0;
     for (int c : P.nodes[i].cuts)
       if (std::find(P.nodes[j].cuts.begin(), P.nodes[j].cuts.end(), c) != P.nodes[j].cuts.end()) ++s;
     return s;
   };
-  while (live.size() > 2) {
+  {
     // the connected pair with the smallest merged tensor (ties: lowest indices)
     double best = -1;
     int bi = -1, bj = -1;
@@ -426,6 +427,12 @@ static void plan_contractions(Plan& P, int ncuts) {
     live.erase(std::find(live.begin(), live.end(), bj));
     live.push_back(r);
   }
+}
+
+static void plan_contractions(Plan& P, int ncuts) {
+  std::vector<int> live;
+  for (size_t i = 0; i < P.nodes.size(); ++i) live.push_back((int)i);
+  while (live.size() > 2) merge_best_pair(P, live, ncuts);
   if (live.size() == 1) {
     // no partner: contract with a constant 1 node (f = 0, no cuts)
     Node one;
@@ -544,6 +551,33 @@ static void build_fd_plan(Plan& P, const cutqc_problem* p) {
     P.nodes.push_back(nd);
   }
   plan_contractions(P, p->n_cuts);
+  finalize_plan(P);
+}
+
+// Adjoint plan for subcircuit c of a circuit cut into more than two
+// subcircuits: every other subcircuit merged into one group node R by the
+// same greedy group builds as the forward plan (recomputed, never stored
+// between calls), then the pair (c, R) as the last step, whose row pairs and
+// deposit tables the adjoint contraction of G against R uses.  Every cut of c
+// joins it to R, so each row of c and of R appears in exactly one term.
+static void build_bwd_plan(Plan& P, const cutqc_problem* p, int csub) {
+  P.n_out = p->n_qubits;
+  P.K = p->n_cuts;
+  P.dtype = p->dtype;
+  for (int c = 0; c < p->n_sub; ++c) {
+    const cutqc_subcircuit& s = p->sub[c];
+    Node nd;
+    nd.orig = c;
+    for (int j = 0; j < s.k_in; ++j) nd.cuts.push_back(s.in_cut[j]);
+    for (int j = 0; j < s.k_out; ++j) nd.cuts.push_back(s.out_cut[j]);
+    for (int i = 0; i < s.n_eff; ++i) nd.bits.push_back(s.out_qubit[i]);
+    P.nodes.push_back(nd);
+  }
+  std::vector<int> live;
+  for (int c = 0; c < p->n_sub; ++c)
+    if (c != csub) live.push_back(c);
+  while (live.size() > 1) merge_best_pair(P, live, p->n_cuts);
+  P.steps.push_back(make_step(P, csub, live[0], -1, {}, p->n_cuts));
   finalize_plan(P);
 }
 
@@ -720,9 +754,12 @@ bool is_device_memory_here(const void* p) {
 static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
                       cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr,
-                      size_t topk_back_off = SIZE_MAX, int* topk_nlists = nullptr) {
+                      size_t topk_back_off = SIZE_MAX, int* topk_nlists = nullptr, bool groups_only = false,
+                      char** base_out = nullptr) {
   // topk_back_off: where in the back region a tensor-core final contraction
-  // may leave its fused top-32 lists (*topk_nlists of them; 0 when it did not)
+  // may leave its fused top-32 lists (*topk_nlists of them; 0 when it did not).
+  // groups_only: run the group builds but not the last step (the adjoint
+  // reads the group tensors at *base_out + P.ws_node[...])
   if (topk_nlists) *topk_nlists = 0;
   size_t tc_ws = 0;
   std::vector<Contraction> cs(P.steps.size());
@@ -770,6 +807,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   }
   char* ws = ws_given ? ws_given : static_cast<char*>(workspace(ds, front + need + back));
   base = ws + front;
+  if (base_out) *base_out = base;
   const std::vector<const void*> orig_tensor = pre(ws);
   auto node_ptr = [&](int i) -> const void* {
     const Node& nd = P.nodes[i];
@@ -801,6 +839,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     const Step& st = P.steps[i];
     Contraction& c = cs[i];
     const bool last_step = (i + 1 == P.steps.size());
+    if (last_step && groups_only) break;
     const bool both_new = !flagged[st.a] || !flagged[st.b];
     TcFusedStats fstats{};
     bool fused_stats = false;
@@ -1362,10 +1401,12 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
     validate(problem, true);
     const cutqc_problem* p = problem;
     if (p->n_qubits > kMaxFD) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs n_qubits <= 34");
-    if (p->n_sub != 2) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint supports circuits cut into two subcircuits");
-    if (!grad_tensor || !grad_tensor[0] || !grad_tensor[1]) fail(CUTQC_ERR_ARG, "NULL gradient pointer");
-    need_aligned(grad_tensor[0], 16, "grad_tensor[0]");
-    need_aligned(grad_tensor[1], 16, "grad_tensor[1]");
+    if (p->n_sub < 2) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs at least two subcircuits");
+    if (!grad_tensor) fail(CUTQC_ERR_ARG, "NULL gradient pointer");
+    for (int c = 0; c < p->n_sub; ++c) {
+      if (!grad_tensor[c]) fail(CUTQC_ERR_ARG, "NULL gradient pointer");
+      need_aligned(grad_tensor[c], 16, "grad_tensor[c]");
+    }
     need_aligned(grad_out, 16, "grad_out");
     need_aligned(loss_value, 8, "loss_value");
     const bool maxcut = loss && loss->kind == CUTQC_LOSS_MAXCUT;
@@ -1374,6 +1415,109 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
     if (maxcut && (loss->n_edges < 0 || (loss->n_edges && !loss->edges))) fail(CUTQC_ERR_ARG, "bad edge list");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     DeviceState& ds = device_state();
+    const double scale = std::ldexp(1.0, -p->n_cuts);
+    // MaxCut bookkeeping of a pair of sides: the edges inside each side and
+    // the bridge endpoints, as index bits (least significant = 0)
+    struct Sides {
+      BwdEdges inA{}, inB{};
+      BwdBits brA{}, brB{};
+    };
+    auto split_edges = [&](const Node& A, const Node& B) {
+      Sides sd;
+      const int fA = A.f(), fB = B.f();
+      std::vector<int> side(p->n_qubits, -1), bit(p->n_qubits, -1);
+      for (int i = 0; i < fA; ++i) {
+        side[A.bits[fA - 1 - i]] = 0;
+        bit[A.bits[fA - 1 - i]] = i;
+      }
+      for (int i = 0; i < fB; ++i) {
+        side[B.bits[fB - 1 - i]] = 1;
+        bit[B.bits[fB - 1 - i]] = i;
+      }
+      for (int k = 0; k < loss->n_edges; ++k) {
+        const int u = loss->edges[2 * k], v = loss->edges[2 * k + 1];
+        if (u < 0 || v < 0 || u >= p->n_qubits || v >= p->n_qubits || u == v) fail(CUTQC_ERR_ARG, "bad edge");
+        if (side[u] == side[v]) {
+          BwdEdges& E = side[u] == 0 ? sd.inA : sd.inB;
+          if (E.n >= 96) fail(CUTQC_ERR_UNSUPPORTED, "more than 96 edges inside one side");
+          E.p[E.n] = bit[u];
+          E.q[E.n] = bit[v];
+          ++E.n;
+        } else {
+          if (sd.brA.n >= 16) fail(CUTQC_ERR_UNSUPPORTED, "more than 16 edges between the sides");
+          const int ua = side[u] == 0 ? u : v, ub = side[u] == 0 ? v : u;
+          sd.brA.p[sd.brA.n++] = bit[ua];
+          sd.brB.p[sd.brB.n++] = bit[ub];
+        }
+      }
+      return sd;
+    };
+    if (p->n_sub > 2) {
+      // every subcircuit c against the group tensor R_c of all the others,
+      // rebuilt by the forward's group builds (recomputation: nothing of the
+      // forward is stored); the workspace is sized for the largest c first so
+      // it is not reallocated while earlier work is in flight
+      std::vector<Plan*> plans(p->n_sub);
+      size_t need = 0;
+      for (int c = 0; c < p->n_sub; ++c) {
+        const std::string key = fd_key(p, 2, nullptr, 0) + "#bwd" + std::to_string(c);
+        plans[c] = &get_plan(ds, key, [&](Plan& P) { build_bwd_plan(P, p, c); });
+        const Step& st = plans[c]->steps.back();
+        const size_t back = maxcut ? align_up((size_t)(2 + 16) * plans[c]->nodes[st.a].rows() * 8) +
+                                         align_up((size_t)(2 + 16) * plans[c]->nodes[st.b].rows() * 8)
+                                   : 0;
+        size_t b = 0;
+        run_plan(ds, *plans[c], 0, back, [](char*) { return std::vector<const void*>(); }, nullptr, nullptr,
+                 CUTQC_CC, s, nullptr, &b, SIZE_MAX, nullptr, true);
+        need = std::max(need, b);
+      }
+      char* ws = static_cast<char*>(workspace(ds, need));
+      auto originals = [p](char*) {
+        std::vector<const void*> t(p->n_sub);
+        for (int c = 0; c < p->n_sub; ++c) t[c] = p->sub[c].tensor;
+        return t;
+      };
+      for (int c = 0; c < p->n_sub; ++c) {
+        Plan& P = *plans[c];
+        const Step& st = P.steps.back();
+        const Node& A = P.nodes[st.a];
+        const Node& B = P.nodes[st.b];
+        if ((int64_t)st.kmax != A.rows() || (int64_t)st.kmax != B.rows())
+          fail(CUTQC_ERR_SHAPE, "internal: a subcircuit's cuts do not all join it to the rest");
+        char* base = nullptr;
+        char* back = run_plan(ds, P, 0, 0, originals, nullptr, nullptr, CUTQC_CC, s, ws, nullptr, SIZE_MAX, nullptr,
+                              true, &base);
+        const void* TR = B.orig >= 0 ? p->sub[B.orig].tensor : static_cast<const void*>(base + P.ws_node[st.b]);
+        char* dtab = static_cast<char*>(P.dtab);
+        const int32_t* rowC = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
+        const int32_t* rowR = rowC + st.kmax;
+        if (maxcut) {
+          const Sides sd = split_edges(A, B);
+          double* sumsC = reinterpret_cast<double*>(back);
+          double* sumsR = reinterpret_cast<double*>(back + align_up((size_t)(2 + 16) * A.rows() * 8));
+          launch_bwd_rowsums(p->sub[c].tensor, P.dtype, A.rows(), A.f(), sd.inA, sd.brA, sumsC, s);
+          launch_bwd_rowsums(TR, P.dtype, B.rows(), B.f(), sd.inB, sd.brB, sumsR, s);
+          launch_bwd_maxcut_grad(rowC, rowR, st.kmax, A.f(), sd.inA, sd.brA, sumsR, B.rows(), scale, grad_tensor[c],
+                                 P.dtype, s);
+          if (c == 0 && loss_value)
+            launch_bwd_maxcut_loss(rowC, rowR, st.kmax, sumsC, A.rows(), sumsR, B.rows(), sd.brA.n, scale,
+                                   loss_value, s);
+        } else {
+          const uint64_t* depC = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
+          const uint64_t* depR = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
+          launch_bwd_cc(TR, grad_out, rowC, rowR, st.kmax, A.f(), B.f(), depC, depR, scale, grad_tensor[c], P.dtype,
+                        s);
+        }
+      }
+      if (!maxcut && loss_value) {
+        // L = sum_x G(x) p(x) = sum dL/dT_0 . T_0 (p is linear in each tensor)
+        CUTQC_CUDA(cudaMemsetAsync(loss_value, 0, sizeof(double), s));
+        launch_dot(grad_tensor[0], p->sub[0].tensor,
+                   (int64_t(1) << (2 * (p->sub[0].k_in + p->sub[0].k_out))) << p->sub[0].n_eff, p->dtype, loss_value,
+                   s);
+      }
+      return;
+    }
     Plan& P = get_plan(ds, fd_key(p, 0, nullptr, 0), [&](Plan& P) { build_fd_plan(P, p); });
     if (P.steps.size() != 1) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint supports a single final contraction");
     const Step& st = P.steps[0];
@@ -1383,7 +1527,6 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
     if (sa < 0 || sb < 0) fail(CUTQC_ERR_UNSUPPORTED, "the adjoint needs two original subcircuits");
     const int fA = A.f(), fB = B.f();
     const int64_t rowsA = A.rows(), rowsB = B.rows();
-    const double scale = std::ldexp(1.0, -P.K);
     char* dtab = static_cast<char*>(P.dtab);
     const int32_t* rowA = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
     const int32_t* rowB = rowA + st.kmax;

@@ -91,16 +91,19 @@ __global__ void k_dd_merge_warp(const T* __restrict__ Tin, int64_t cols, int a, 
     const T* base = Tin + row * cols + (dep_tab(depAct, nbA, xa) | zoom) + dep_tab(depMrg, nbM, (uint64_t)lane);
     Acc acc{};
     for (int64_t x0 = 0; x0 < nm; x0 += 32 * 16) {
-      T run = T(0);
+      T v[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {   // 16 independent loads in flight per lane
         const int64_t xh = x0 + 32 * r;   // nm is a multiple of 32 (mg >= 5)
-        if (xh < nm) run += base[dep_tab(depMrg, nbM, (uint64_t)xh)];
+        v[r] = xh < nm ? base[dep_tab(depMrg, nbM, (uint64_t)xh)] : T(0);
       }
-      if constexpr (sizeof(T) == 4)
-        acc = ff_add(acc, FF{run, 0.0f});
-      else
-        acc += run;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        if constexpr (sizeof(T) == 4)
+          acc = ff_add(acc, FF{v[r], 0.0f});
+        else
+          acc += v[r];
+      }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -142,13 +145,16 @@ __global__ void k_dd_merge_thread(const T* __restrict__ Tin, int64_t cols, int a
 // ... (one warp instruction covers 32 consecutive float4 of one run, or
 // several whole runs).  With runs of at most 1024 values (PER = float4 per
 // lane <= 8) a group takes 8 / PER outputs per step, so every lane has 8
-// independent loads in flight.  Sums cover up to 32 values in plain FP32
-// (pairwise), everything above in compensated FP32.  `dense`: the active bits
+// independent loads in flight.  Every addition is compensated (TwoSum), so
+// the stored sum plus its compensation term carry the merged value to about
+// FP64 accuracy: the FP64 re-ranking of candidate bins reads them.  `dense`: the active bits
 // are the bits directly above the merged ones, so a run starts at
 // row * cols + zoom + (xa << mg) without the deposit table.  Outputs too few
 // to fill the GPU are split into 2^lnch chunks whose partial sums go to
 // `part` and are combined in chunk order by k_dd_merge_finish.
-__device__ __forceinline__ float sum4(float4 v) { return (v.x + v.y) + (v.z + v.w); }
+__device__ __forceinline__ FF sum4(float4 v) {
+  return ff_add(ff_add(FF{v.x, 0.0f}, FF{v.y, 0.0f}), ff_add(FF{v.z, 0.0f}, FF{v.w, 0.0f}));
+}
 
 template <int G, int PER>
 __global__ void k_dd_merge_run(const float* __restrict__ Tin, int64_t cols, int a, int mg,
@@ -174,48 +180,49 @@ __global__ void k_dd_merge_run(const float* __restrict__ Tin, int64_t cols, int 
   for (int64_t ub = warp * GPW * U; ub < n_units; ub += nwarps * GPW * U) {
     FF acc[U];
     if constexpr (PER > 0) {
-      float t[8];
+      float4 q[8];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         const int64_t u = ub + k * GPW + gi;
         const bool ok = u < n_units;
         const float4* p = unit_ptr(ok ? u : 0);
 #pragma unroll
-        for (int e = 0; e < PER; ++e) t[k * PER + e] = ok ? sum4(__ldcs(p + e * G)) : 0.0f;
+        for (int e = 0; e < PER; ++e) q[k * PER + e] = ok ? __ldcs(p + e * G) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
+      FF t[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) t[j] = sum4(q[j]);
 #pragma unroll
       for (int w = 1; w < PER; w <<= 1)
 #pragma unroll
-        for (int j = 0; j < 8; j += 2 * w) t[j] += t[j + w];
+        for (int j = 0; j < 8; j += 2 * w) t[j] = ff_add(t[j], t[j + w]);
 #pragma unroll
-      for (int k = 0; k < U; ++k) acc[k] = FF{t[k * PER], 0.0f};
+      for (int k = 0; k < U; ++k) acc[k] = t[k * PER];
     } else {
       const int64_t u = ub + gi;
       acc[0] = FF{0.0f, 0.0f};
       if (u < n_units) {
         const float4* p = unit_ptr(u);
         for (int64_t j0 = 0; j0 < per; j0 += 8) {   // per is a power of two >= 16 here
-          float t[8];
+          float4 q[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) t[j] = sum4(__ldcs(p + (j0 + j) * G));
+          for (int j = 0; j < 8; ++j) q[j] = __ldcs(p + (j0 + j) * G);
+          FF t[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) t[j] = sum4(q[j]);
 #pragma unroll
           for (int w = 4; w > 0; w >>= 1)
 #pragma unroll
-            for (int j = 0; j < w; ++j) t[j] += t[j + w];
-          acc[0] = ff_add(acc[0], FF{t[0], 0.0f});
+            for (int j = 0; j < w; ++j) t[j] = ff_add(t[j], t[j + w]);
+          acc[0] = ff_add(acc[0], t[0]);
         }
       }
     }
-    // across the group: plain FP32 while a partial covers <= 32 values
+    // across the group
 #pragma unroll
     for (int off = 1; off < G; off <<= 1) {
 #pragma unroll
-      for (int k = 0; k < U; ++k) {
-        if (PER > 0 && 8 * PER * off <= 32)
-          acc[k].s += __shfl_xor_sync(0xffffffffu, acc[k].s, off);
-        else
-          acc[k] = ff_add(acc[k], ff_shfl_xor(acc[k], off));
-      }
+      for (int k = 0; k < U; ++k) acc[k] = ff_add(acc[k], ff_shfl_xor(acc[k], off));
     }
 #pragma unroll
     for (int k = 0; k < U; ++k) {

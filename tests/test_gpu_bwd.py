@@ -14,6 +14,9 @@ from test_gpu_fd import env, oracle_case, to_dev  # noqa: E402,F401
 pytestmark = pytest.mark.gpu
 
 TWO_SUB = ["hwea10_k1", "bv6_k1", "grid3x4_k3", "qaoa8_k4", "hwea16_s2", "grid4x5_k5"]
+# three and four subcircuits: each subcircuit against the group tensor of the
+# others, rebuilt by the forward's group builds
+MULTI_SUB = ["hwea9_s3", "grid4x4_s4"]
 
 
 def rel_err(got, want):
@@ -21,7 +24,7 @@ def rel_err(got, want):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("name", TWO_SUB)
+@pytest.mark.parametrize("name", TWO_SUB + MULTI_SUB)
 def test_backward_explicit_G(env, name, dtype):
     torch, cutqc = env
     from oracle import reconstruct as rc
@@ -43,7 +46,7 @@ def test_backward_explicit_G(env, name, dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("name", ["qaoa8_k4", "hwea10_k1", "grid3x4_k3"])
+@pytest.mark.parametrize("name", ["qaoa8_k4", "hwea10_k1", "grid3x4_k3"] + MULTI_SUB)
 def test_backward_maxcut(env, name, dtype):
     torch, cutqc = env
     from oracle import reconstruct as rc
@@ -65,13 +68,14 @@ def test_backward_maxcut(env, name, dtype):
     assert loss.item() == pytest.approx(brute, abs=1e-5 if dtype == "f32" else 1e-11)
 
 
-def test_backward_central_differences_fp64(env):
+@pytest.mark.parametrize("name", ["qaoa8_k4", "grid4x4_s4"])
+def test_backward_central_differences_fp64(env, name):
     """L is linear in each tensor: FP64 central differences (h = 1e-6) of the
     library's own loss value match its gradient."""
     torch, cutqc = env
-    cc, Ts = oracle_case("qaoa8_k4", cases.SMALL["qaoa8_k4"])
+    cc, Ts = oracle_case(name, cases.SMALL[name])
     ts = to_dev(torch, Ts, torch.float64)
-    edges = cc.edges
+    edges = getattr(cc, "edges", None) or [(q, q + 1) for q in range(cc.n - 1)] + [(0, cc.n - 1)]
 
     def loss_of(tensors):
         problem = cutqc.Problem.from_cut(cc, tensors)
@@ -83,7 +87,7 @@ def test_backward_central_differences_fp64(env):
     L0, grads = loss_of(ts)
     h = 1e-6
     rng = np.random.default_rng(1)
-    for c in range(2):
+    for c in range(len(ts)):
         for i in rng.choice(ts[c].numel(), 6, replace=False):
             tp = [t.clone() for t in ts]
             tm = [t.clone() for t in ts]
@@ -112,15 +116,16 @@ def test_autograd_functions(env):
 
 def test_qaoa30_maxcut_full_size(env):
     """The 30-qubit QAOA MaxCut workload (two 15-node clusters, 2 bridges,
-    K = 4, FP32 tensors from the GPU simulator): sampled gradient entries
-    against the oracle's chain rule, Euler's identity L = sum T * dL/dT for
-    each side, and FP64 central differences of the loss."""
+    K = 4; the oracle's simulated tensors rounded to FP32 for both sides): 64
+    sampled gradient entries per subcircuit against the oracle's chain rule,
+    Euler's identity L = sum T * dL/dT for each side, and FP64 central
+    differences of the loss."""
     torch, cutqc = env
     from oracle import reconstruct as rc
     from paper_2012_02333_gb300 import circuits as C
-    cc = C.qaoa_2cluster(15, 0)
+    cc, Ts = oracle_case("qaoa30", lambda: C.qaoa_2cluster(15, 0))
     assert cc.n == 30 and cc.n_cuts == 4
-    ts = cutqc.simulate_tensors(cc, torch.float32)
+    ts = to_dev(torch, [T.astype(np.float32) for T in Ts], torch.float32)
     problem = cutqc.Problem.from_cut(cc, ts)
     grads = [torch.empty_like(t) for t in ts]
     loss = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -135,7 +140,7 @@ def test_qaoa30_maxcut_full_size(env):
     rng = np.random.default_rng(3)
     for c, s in enumerate(cc.subs):
         rows = 4 ** (s.k_in + s.k_out)
-        for _ in range(6):
+        for _ in range(64):
             r, x = int(rng.integers(rows)), int(rng.integers(2 ** s.n_eff))
             want = rc.grad_entry(cc.subs, T64, cc.n, cc.n_cuts, c, r, x, f)
             got = g64[c][r * 2 ** s.n_eff + x]
