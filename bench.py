@@ -47,7 +47,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM traffic (read + write bytes) of one k_tc_gemm launch on this workload from
 # the ncu capture summarised in profiles/k_tc_gemm_supremacy_4x6_k4.md, valid while
 # the kernel source is unchanged (first 16 hex digits of its SHA-256)
-TRAFFIC_TC = {"sha256_16": "5dc2ea10a6849376", "bytes": 15.93e6}
+TRAFFIC_TC = {"sha256_16": "37e9963e0610294d", "bytes": 15.709e6}
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 

@@ -114,9 +114,7 @@ print("NOALLOC_FRESH_OK")
 
 def test_noalloc_in_a_fresh_process_allocates_nothing(env):
     code = _FRESH.format(root=ROOT, tests=os.path.dirname(os.path.abspath(__file__)))
-    e = dict(os.environ)
-    e["CUDA_MODULE_LOADING"] = "EAGER"   # the library's code is loaded with the context, not at a call
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=e, cwd=ROOT, timeout=600)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode == 0 and "NOALLOC_FRESH_OK" in r.stdout, r.stdout[-3000:] + r.stderr[-3000:]
 
 
