@@ -216,6 +216,9 @@ struct DeviceState {
   int* status = nullptr;          // device status word written by kernels with bounded waits
   void* aux = nullptr;            // distance / sampling scratch (zeroed when (re)allocated)
   size_t aux_bytes = 0;
+  // device work lists of batched low-rank contractions, per batch (they point
+  // into the workspace, so they go whenever the captured graphs go)
+  std::unordered_map<std::string, void*> lr_tables;
 };
 static std::map<int, DeviceState> g_dev;
 
@@ -287,6 +290,9 @@ static void drop_graphs(DeviceState& ds) {
   for (auto& kv : ds.graphs)
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
   ds.graphs.clear();
+  for (auto& kv : ds.lr_tables)
+    if (kv.second) cudaFree(kv.second);
+  ds.lr_tables.clear();
 }
 
 static void* workspace(DeviceState& ds, size_t bytes) {
@@ -755,7 +761,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
                       const std::function<std::vector<const void*>(char*)>& pre, void* out, double* sum, int algo,
                       cudaStream_t s, char* ws_given = nullptr, size_t* bytes_only = nullptr,
                       size_t topk_back_off = SIZE_MAX, int* topk_nlists = nullptr, bool groups_only = false,
-                      char** base_out = nullptr) {
+                      char** base_out = nullptr, std::vector<Contraction>* defer_lowrank = nullptr) {
   // topk_back_off: where in the back region a tensor-core final contraction
   // may leave its fused top-32 lists (*topk_nlists of them; 0 when it did not).
   // groups_only: run the group builds but not the last step (the adjoint
@@ -914,6 +920,10 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     }
     if (final_step && use_tc_final)
       launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s, fused_stats ? &fstats : nullptr);
+    else if (final_step && lowrank_eligible(c) && !c.out_host && defer_lowrank)
+      defer_lowrank->push_back(c);   // the caller launches every deferred problem together
+    else if (final_step && lowrank_eligible(c))
+      launch_lowrank(c, s);
     else
       launch_cc_gemm(c, s);
     if (final_step) g_last_algo = use_tc_final ? (algo == CUTQC_AUTO ? CUTQC_TC_BF16X3 : algo) : CUTQC_CC;
@@ -997,10 +1007,37 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
   auto algo_of = [&](int i) {
     return (algo == CUTQC_AUTO && plans[i]->tuned == CUTQC_CC) ? (int)CUTQC_CC : algo;
   };
+  // Low-rank CUDA-core final contractions are not launched per problem: they
+  // are collected (per dtype) and run as one launch over a device work list.
+  std::vector<Contraction> lr[2];
+  auto launch_deferred = [&](cudaStream_t st) {
+    for (int d = 0; d < 2; ++d) {
+      if (lr[d].empty()) continue;
+      const std::string tk = gk + "#lr" + std::to_string(d);
+      std::vector<char> host;
+      int64_t items = 0;
+      lowrank_batch_tables(lr[d], host, &items);
+      auto it2 = ds.lr_tables.find(tk);
+      if (it2 == ds.lr_tables.end()) {
+        // first (eager) call: upload the work list; captured replays reuse it
+        void* dev = nullptr;
+        CUTQC_CUDA(cudaMalloc(&dev, host.size()));
+        CUTQC_CUDA(cudaMemcpy(dev, host.data(), host.size(), cudaMemcpyHostToDevice));
+        it2 = ds.lr_tables.emplace(tk, dev).first;
+      }
+      launch_lowrank_batch(it2->second, lr[d], items, st);
+      lr[d].clear();
+    }
+  };
+  auto run_one = [&](int i, cudaStream_t st, char* w) {
+    std::vector<Contraction> d;
+    run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i), st, w,
+             nullptr, SIZE_MAX, nullptr, false, nullptr, &d);
+    for (const Contraction& c : d) lr[c.dtype == CUTQC_F64 ? 1 : 0].push_back(c);
+  };
   // eager run of the whole batch on the caller's stream
-  for (int i = 0; i < n; ++i)
-    run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i), s,
-             ws + off[i]);
+  for (int i = 0; i < n; ++i) run_one(i, s, ws + off[i]);
+  launch_deferred(s);
   // capture the same launches over parallel branches for later calls
   if (!ds.fork) {
     for (int b = 0; b < kBranches; ++b) {
@@ -1015,13 +1052,12 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     CUTQC_CUDA(cudaStreamBeginCapture(ds.branch[0], cudaStreamCaptureModeThreadLocal));
     CUTQC_CUDA(cudaEventRecord(ds.fork, ds.branch[0]));
     for (int b = 1; b < kBranches; ++b) CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[b], ds.fork, 0));
-    for (int i = 0; i < n; ++i)
-      run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i),
-               ds.branch[i % kBranches], ws + off[i]);
+    for (int i = 0; i < n; ++i) run_one(i, ds.branch[i % kBranches], ws + off[i]);
     for (int b = 1; b < kBranches; ++b) {
       CUTQC_CUDA(cudaEventRecord(ds.join[b], ds.branch[b]));
       CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.join[b], 0));
     }
+    launch_deferred(ds.branch[0]);
     CUTQC_CUDA(cudaStreamEndCapture(ds.branch[0], &graph));
   } catch (...) {
     g_capturing = false;

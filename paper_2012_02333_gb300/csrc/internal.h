@@ -157,6 +157,16 @@ void launch_row_stats(const void* T, int dtype, int rows, int f, int32_t* flags,
 void launch_compact(const Contraction& c, cudaStream_t s);
 void launch_cc_gemm(const Contraction& c, cudaStream_t s);
 void launch_fill_zero(void* p, size_t bytes, cudaStream_t s);
+// Low-rank final contraction (at most 16 kept terms, the N side owning the
+// two lowest output bits): one problem, or a device list of problems and work
+// items built by lowrank_batch_tables (all of one dtype) in one launch.
+bool lowrank_eligible(const Contraction& c);
+int64_t lowrank_items(const Contraction& c);
+void launch_lowrank(const Contraction& c, cudaStream_t s);
+size_t lowrank_batch_bytes(const std::vector<Contraction>& cs);
+void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>& host, int64_t* n_items);
+void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>& cs, int64_t n_items,
+                          cudaStream_t s);
 
 // k_attr.cu: tensor T[a][b][x] of one subcircuit from its variant distributions
 // P[s][mb][y] (Eq. 2, Eq. 3); arguments already validated

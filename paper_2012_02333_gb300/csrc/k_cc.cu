@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 
@@ -602,7 +604,285 @@ void launch_typed(const Contraction& c, cudaStream_t s) {
   if (c.profile) prof_end(s, ev);
 }
 
+// ---- low-rank contraction (at most 16 kept terms) --------------------------
+// P[m][n] = scale * sum_{k < kc} A[ra[k]][m] B[rb[k]][n] for kc <= 16, the
+// shape of circuits cut by one or two wires (4 or 16 terms) whose outputs run
+// to 2^26 .. 2^28: the work is a few FMAs per output and the output stream is
+// everything, so a thread keeps 4 consecutive columns of the kc B rows in
+// registers and walks rows m, staging each item's A panel (64 rows x kc) in
+// shared memory, and every output goes out as one 16-byte streaming store
+// (FP32; two for FP64) of 4 consecutive outputs (the N side owns the two
+// lowest output bits).  The FP64 sum is carried per thread in compensated
+// FP32 (FP32 tensors) and added once per warp and item.  Work items (problem,
+// 64 rows, up to 1024 columns) come from a device list over many problems, so
+// every low-rank final contraction of a batch is one launch.
+template <typename T>
+struct LRProblem {
+  const T* A;
+  const T* B;
+  const int32_t* crow;     // [2][kmax]: compacted row pairs
+  const int32_t* kcount;
+  int kmax;
+  int fA, fB, nbA, nbB;
+  const uint64_t* depA;
+  const uint64_t* depB;
+  T* out;
+  double* sum;
+  double scale;
+};
+struct LRItem {
+  int prob;
+  int n0;
+  int64_t m0;
+};
+constexpr int LR_MB = 64;      // rows per item
+constexpr int LR_NT = 1024;    // columns per item (256 threads x 4)
+
+template <typename T>
+struct LRArgs {
+  const LRProblem<T>* probs;   // device list (batch) or null: `one` and an implicit item grid
+  const LRItem* items;
+  int64_t n_items;
+  LRProblem<T> one;
+  int64_t one_tiles_n;
+};
+
+struct FFs {
+  float s, c;
+};
+__device__ __forceinline__ FFs ffs_add(FFs a, float b) {
+  const float s = a.s + b;
+  const float bb = s - a.s;
+  return {s, a.c + ((a.s - (s - bb)) + (b - bb))};
+}
+
+template <typename T, int KC>
+__device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m0, int n0, T (*As)[16],
+                                        uint64_t* gAs) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t M = int64_t(1) << p.fA;
+  const int N = 1 << p.fB;
+  const int cols = N < LR_NT ? N : LR_NT;
+  const int tpr = cols / 4;                 // threads per row
+  const int rpp = 256 / tpr;                // rows per pass
+  const int c4 = 4 * (tid % tpr), rs = tid / tpr;
+  const int32_t* ra = p.crow;
+  const int32_t* rb = p.crow + p.kmax;
+  // the A panel and the rows' output offsets
+  for (int idx = tid; idx < LR_MB * KC; idx += 256) {
+    const int i = idx % LR_MB, k = idx / LR_MB;
+    As[i][k] = (k < kc && m0 + i < M) ? p.A[(int64_t)ra[k] * M + m0 + i] : T(0);
+  }
+  for (int i = tid; i < LR_MB; i += 256) gAs[i] = m0 + i < M ? deposit(p.depA, p.nbA, (uint64_t)(m0 + i)) : 0;
+  // this thread's 4 columns of the kc B rows
+  T b[KC][4];
+  const int n = n0 + c4;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) b[k][j] = T(0);
+    if (k < kc && rs < rpp) {
+      const T* src = p.B + (int64_t)rb[k] * N + n;
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(src));
+        b[k][0] = v.x;
+        b[k][1] = v.y;
+        b[k][2] = v.z;
+        b[k][3] = v.w;
+      } else {
+        const double2 v0 = __ldg(reinterpret_cast<const double2*>(src));
+        const double2 v1 = __ldg(reinterpret_cast<const double2*>(src) + 1);
+        b[k][0] = v0.x;
+        b[k][1] = v0.y;
+        b[k][2] = v1.x;
+        b[k][3] = v1.y;
+      }
+    }
+  }
+  const uint64_t gB = deposit(p.depB, p.nbB, (uint64_t)n);
+  __syncthreads();
+  const T sc = (T)p.scale;
+  FFs acc{0.0f, 0.0f};
+  double acc64 = 0.0;
+  const int rows = (int)((M - m0) < LR_MB ? (M - m0) : LR_MB);
+  for (int i = rs; i < rows; i += rpp) {
+    T v[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+    for (int k = 0; k < KC; ++k) {
+      const T a = As[i][k];   // zero beyond kc
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = fma(a, b[k][j], v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] *= sc;
+    T* dst = p.out + gAs[i] + gB;
+    if constexpr (sizeof(T) == 4) {
+      __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+      acc = ffs_add(acc, (v[0] + v[1]) + (v[2] + v[3]));
+    } else {
+      __stcs(reinterpret_cast<double2*>(dst), make_double2(v[0], v[1]));
+      __stcs(reinterpret_cast<double2*>(dst) + 1, make_double2(v[2], v[3]));
+      acc64 += (v[0] + v[1]) + (v[2] + v[3]);
+    }
+  }
+  if (p.sum) {
+    double t = sizeof(T) == 4 ? (double)acc.s + (double)acc.c : acc64;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0 && t != 0.0) atomicAdd(p.sum, t);
+  }
+  __syncthreads();   // the panel is rewritten by the next item
+}
+
+template <typename T>
+__global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
+  __shared__ T As[LR_MB][16];
+  __shared__ uint64_t gAs[LR_MB];
+  for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    LRProblem<T> p;
+    int64_t m0;
+    int n0;
+    if (a.probs) {
+      const LRItem item = a.items[it];
+      p = a.probs[item.prob];
+      m0 = item.m0;
+      n0 = item.n0;
+    } else {
+      p = a.one;
+      m0 = (it / a.one_tiles_n) * LR_MB;
+      n0 = (int)(it % a.one_tiles_n) * LR_NT;
+    }
+    const int kc = *p.kcount;
+    if (kc <= 4)
+      lr_item<T, 4>(p, kc, m0, n0, As, gAs);
+    else if (kc <= 8)
+      lr_item<T, 8>(p, kc, m0, n0, As, gAs);
+    else
+      lr_item<T, 16>(p, kc, m0, n0, As, gAs);
+  }
+}
+
+template <typename T>
+LRProblem<T> lr_problem(const Contraction& c) {
+  LRProblem<T> p{};
+  p.A = static_cast<const T*>(c.A);
+  p.B = static_cast<const T*>(c.B);
+  p.crow = c.crow;
+  p.kcount = c.kcount;
+  p.kmax = c.kmax;
+  p.fA = c.fA;
+  p.fB = c.fB;
+  p.nbA = std::max((c.fA + 7) / 8, 1);
+  p.nbB = std::max((c.fB + 7) / 8, 1);
+  p.depA = c.depA;
+  p.depB = c.depB;
+  p.out = static_cast<T*>(c.out);
+  p.sum = c.sum;
+  p.scale = c.scale;
+  return p;
+}
+
+int lr_grid(int64_t items) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    CUTQC_CUDA(cudaGetDevice(&dev));
+    CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  return (int)std::min<int64_t>(items, (int64_t)sms * 4);
+}
+
 }  // namespace
+
+bool lowrank_eligible(const Contraction& c) {
+  return c.batch == 1 && c.kmax <= 16 && c.fB >= 2 && c.fB <= 30 && c.vecB >= 4 && c.fA <= 40;
+}
+
+int64_t lowrank_items(const Contraction& c) {
+  const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
+  const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
+  return tiles_n * tiles_m;
+}
+
+size_t lowrank_batch_bytes(const std::vector<Contraction>& cs) {
+  int64_t items = 0;
+  for (const Contraction& c : cs) items += lowrank_items(c);
+  return (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256 +
+         (size_t)items * sizeof(LRItem);
+}
+
+void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>& host, int64_t* n_items) {
+  const bool f64 = !cs.empty() && cs[0].dtype == CUTQC_F64;
+  const size_t psz = f64 ? sizeof(LRProblem<double>) : sizeof(LRProblem<float>);
+  const size_t poff = (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256;
+  host.assign(lowrank_batch_bytes(cs), 0);
+  int64_t it = 0;
+  for (size_t i = 0; i < cs.size(); ++i) {
+    if ((cs[i].dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
+    if (f64) {
+      const LRProblem<double> p = lr_problem<double>(cs[i]);
+      std::memcpy(host.data() + i * psz, &p, psz);
+    } else {
+      const LRProblem<float> p = lr_problem<float>(cs[i]);
+      std::memcpy(host.data() + i * psz, &p, psz);
+    }
+    const int64_t tiles_n = cs[i].fB >= 10 ? (int64_t(1) << (cs[i].fB - 10)) : 1;
+    const int64_t tiles_m = ((int64_t(1) << cs[i].fA) + LR_MB - 1) / LR_MB;
+    for (int64_t tm = 0; tm < tiles_m; ++tm)
+      for (int64_t tn = 0; tn < tiles_n; ++tn) {
+        LRItem item{(int)i, (int)(tn * LR_NT), tm * LR_MB};
+        std::memcpy(host.data() + poff + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
+        ++it;
+      }
+  }
+  *n_items = it;
+}
+
+void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>& cs, int64_t n_items,
+                          cudaStream_t s) {
+  if (cs.empty() || n_items == 0) return;
+  const size_t poff = (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256;
+  const char* t = static_cast<const char*>(dev_tables);
+  if (cs[0].dtype == CUTQC_F64) {
+    LRArgs<double> a{};
+    a.probs = reinterpret_cast<const LRProblem<double>*>(t);
+    a.items = reinterpret_cast<const LRItem*>(t + poff);
+    a.n_items = n_items;
+    k_lowrank<double><<<lr_grid(n_items), 256, 0, s>>>(a);
+  } else {
+    LRArgs<float> a{};
+    a.probs = reinterpret_cast<const LRProblem<float>*>(t);
+    a.items = reinterpret_cast<const LRItem*>(t + poff);
+    a.n_items = n_items;
+    k_lowrank<float><<<lr_grid(n_items), 256, 0, s>>>(a);
+  }
+  count_launch();
+  check_launch("k_lowrank");
+}
+
+void launch_lowrank(const Contraction& c, cudaStream_t s) {
+  if (!lowrank_eligible(c)) fail(CUTQC_ERR_UNSUPPORTED, "shape not supported by the low-rank contraction");
+  const int64_t items = lowrank_items(c);
+  const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
+  cudaEvent_t ev = nullptr;
+  if (c.profile) prof_begin(s, &ev);
+  if (c.dtype == CUTQC_F64) {
+    LRArgs<double> a{};
+    a.one = lr_problem<double>(c);
+    a.n_items = items;
+    a.one_tiles_n = tiles_n;
+    k_lowrank<double><<<lr_grid(items), 256, 0, s>>>(a);
+  } else {
+    LRArgs<float> a{};
+    a.one = lr_problem<float>(c);
+    a.n_items = items;
+    a.one_tiles_n = tiles_n;
+    k_lowrank<float><<<lr_grid(items), 256, 0, s>>>(a);
+  }
+  count_launch();
+  check_launch("k_lowrank");
+  if (c.profile) prof_end(s, ev);
+}
 
 void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s) {
   const int64_t blocks = jobs.rows[0] + (jobs.n > 1 ? jobs.rows[1] : 0);
