@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="supremacy_4x6",
                     choices=["supremacy_4x6", "hwea10", "batch64", "qaoa30", "dd80", "attr_qaoa30", "attr_merged_qaoa30",
-                             "metrics_qaoa30", "sim_supremacy4x6"],
+                             "metrics_qaoa30", "sim_supremacy4x6", "peaks"],
                     help="supremacy_4x6 is the benchmark line; the others time the other configurations")
     return ap.parse_args()
 
@@ -833,8 +833,42 @@ def launch_ranks(n):
     return subprocess.call(cmd)
 
 
+def run_peaks(args):
+    """Library peaks beside the driver's BF16 and copy figures: a plain
+    torch.matmul of 8192^3 in TF32 (tensor cores), FP32 without TF32 (the
+    library's CUDA-core GEMM) and FP64, best of `steps` after `warmup`, CUDA
+    events; 2 N^3 flops each."""
+    import torch
+    torch.cuda.set_device(0)
+    out = {}
+    for name, dt, tf32 in (("tf32_tflops", torch.float32, True), ("fp32_tflops", torch.float32, False),
+                           ("fp64_tflops", torch.float64, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        n = 8192
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b = torch.randn(n, n, dtype=dt, device="cuda")
+        c = torch.empty(n, n, dtype=dt, device="cuda")
+        for _ in range(max(args.warmup, 3)):
+            torch.matmul(a, b, out=c)
+        best = 1e30
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+        del a, b, c
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps({"peaks": out, "how": "torch.matmul 8192^3, best of %d, CUDA events" % args.steps}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "peaks":
+        run_peaks(args)
+        return
     if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
         sys.exit(launch_ranks(args.gpus))
     if args.impl == "reference":

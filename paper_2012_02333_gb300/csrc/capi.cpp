@@ -846,6 +846,30 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     Contraction& c = cs[i];
     const bool last_step = (i + 1 == P.steps.size());
     if (last_step && groups_only) break;
+    if (last_step && !use_tc_final && defer_lowrank && lowrank_eligible(c) && !flagged[st.a] && !flagged[st.b] &&
+        !is_host_memory(out)) {
+      // a low-rank CUDA-core final contraction: its row statistics, its
+      // compaction and the contraction run in the caller's one launch over
+      // every such problem of a batch
+      flagged[st.a] = flagged[st.b] = 1;
+      c.A = node_ptr(st.a);
+      c.B = node_ptr(st.b);
+      c.rows = reinterpret_cast<const int32_t*>(dtab + st.off_rows);
+      c.depA = reinterpret_cast<const uint64_t*>(dtab + st.off_depA);
+      c.depB = reinterpret_cast<const uint64_t*>(dtab + st.off_depB);
+      c.crow = reinterpret_cast<int32_t*>(base + st.ws_crow);
+      c.kcount = reinterpret_cast<int32_t*>(base + st.ws_kcount);
+      c.nzA = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.a]);
+      c.nzB = reinterpret_cast<const int32_t*>(base + P.ws_nz[st.b]);
+      c.rmaxA = reinterpret_cast<const float*>(base + P.ws_rmax[st.a]);
+      c.rmaxB = reinterpret_cast<const float*>(base + P.ws_rmax[st.b]);
+      c.status = status_word(ds);
+      c.out = out;
+      c.sum = sum;
+      defer_lowrank->push_back(c);
+      g_last_algo = CUTQC_CC;
+      break;
+    }
     const bool both_new = !flagged[st.a] || !flagged[st.b];
     TcFusedStats fstats{};
     bool fused_stats = false;
@@ -920,8 +944,6 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     }
     if (final_step && use_tc_final)
       launch_tc_bf16x3(c, base + align_up(P.ws_bytes), tc_ws, s, fused_stats ? &fstats : nullptr);
-    else if (final_step && lowrank_eligible(c) && !c.out_host && defer_lowrank)
-      defer_lowrank->push_back(c);   // the caller launches every deferred problem together
     else if (final_step && lowrank_eligible(c))
       launch_lowrank(c, s);
     else

@@ -762,6 +762,93 @@ __global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
   }
 }
 
+// ---- one persistent launch for every low-rank problem of a batch ----------
+// Phase 1: the row non-zero flags (and max |.|) of every problem's two
+// operands, one block per row over all problems; phase 2: each problem's
+// stable compaction of its row pairs (early termination, Sec. 4.2), one block
+// per problem, which also clears its FP64 sum; phase 3: the low-rank items of
+// every problem.  Between the phases a grid barrier (cooperative launch, so
+// every block is resident; each wait is bounded and a timeout records the
+// status word and ends the block).
+struct BatchRowJob {
+  const void* T;
+  int64_t rows, cols, first;   // first: the job's first row in the global row order
+  int32_t* flags;
+  float* rmax;
+};
+template <typename T>
+struct BatchArgs {
+  const LRProblem<T>* probs;
+  const CompactJob* cjobs;
+  const BatchRowJob* rjobs;
+  const LRItem* items;
+  int nprob, nrjobs;
+  int64_t nrows, n_items;
+  unsigned* barrier;           // two counters, zeroed before the launch
+  int* status;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// every block arrives once; false (after recording the timeout) if the others
+// do not all arrive within 2 s
+__device__ bool batch_grid_sync(unsigned* ctr, int* status) {
+  __shared__ int pass;
+  __threadfence();   // this thread's writes of the phase, at GPU scope
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+    const uint64_t t0 = global_ns();
+    int ok = 1;
+    while (ld_acquire_u32(ctr) < gridDim.x) {
+      if (global_ns() - t0 > 2000000000ull) {
+        ok = 0;
+        atomicExch(status, (int)DEV_TIMEOUT);
+        break;
+      }
+      __nanosleep(32);
+    }
+    pass = ok;
+  }
+  __syncthreads();
+  return pass != 0;
+}
+
+template <typename T>
+__global__ __launch_bounds__(256) void k_batch_cc(const BatchArgs<T> a) {
+  __shared__ T As[LR_MB][16];
+  __shared__ uint64_t gAs[LR_MB];
+  for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+    int j = 0;
+    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first <= r) ++j;
+    const BatchRowJob& rj = a.rjobs[j];
+    const int64_t row = r - rj.first;
+    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols, rj.cols, rj.flags + row, rj.rmax + row);
+  }
+  if (!batch_grid_sync(a.barrier, a.status)) return;
+  for (int p = blockIdx.x; p < a.nprob; p += gridDim.x) compact_block(a.cjobs[p]);
+  if (!batch_grid_sync(a.barrier + 1, a.status)) return;
+  for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
+    const LRItem item = a.items[it];
+    const LRProblem<T> p = a.probs[item.prob];
+    const int kc = *p.kcount;
+    if (kc <= 4)
+      lr_item<T, 4>(p, kc, item.m0, item.n0, As, gAs);
+    else if (kc <= 8)
+      lr_item<T, 8>(p, kc, item.m0, item.n0, As, gAs);
+    else
+      lr_item<T, 16>(p, kc, item.m0, item.n0, As, gAs);
+  }
+}
+
 template <typename T>
 LRProblem<T> lr_problem(const Contraction& c) {
   LRProblem<T> p{};
@@ -804,60 +891,130 @@ int64_t lowrank_items(const Contraction& c) {
   return tiles_n * tiles_m;
 }
 
-size_t lowrank_batch_bytes(const std::vector<Contraction>& cs) {
-  int64_t items = 0;
-  for (const Contraction& c : cs) items += lowrank_items(c);
-  return (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256 +
-         (size_t)items * sizeof(LRItem);
+// device tables of a batch: [problems][compaction jobs][row jobs][items][2 barrier counters]
+struct BatchLayout {
+  size_t probs, cjobs, rjobs, items, barrier, bytes;
+  int64_t n_items, nrows;
+};
+static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+static BatchLayout batch_layout(const std::vector<Contraction>& cs) {
+  BatchLayout L{};
+  const size_t P = cs.size();
+  for (const Contraction& c : cs) {
+    L.n_items += lowrank_items(c);
+    L.nrows += (int64_t)c.rowsA + c.rowsB;
+  }
+  L.probs = 0;
+  L.cjobs = up256(P * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)));
+  L.rjobs = L.cjobs + up256(P * sizeof(CompactJob));
+  L.items = L.rjobs + up256(2 * P * sizeof(BatchRowJob));
+  L.barrier = L.items + up256((size_t)L.n_items * sizeof(LRItem));
+  L.bytes = L.barrier + 256;
+  return L;
 }
 
+size_t lowrank_batch_bytes(const std::vector<Contraction>& cs) { return batch_layout(cs).bytes; }
+
 void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>& host, int64_t* n_items) {
+  const BatchLayout L = batch_layout(cs);
   const bool f64 = !cs.empty() && cs[0].dtype == CUTQC_F64;
   const size_t psz = f64 ? sizeof(LRProblem<double>) : sizeof(LRProblem<float>);
-  const size_t poff = (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256;
-  host.assign(lowrank_batch_bytes(cs), 0);
-  int64_t it = 0;
+  host.assign(L.bytes, 0);
+  int64_t it = 0, row0 = 0;
   for (size_t i = 0; i < cs.size(); ++i) {
-    if ((cs[i].dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
+    const Contraction& c = cs[i];
+    if ((c.dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
+    if (!c.rows || !c.nzA || !c.nzB || !c.rmaxA || !c.rmaxB) fail(CUTQC_ERR_ARG, "batched problem without its tables");
     if (f64) {
-      const LRProblem<double> p = lr_problem<double>(cs[i]);
-      std::memcpy(host.data() + i * psz, &p, psz);
+      const LRProblem<double> p = lr_problem<double>(c);
+      std::memcpy(host.data() + L.probs + i * psz, &p, psz);
     } else {
-      const LRProblem<float> p = lr_problem<float>(cs[i]);
-      std::memcpy(host.data() + i * psz, &p, psz);
+      const LRProblem<float> p = lr_problem<float>(c);
+      std::memcpy(host.data() + L.probs + i * psz, &p, psz);
     }
-    const int64_t tiles_n = cs[i].fB >= 10 ? (int64_t(1) << (cs[i].fB - 10)) : 1;
-    const int64_t tiles_m = ((int64_t(1) << cs[i].fA) + LR_MB - 1) / LR_MB;
+    CompactJob cj{};
+    cj.active = 1;
+    cj.rows = c.rows;
+    cj.kmax = c.kmax;
+    cj.nzA = c.nzA;
+    cj.nzB = c.nzB;
+    cj.crow = c.crow;
+    cj.kcount = c.kcount;
+    cj.sum_zero = c.sum;
+    std::memcpy(host.data() + L.cjobs + i * sizeof(CompactJob), &cj, sizeof(CompactJob));
+    for (int side = 0; side < 2; ++side) {
+      BatchRowJob rj{};
+      rj.T = side ? c.B : c.A;
+      rj.rows = side ? c.rowsB : c.rowsA;
+      rj.cols = int64_t(1) << (side ? c.fB : c.fA);
+      rj.first = row0;
+      rj.flags = const_cast<int32_t*>(side ? c.nzB : c.nzA);
+      rj.rmax = const_cast<float*>(side ? c.rmaxB : c.rmaxA);
+      row0 += rj.rows;
+      std::memcpy(host.data() + L.rjobs + (2 * i + side) * sizeof(BatchRowJob), &rj, sizeof(BatchRowJob));
+    }
+    const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
+    const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
     for (int64_t tm = 0; tm < tiles_m; ++tm)
       for (int64_t tn = 0; tn < tiles_n; ++tn) {
         LRItem item{(int)i, (int)(tn * LR_NT), tm * LR_MB};
-        std::memcpy(host.data() + poff + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
+        std::memcpy(host.data() + L.items + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
         ++it;
       }
   }
   *n_items = it;
 }
 
+template <typename T>
+static void launch_batch_typed(const char* t, const BatchLayout& L, int nprob, int* status, cudaStream_t s) {
+  static int per_sm = 0, sms = 0;
+  if (!per_sm) {
+    int dev = 0;
+    CUTQC_CUDA(cudaGetDevice(&dev));
+    CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cc<T>, 256, 0));
+    if (per_sm < 1) fail(CUTQC_ERR_CUDA, "the batched contraction cannot be resident");
+  }
+  BatchArgs<T> a{};
+  a.probs = reinterpret_cast<const LRProblem<T>*>(t + L.probs);
+  a.cjobs = reinterpret_cast<const CompactJob*>(t + L.cjobs);
+  a.rjobs = reinterpret_cast<const BatchRowJob*>(t + L.rjobs);
+  a.items = reinterpret_cast<const LRItem*>(t + L.items);
+  a.nprob = nprob;
+  a.nrjobs = 2 * nprob;
+  a.nrows = L.nrows;
+  a.n_items = L.n_items;
+  a.barrier = reinterpret_cast<unsigned*>(const_cast<char*>(t) + L.barrier);
+  a.status = status;
+  const int64_t want = std::max(std::max(L.nrows, L.n_items), (int64_t)nprob);
+  const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)per_sm * sms);
+  CUTQC_CUDA(cudaMemsetAsync(a.barrier, 0, 2 * sizeof(unsigned), s));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every block resident: the grid barriers cannot starve
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_batch_cc<T>, a));
+  count_launch();
+  check_launch("k_batch_cc");
+}
+
 void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>& cs, int64_t n_items,
                           cudaStream_t s) {
-  if (cs.empty() || n_items == 0) return;
-  const size_t poff = (cs.size() * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)) + 255) / 256 * 256;
+  if (cs.empty()) return;
+  const BatchLayout L = batch_layout(cs);
+  if (L.n_items != n_items) fail(CUTQC_ERR_ARG, "batch tables do not match the problems");
+  if (!cs[0].status) fail(CUTQC_ERR_ARG, "the batched contraction needs the device status word");
   const char* t = static_cast<const char*>(dev_tables);
-  if (cs[0].dtype == CUTQC_F64) {
-    LRArgs<double> a{};
-    a.probs = reinterpret_cast<const LRProblem<double>*>(t);
-    a.items = reinterpret_cast<const LRItem*>(t + poff);
-    a.n_items = n_items;
-    k_lowrank<double><<<lr_grid(n_items), 256, 0, s>>>(a);
-  } else {
-    LRArgs<float> a{};
-    a.probs = reinterpret_cast<const LRProblem<float>*>(t);
-    a.items = reinterpret_cast<const LRItem*>(t + poff);
-    a.n_items = n_items;
-    k_lowrank<float><<<lr_grid(n_items), 256, 0, s>>>(a);
-  }
-  count_launch();
-  check_launch("k_lowrank");
+  if (cs[0].dtype == CUTQC_F64)
+    launch_batch_typed<double>(t, L, (int)cs.size(), cs[0].status, s);
+  else
+    launch_batch_typed<float>(t, L, (int)cs.size(), cs[0].status, s);
 }
 
 void launch_lowrank(const Contraction& c, cudaStream_t s) {
