@@ -48,8 +48,12 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # the ncu capture summarised in profiles/k_tc_gemm_supremacy_4x6_k4.md, valid while
 # the kernel source is unchanged (first 16 hex digits of its SHA-256)
 TRAFFIC_TC = {"sha256_16": "37e9963e0610294d", "bytes": 15.709e6}
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-FP32_ALU_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# Library peaks of the machine's GB300 beside the driver's BF16 and copy figures,
+# measured with `python bench.py --workload peaks --steps 10 --warmup 3`
+# (torch.matmul 8192^3, best of 10): TF32 tensor cores, FP32 without TF32
+# (CUDA cores) and FP64; summarised in profiles/peaks_gb300.md
+LIBRARY_PEAKS = {"tf32_tflops": 1053.7, "fp32_tflops": 69.96, "fp64_tflops": 1.101}
+FP32_ALU_TFLOPS = LIBRARY_PEAKS["fp32_tflops"]
 
 
 def parse():
@@ -78,13 +82,13 @@ def peaks():
 
 def tc_peak(pk, pk_src, algo):
     """Tensor peak for the split form that ran: the measured BF16 burst peak,
-    or for TF32 the measured TF32 peak if the peaks file has one, else the
-    BF16 peak times the nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)."""
+    or for TF32 the measured TF32 peak (the peaks file's if it has one, else
+    the library peak measured on this machine)."""
     from paper_2012_02333_gb300 import cutqc
     if algo == getattr(cutqc, "CUTQC_TC_TF32X3", -1):
         if "tf32_tflops" in pk:
             return pk["tf32_tflops"], f"{pk_src} tf32"
-        return pk["bf16_tflops"] * 1.1 / 2.25, f"{pk_src} bf16 burst x nominal tf32/bf16 ratio 1.1/2.25"
+        return LIBRARY_PEAKS["tf32_tflops"], "measured tf32 (torch.matmul, LIBRARY_PEAKS)"
     return pk["bf16_tflops"], f"{pk_src} bf16 burst"
 
 
@@ -446,7 +450,7 @@ def run_ours(args):
         else:
             comp = {"flops_per_launch": flops1, "achieved_tflops": flops1 / t_s / 1e12,
                     "peak_tflops": FP32_ALU_TFLOPS, "frac": flops1 / t_s / 1e12 / FP32_ALU_TFLOPS,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                    "peak_source": "measured fp32 CUDA-core matmul (LIBRARY_PEAKS)",
                     "t_roof_us": flops1 / (FP32_ALU_TFLOPS * 1e12) * 1e6}
             cbound = "alu"
         if comp["t_roof_us"] >= hbm["t_roof_us"]:

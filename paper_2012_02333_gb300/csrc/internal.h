@@ -150,6 +150,7 @@ struct RowStatsJobs {   // up to two tensors whose rows get non-zero flags and m
   int64_t rows[2], cols[2];
   int32_t* flags[2];
   float* rmax[2];
+  int chunks[2];          // blocks per row (set by the launcher; long rows of few-row tensors are split)
   CompactJob cj;
 };
 void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s);

@@ -160,14 +160,32 @@ template <typename T>
 __global__ void k_row_stats(RowStatsJobs jobs) {
   CUTQC_PDL_LAUNCH();   // the operand preparation may launch and wait on this grid
   __shared__ int is_last;
+  __shared__ int32_t part_nz;
+  __shared__ float part_max;
   int j = 0;
-  int64_t r = blockIdx.x;
-  if (r >= jobs.rows[0]) {
-    r -= jobs.rows[0];
+  int64_t u = blockIdx.x;
+  if (u >= jobs.rows[0] * jobs.chunks[0]) {
+    u -= jobs.rows[0] * jobs.chunks[0];
     j = 1;
   }
   const T* t = static_cast<const T*>(jobs.t[j]);
-  row_stats_block<T>(t + r * jobs.cols[j], jobs.cols[j], jobs.flags[j] + r, jobs.rmax[j] + r);
+  // select, not a dynamic index into the parameter arrays
+  const int chunks = j ? jobs.chunks[1] : jobs.chunks[0];
+  const int64_t cols = j ? jobs.cols[1] : jobs.cols[0];
+  int32_t* flags = j ? jobs.flags[1] : jobs.flags[0];
+  float* rmax = j ? jobs.rmax[1] : jobs.rmax[0];
+  if (chunks == 1) {
+    row_stats_block<T>(t + u * cols, cols, flags + u, rmax + u);
+  } else {
+    // a chunk of a long row: combined into the row's cleared flag and maximum
+    const int64_t r = u / chunks, ch = u % chunks, cc = cols / chunks;
+    row_stats_block<T>(t + r * cols + ch * cc, cc, &part_nz, &part_max);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (part_nz) atomicOr(flags + r, 1);
+      atomicMax(reinterpret_cast<int*>(rmax + r), __float_as_int(part_max));   // maxima are >= 0
+    }
+  }
   if (!jobs.cj.active) return;
   if (threadIdx.x == 0) {
     __threadfence();
@@ -763,8 +781,10 @@ __global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
 }
 
 // ---- one persistent launch for every low-rank problem of a batch ----------
-// Phase 1: the row non-zero flags (and max |.|) of every problem's two
-// operands, one block per row over all problems; phase 2: each problem's
+// Phase 0 clears the row flags and maxima; phase 1: the row non-zero flags
+// (and max |.|) of every problem's two operands, one block per chunk of at
+// most 2^16 columns of a row over all problems (operands of one or two rows of
+// 2^26 columns occur), combined with atomics; phase 2: each problem's
 // stable compaction of its row pairs (early termination, Sec. 4.2), one block
 // per problem, which also clears its FP64 sum; phase 3: the low-rank items of
 // every problem.  Between the phases a grid barrier (cooperative launch, so
@@ -772,10 +792,14 @@ __global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
 // status word and ends the block).
 struct BatchRowJob {
   const void* T;
-  int64_t rows, cols, first;   // first: the job's first row in the global row order
+  int64_t rows, cols;
+  int64_t first;               // the job's first unit (row chunk) in the global unit order
+  int64_t first_row;           // the job's first row in the global row order
+  int chunks;                  // column chunks per row (long rows are split over blocks)
   int32_t* flags;
   float* rmax;
 };
+constexpr int64_t BATCH_CHUNK = int64_t(1) << 16;   // columns per row chunk
 template <typename T>
 struct BatchArgs {
   const LRProblem<T>* probs;
@@ -783,8 +807,8 @@ struct BatchArgs {
   const BatchRowJob* rjobs;
   const LRItem* items;
   int nprob, nrjobs;
-  int64_t nrows, n_items;
-  unsigned* barrier;           // two counters, zeroed before the launch
+  int64_t nrows, nunits, n_items;
+  unsigned* barrier;           // three counters, zeroed before the launch
   int* status;
 };
 
@@ -826,16 +850,34 @@ template <typename T>
 __global__ __launch_bounds__(256) void k_batch_cc(const BatchArgs<T> a) {
   __shared__ T As[LR_MB][16];
   __shared__ uint64_t gAs[LR_MB];
-  for (int64_t r = blockIdx.x; r < a.nrows; r += gridDim.x) {
+  __shared__ int32_t part_nz;
+  __shared__ float part_max;
+  // phase 0: clear every row's flag and maximum (phase 1 combines chunks into them)
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nrows;
+       r += (int64_t)gridDim.x * blockDim.x) {
     int j = 0;
-    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first <= r) ++j;
-    const BatchRowJob& rj = a.rjobs[j];
-    const int64_t row = r - rj.first;
-    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols, rj.cols, rj.flags + row, rj.rmax + row);
+    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first_row <= r) ++j;
+    a.rjobs[j].flags[r - a.rjobs[j].first_row] = 0;
+    a.rjobs[j].rmax[r - a.rjobs[j].first_row] = 0.0f;
   }
   if (!batch_grid_sync(a.barrier, a.status)) return;
-  for (int p = blockIdx.x; p < a.nprob; p += gridDim.x) compact_block(a.cjobs[p]);
+  // phase 1: one block per row chunk of at most 2^16 columns
+  for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
+    int j = 0;
+    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first <= u) ++j;
+    const BatchRowJob& rj = a.rjobs[j];
+    const int64_t row = (u - rj.first) / rj.chunks, ch = (u - rj.first) % rj.chunks;
+    const int64_t ccols = rj.cols / rj.chunks;
+    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols + ch * ccols, ccols, &part_nz, &part_max);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      if (part_nz) atomicOr(rj.flags + row, 1);
+      atomicMax(reinterpret_cast<int*>(rj.rmax + row), __float_as_int(part_max));   // maxima are >= 0
+    }
+  }
   if (!batch_grid_sync(a.barrier + 1, a.status)) return;
+  for (int p = blockIdx.x; p < a.nprob; p += gridDim.x) compact_block(a.cjobs[p]);
+  if (!batch_grid_sync(a.barrier + 2, a.status)) return;
   for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     const LRItem item = a.items[it];
     const LRProblem<T> p = a.probs[item.prob];
@@ -891,10 +933,10 @@ int64_t lowrank_items(const Contraction& c) {
   return tiles_n * tiles_m;
 }
 
-// device tables of a batch: [problems][compaction jobs][row jobs][items][2 barrier counters]
+// device tables of a batch: [problems][compaction jobs][row jobs][items][3 barrier counters]
 struct BatchLayout {
   size_t probs, cjobs, rjobs, items, barrier, bytes;
-  int64_t n_items, nrows;
+  int64_t n_items, nrows, nunits;
 };
 static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -904,6 +946,10 @@ static BatchLayout batch_layout(const std::vector<Contraction>& cs) {
   for (const Contraction& c : cs) {
     L.n_items += lowrank_items(c);
     L.nrows += (int64_t)c.rowsA + c.rowsB;
+    for (int f : {c.fA, c.fB}) {
+      const int64_t cols = int64_t(1) << f;
+      L.nunits += (f == c.fA ? c.rowsA : c.rowsB) * std::max<int64_t>(1, cols / BATCH_CHUNK);
+    }
   }
   L.probs = 0;
   L.cjobs = up256(P * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)));
@@ -921,7 +967,7 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
   const bool f64 = !cs.empty() && cs[0].dtype == CUTQC_F64;
   const size_t psz = f64 ? sizeof(LRProblem<double>) : sizeof(LRProblem<float>);
   host.assign(L.bytes, 0);
-  int64_t it = 0, row0 = 0;
+  int64_t it = 0, row0 = 0, unit0 = 0;
   for (size_t i = 0; i < cs.size(); ++i) {
     const Contraction& c = cs[i];
     if ((c.dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
@@ -948,10 +994,13 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
       rj.T = side ? c.B : c.A;
       rj.rows = side ? c.rowsB : c.rowsA;
       rj.cols = int64_t(1) << (side ? c.fB : c.fA);
-      rj.first = row0;
+      rj.first_row = row0;
+      rj.first = unit0;
+      rj.chunks = (int)std::max<int64_t>(1, rj.cols / BATCH_CHUNK);
       rj.flags = const_cast<int32_t*>(side ? c.nzB : c.nzA);
       rj.rmax = const_cast<float*>(side ? c.rmaxB : c.rmaxA);
       row0 += rj.rows;
+      unit0 += rj.rows * rj.chunks;
       std::memcpy(host.data() + L.rjobs + (2 * i + side) * sizeof(BatchRowJob), &rj, sizeof(BatchRowJob));
     }
     const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
@@ -984,12 +1033,13 @@ static void launch_batch_typed(const char* t, const BatchLayout& L, int nprob, i
   a.nprob = nprob;
   a.nrjobs = 2 * nprob;
   a.nrows = L.nrows;
+  a.nunits = L.nunits;
   a.n_items = L.n_items;
   a.barrier = reinterpret_cast<unsigned*>(const_cast<char*>(t) + L.barrier);
   a.status = status;
-  const int64_t want = std::max(std::max(L.nrows, L.n_items), (int64_t)nprob);
+  const int64_t want = std::max(std::max(L.nunits, L.n_items), (int64_t)nprob);
   const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)per_sm * sms);
-  CUTQC_CUDA(cudaMemsetAsync(a.barrier, 0, 2 * sizeof(unsigned), s));
+  CUTQC_CUDA(cudaMemsetAsync(a.barrier, 0, 3 * sizeof(unsigned), s));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(256);
@@ -1042,9 +1092,20 @@ void launch_lowrank(const Contraction& c, cudaStream_t s) {
 }
 
 void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s) {
-  const int64_t blocks = jobs.rows[0] + (jobs.n > 1 ? jobs.rows[1] : 0);
   RowStatsJobs j = jobs;
   if (j.n < 2) j.rows[1] = 0;
+  // tensors with fewer rows than SMs and long rows: a block per chunk of
+  // 2^16 columns, combined with atomics into outputs cleared first
+  int64_t blocks = 0;
+  for (int k = 0; k < 2; ++k) {
+    j.chunks[k] = 1;
+    if (k < j.n && j.rows[k] < 152 && j.cols[k] > (int64_t(1) << 18)) {
+      j.chunks[k] = (int)(j.cols[k] >> 16);
+      CUTQC_CUDA(cudaMemsetAsync(j.flags[k], 0, (size_t)j.rows[k] * sizeof(int32_t), s));
+      CUTQC_CUDA(cudaMemsetAsync(j.rmax[k], 0, (size_t)j.rows[k] * sizeof(float), s));
+    }
+    blocks += j.rows[k] * j.chunks[k];
+  }
   const int64_t cmax = std::max(j.cols[0], j.n > 1 ? j.cols[1] : int64_t(0));
   const int threads = cmax >= 256 ? 256 : 32;
   if (dtype == CUTQC_F64)

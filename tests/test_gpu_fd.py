@@ -271,3 +271,21 @@ def test_reconstruction_of_searched_cuts(env, make, D, nC):
     assert np.abs(out64.cpu().numpy() - truth).max() <= 1e-12
     out32, _ = cutqc.reconstruct_fd(cc, to_dev(torch, [t.astype(np.float32) for t in T], torch.float32))
     assert np.abs(out32.double().cpu().numpy() - truth).max() <= TOL32
+
+
+@pytest.mark.parametrize("algo", ["cc", "auto"])
+def test_single_row_operands_of_long_rows(env, algo):
+    """Two uncut blocks of 20 and 4 qubits (K = 0: one Kronecker term, both
+    operands a single row, one of 2^20 entries): the row statistics split the
+    long row over many blocks and combine the chunks; all 2^24 outputs against
+    the oracle."""
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    from paper_2012_02333_gb300 import circuits as C
+    cc, Ts = oracle_case("hwea24_k0", lambda: C.cut_circuit(C.hwea(24, 3), [0] * 20 + [1] * 4, max_cuts=0))
+    assert cc.n_cuts == 0 and len(cc.subs) == 2
+    T32 = [T.astype(np.float32) for T in Ts]
+    ref = rc.fd_full(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts)
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
+    assert np.abs(out.double().cpu().numpy() - ref).max() <= TOL32
+    assert float(sp.item()) == pytest.approx(ref.sum(), abs=TOL32)
