@@ -99,8 +99,11 @@ typedef enum { CUTQC_F64 = 0, CUTQC_F32 = 1 } cutqc_dtype;
  *                  tensor memory.  Error per product <= ~3 * 2^-22 |a||b|, at
  *                  half the BF16 tensor rate and 4/3 of the BF16 x3 operand
  *                  bytes.  Never chosen by CUTQC_AUTO.
- *  CUTQC_AUTO      FP64 tensors: CUTQC_CC.  FP32 tensors: the tensor-core
- *                  path when the shape allows it (else CUTQC_CC), with the
+ *  CUTQC_AUTO      FP64 tensors: CUTQC_CC.  FP32 tensors: CUTQC_CC when the
+ *                  final contraction has at most 16 Kronecker terms (a
+ *                  streaming form whose output stream is all the work),
+ *                  otherwise the tensor-core path when the shape allows it
+ *                  (else CUTQC_CC), with the
  *                  number of products chosen on the device per call from
  *                  the a-priori bound S = 2^-K sum_e max|A_e| max|B_e|:
  *                  x3 when 3 * 2^-18 * S <= 2.5e-7, otherwise x6, so the

@@ -212,7 +212,7 @@ struct DeviceState {
   std::vector<std::string> order;
   std::unordered_map<std::string, GraphEntry> graphs;   // captured batched calls
   cudaStream_t branch[kBranches] = {};
-  cudaEvent_t fork = nullptr, join[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {}, mid[kBranches] = {};
   int* status = nullptr;          // device status word written by kernels with bounded waits
   void* aux = nullptr;            // distance / sampling scratch (zeroed when (re)allocated)
   size_t aux_bytes = 0;
@@ -779,12 +779,6 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     CUTQC_CUDA(cudaMemcpy(static_cast<char*>(ds.one) + 8, &one32, 4, cudaMemcpyHostToDevice));
   }
   const void* one = P.dtype == CUTQC_F64 ? ds.one : static_cast<char*>(ds.one) + 8;
-  // decide the algorithm of the final step
-  if (algo == CUTQC_AUTO && P.tuned == CUTQC_CC) algo = CUTQC_CC;
-  int final_algo = algo;
-  if (final_algo == CUTQC_AUTO) final_algo = (P.dtype == CUTQC_F32) ? CUTQC_TC_BF16X3 : CUTQC_CC;
-  const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6 || final_algo == CUTQC_TC_TF32X3;
-  if (tc_algo && P.dtype != CUTQC_F32) fail(CUTQC_ERR_ARG, "the tensor-core forms need FP32 tensors");
   for (size_t i = 0; i < P.steps.size(); ++i) {
     Contraction& c = cs[i];
     const Step& st = P.steps[i];
@@ -799,6 +793,16 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
     c.rowsA = (int)P.nodes[st.a].rows();
     c.rowsB = (int)P.nodes[st.b].rows();
   }
+  // decide the algorithm of the final step: under CUTQC_AUTO a contraction
+  // of at most 16 kept terms takes the streaming CUDA-core form (its output
+  // stream is all the work; measured faster than the tensor-core form), the
+  // rest of FP32 the tensor-core form where the shape allows it
+  int final_algo = algo;
+  if (final_algo == CUTQC_AUTO)
+    final_algo = (P.dtype == CUTQC_F32 && !lowrank_eligible(cs.back())) ? CUTQC_TC_BF16X3 : CUTQC_CC;
+  if (algo == CUTQC_AUTO && final_algo == CUTQC_CC) algo = CUTQC_CC;
+  const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6 || final_algo == CUTQC_TC_TF32X3;
+  if (tc_algo && P.dtype != CUTQC_F32) fail(CUTQC_ERR_ARG, "the tensor-core forms need FP32 tensors");
   size_t need = P.ws_bytes;
   const bool use_tc_final = tc_algo && tc_supported(cs.back());
   if (use_tc_final) {
@@ -1051,20 +1055,40 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
       lr[d].clear();
     }
   };
-  auto run_one = [&](int i, cudaStream_t st, char* w) {
+  auto run_one = [&](int i, cudaStream_t st, char* w, bool defer) {
     std::vector<Contraction> d;
     run_plan(ds, *plans[i], 0, 0, tensors_of(&problems[i]), out[i], sum_p ? sum_p + i : nullptr, algo_of(i), st, w,
-             nullptr, SIZE_MAX, nullptr, false, nullptr, &d);
+             nullptr, SIZE_MAX, nullptr, false, nullptr, defer ? &d : nullptr);
     for (const Contraction& c : d) lr[c.dtype == CUTQC_F64 ? 1 : 0].push_back(c);
   };
+  // the problems whose final contraction is deferred into the batched
+  // low-rank launches (the same decision run_plan takes), and the rest
+  std::vector<int> deferred, others;
+  for (int i = 0; i < n; ++i) {
+    const Plan& P = *plans[i];
+    const Step& st = P.steps.back();
+    Contraction c;
+    c.batch = st.batch;
+    c.kmax = st.kmax;
+    c.fA = P.nodes[st.a].f();
+    c.fB = P.nodes[st.b].f();
+    c.vecB = st.vecB;
+    c.dtype = P.dtype;
+    const int a = algo_of(i);
+    const bool cc_final = a == CUTQC_CC || (a == CUTQC_AUTO && (lowrank_eligible(c) || P.dtype != CUTQC_F32)) ||
+                          !tc_supported(c);
+    (cc_final && lowrank_eligible(c) && !is_host_memory(out[i]) ? deferred : others).push_back(i);
+  }
   // eager run of the whole batch on the caller's stream
-  for (int i = 0; i < n; ++i) run_one(i, s, ws + off[i]);
+  for (int i : deferred) run_one(i, s, ws + off[i], true);
   launch_deferred(s);
+  for (int i : others) run_one(i, s, ws + off[i], false);
   // capture the same launches over parallel branches for later calls
   if (!ds.fork) {
     for (int b = 0; b < kBranches; ++b) {
       CUTQC_CUDA(cudaStreamCreateWithFlags(&ds.branch[b], cudaStreamNonBlocking));
       CUTQC_CUDA(cudaEventCreateWithFlags(&ds.join[b], cudaEventDisableTiming));
+      CUTQC_CUDA(cudaEventCreateWithFlags(&ds.mid[b], cudaEventDisableTiming));
     }
     CUTQC_CUDA(cudaEventCreateWithFlags(&ds.fork, cudaEventDisableTiming));
   }
@@ -1074,12 +1098,21 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     CUTQC_CUDA(cudaStreamBeginCapture(ds.branch[0], cudaStreamCaptureModeThreadLocal));
     CUTQC_CUDA(cudaEventRecord(ds.fork, ds.branch[0]));
     for (int b = 1; b < kBranches; ++b) CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[b], ds.fork, 0));
-    for (int i = 0; i < n; ++i) run_one(i, ds.branch[i % kBranches], ws + off[i]);
+    // branch 0 runs the batched low-rank launches once the deferred problems'
+    // group builds (on the other branches) are done; the other problems follow
+    // on branches 1.. and run beside it
+    int k = 0;
+    for (int i : deferred) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], true);
+    for (int b = 1; b < kBranches; ++b) {
+      CUTQC_CUDA(cudaEventRecord(ds.mid[b], ds.branch[b]));
+      CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.mid[b], 0));
+    }
+    launch_deferred(ds.branch[0]);
+    for (int i : others) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], false);
     for (int b = 1; b < kBranches; ++b) {
       CUTQC_CUDA(cudaEventRecord(ds.join[b], ds.branch[b]));
       CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.join[b], 0));
     }
-    launch_deferred(ds.branch[0]);
     CUTQC_CUDA(cudaStreamEndCapture(ds.branch[0], &graph));
   } catch (...) {
     g_capturing = false;
@@ -1659,6 +1692,7 @@ void cutqc_release(void) {
     for (int b = 0; b < kBranches; ++b) {
       if (kv.second.branch[b]) cudaStreamDestroy(kv.second.branch[b]);
       if (kv.second.join[b]) cudaEventDestroy(kv.second.join[b]);
+      if (kv.second.mid[b]) cudaEventDestroy(kv.second.mid[b]);
     }
     if (kv.second.fork) cudaEventDestroy(kv.second.fork);
     kv.second.plans.clear();

@@ -780,114 +780,61 @@ __global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
   }
 }
 
-// ---- one persistent launch for every low-rank problem of a batch ----------
-// Phase 0 clears the row flags and maxima; phase 1: the row non-zero flags
-// (and max |.|) of every problem's two operands, one block per chunk of at
-// most 2^16 columns of a row over all problems (operands of one or two rows of
-// 2^26 columns occur), combined with atomics; phase 2: each problem's
-// stable compaction of its row pairs (early termination, Sec. 4.2), one block
-// per problem, which also clears its FP64 sum; phase 3: the low-rank items of
-// every problem.  Between the phases a grid barrier (cooperative launch, so
-// every block is resident; each wait is bounded and a timeout records the
-// status word and ends the block).
+// ---- every low-rank problem of a batch in three launches -----------------
+// k_batch_rowstats: the row non-zero flags and max |.| of every problem's two
+// operands, one block per chunk of at most 2^16 columns of a row over all
+// problems (operands of one or two rows of 2^25-2^26 columns occur), each
+// chunk's partial result to its own slot; k_batch_compact: one block per
+// problem combines its rows' chunks into the flags and maxima, then compacts
+// its row pairs (early termination, Sec. 4.2) and clears its FP64 sum;
+// k_lowrank: the items of every problem.  No launch waits on another's
+// blocks, so the three can run beside the batch's tensor-core problems.
 struct BatchRowJob {
   const void* T;
   int64_t rows, cols;
   int64_t first;               // the job's first unit (row chunk) in the global unit order
-  int64_t first_row;           // the job's first row in the global row order
-  int chunks;                  // column chunks per row (long rows are split over blocks)
+  int chunks;                  // column chunks per row
   int32_t* flags;
   float* rmax;
 };
 constexpr int64_t BATCH_CHUNK = int64_t(1) << 16;   // columns per row chunk
-template <typename T>
-struct BatchArgs {
-  const LRProblem<T>* probs;
-  const CompactJob* cjobs;
-  const BatchRowJob* rjobs;
-  const LRItem* items;
-  int nprob, nrjobs;
-  int64_t nrows, nunits, n_items;
-  unsigned* barrier;           // three counters, zeroed before the launch
-  int* status;
-};
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-  return t;
-}
-// every block arrives once; false (after recording the timeout) if the others
-// do not all arrive within 2 s
-__device__ bool batch_grid_sync(unsigned* ctr, int* status) {
-  __shared__ int pass;
-  __threadfence();   // this thread's writes of the phase, at GPU scope
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
-    const uint64_t t0 = global_ns();
-    int ok = 1;
-    while (ld_acquire_u32(ctr) < gridDim.x) {
-      if (global_ns() - t0 > 2000000000ull) {
-        ok = 0;
-        atomicExch(status, (int)DEV_TIMEOUT);
-        break;
-      }
-      __nanosleep(32);
-    }
-    pass = ok;
-  }
-  __syncthreads();
-  return pass != 0;
-}
 
 template <typename T>
-__global__ __launch_bounds__(256) void k_batch_cc(const BatchArgs<T> a) {
-  __shared__ T As[LR_MB][16];
-  __shared__ uint64_t gAs[LR_MB];
-  __shared__ int32_t part_nz;
-  __shared__ float part_max;
-  // phase 0: clear every row's flag and maximum (phase 1 combines chunks into them)
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.nrows;
-       r += (int64_t)gridDim.x * blockDim.x) {
+__global__ __launch_bounds__(256) void k_batch_rowstats(const BatchRowJob* __restrict__ rjobs, int nrjobs,
+                                                        int64_t nunits, int32_t* __restrict__ part_nz,
+                                                        float* __restrict__ part_max) {
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
     int j = 0;
-    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first_row <= r) ++j;
-    a.rjobs[j].flags[r - a.rjobs[j].first_row] = 0;
-    a.rjobs[j].rmax[r - a.rjobs[j].first_row] = 0.0f;
-  }
-  if (!batch_grid_sync(a.barrier, a.status)) return;
-  // phase 1: one block per row chunk of at most 2^16 columns
-  for (int64_t u = blockIdx.x; u < a.nunits; u += gridDim.x) {
-    int j = 0;
-    while (j + 1 < a.nrjobs && a.rjobs[j + 1].first <= u) ++j;
-    const BatchRowJob& rj = a.rjobs[j];
+    while (j + 1 < nrjobs && rjobs[j + 1].first <= u) ++j;
+    const BatchRowJob& rj = rjobs[j];
     const int64_t row = (u - rj.first) / rj.chunks, ch = (u - rj.first) % rj.chunks;
-    const int64_t ccols = rj.cols / rj.chunks;
-    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols + ch * ccols, ccols, &part_nz, &part_max);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (part_nz) atomicOr(rj.flags + row, 1);
-      atomicMax(reinterpret_cast<int*>(rj.rmax + row), __float_as_int(part_max));   // maxima are >= 0
-    }
+    const int64_t cc = rj.cols / rj.chunks;
+    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols + ch * cc, cc, part_nz + u, part_max + u);
+    __syncthreads();   // the block's shared reduction buffer is reused by the next unit
   }
-  if (!batch_grid_sync(a.barrier + 1, a.status)) return;
-  for (int p = blockIdx.x; p < a.nprob; p += gridDim.x) compact_block(a.cjobs[p]);
-  if (!batch_grid_sync(a.barrier + 2, a.status)) return;
-  for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-    const LRItem item = a.items[it];
-    const LRProblem<T> p = a.probs[item.prob];
-    const int kc = *p.kcount;
-    if (kc <= 4)
-      lr_item<T, 4>(p, kc, item.m0, item.n0, As, gAs);
-    else if (kc <= 8)
-      lr_item<T, 8>(p, kc, item.m0, item.n0, As, gAs);
-    else
-      lr_item<T, 16>(p, kc, item.m0, item.n0, As, gAs);
+}
+
+__global__ __launch_bounds__(256) void k_batch_compact(const CompactJob* __restrict__ cjobs,
+                                                       const BatchRowJob* __restrict__ rjobs, int nprob,
+                                                       const int32_t* __restrict__ part_nz,
+                                                       const float* __restrict__ part_max) {
+  for (int p = blockIdx.x; p < nprob; p += gridDim.x) {
+    for (int side = 0; side < 2; ++side) {
+      const BatchRowJob& rj = rjobs[2 * p + side];
+      for (int64_t r = threadIdx.x; r < rj.rows; r += blockDim.x) {
+        int32_t nz = 0;
+        float mx = 0.0f;
+        for (int c = 0; c < rj.chunks; ++c) {
+          nz |= part_nz[rj.first + r * rj.chunks + c];
+          mx = fmaxf(mx, part_max[rj.first + r * rj.chunks + c]);
+        }
+        rj.flags[r] = nz;
+        rj.rmax[r] = mx;
+      }
+    }
+    __syncthreads();
+    compact_block(cjobs[p]);
+    __syncthreads();
   }
 }
 
@@ -933,30 +880,29 @@ int64_t lowrank_items(const Contraction& c) {
   return tiles_n * tiles_m;
 }
 
-// device tables of a batch: [problems][compaction jobs][row jobs][items][3 barrier counters]
+// device tables of a batch: [problems][compaction jobs][row jobs][items][chunk flags][chunk maxima]
 struct BatchLayout {
-  size_t probs, cjobs, rjobs, items, barrier, bytes;
-  int64_t n_items, nrows, nunits;
+  size_t probs, cjobs, rjobs, items, part_nz, part_max, bytes;
+  int64_t n_items, nunits;
 };
 static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+static int64_t row_chunks(int64_t cols) { return std::max<int64_t>(1, cols / BATCH_CHUNK); }
 
 static BatchLayout batch_layout(const std::vector<Contraction>& cs) {
   BatchLayout L{};
   const size_t P = cs.size();
   for (const Contraction& c : cs) {
     L.n_items += lowrank_items(c);
-    L.nrows += (int64_t)c.rowsA + c.rowsB;
-    for (int f : {c.fA, c.fB}) {
-      const int64_t cols = int64_t(1) << f;
-      L.nunits += (f == c.fA ? c.rowsA : c.rowsB) * std::max<int64_t>(1, cols / BATCH_CHUNK);
-    }
+    L.nunits += (int64_t)c.rowsA * row_chunks(int64_t(1) << c.fA) + (int64_t)c.rowsB * row_chunks(int64_t(1) << c.fB);
   }
   L.probs = 0;
   L.cjobs = up256(P * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)));
   L.rjobs = L.cjobs + up256(P * sizeof(CompactJob));
   L.items = L.rjobs + up256(2 * P * sizeof(BatchRowJob));
-  L.barrier = L.items + up256((size_t)L.n_items * sizeof(LRItem));
-  L.bytes = L.barrier + 256;
+  L.part_nz = L.items + up256((size_t)L.n_items * sizeof(LRItem));
+  L.part_max = L.part_nz + up256((size_t)L.nunits * sizeof(int32_t));
+  L.bytes = L.part_max + up256((size_t)L.nunits * sizeof(float));
   return L;
 }
 
@@ -967,7 +913,7 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
   const bool f64 = !cs.empty() && cs[0].dtype == CUTQC_F64;
   const size_t psz = f64 ? sizeof(LRProblem<double>) : sizeof(LRProblem<float>);
   host.assign(L.bytes, 0);
-  int64_t it = 0, row0 = 0, unit0 = 0;
+  int64_t it = 0, unit0 = 0;
   for (size_t i = 0; i < cs.size(); ++i) {
     const Contraction& c = cs[i];
     if ((c.dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
@@ -994,12 +940,10 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
       rj.T = side ? c.B : c.A;
       rj.rows = side ? c.rowsB : c.rowsA;
       rj.cols = int64_t(1) << (side ? c.fB : c.fA);
-      rj.first_row = row0;
       rj.first = unit0;
-      rj.chunks = (int)std::max<int64_t>(1, rj.cols / BATCH_CHUNK);
+      rj.chunks = (int)row_chunks(rj.cols);
       rj.flags = const_cast<int32_t*>(side ? c.nzB : c.nzA);
       rj.rmax = const_cast<float*>(side ? c.rmaxB : c.rmaxA);
-      row0 += rj.rows;
       unit0 += rj.rows * rj.chunks;
       std::memcpy(host.data() + L.rjobs + (2 * i + side) * sizeof(BatchRowJob), &rj, sizeof(BatchRowJob));
     }
@@ -1015,56 +959,41 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
   *n_items = it;
 }
 
-template <typename T>
-static void launch_batch_typed(const char* t, const BatchLayout& L, int nprob, int* status, cudaStream_t s) {
-  static int per_sm = 0, sms = 0;
-  if (!per_sm) {
-    int dev = 0;
-    CUTQC_CUDA(cudaGetDevice(&dev));
-    CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_cc<T>, 256, 0));
-    if (per_sm < 1) fail(CUTQC_ERR_CUDA, "the batched contraction cannot be resident");
-  }
-  BatchArgs<T> a{};
-  a.probs = reinterpret_cast<const LRProblem<T>*>(t + L.probs);
-  a.cjobs = reinterpret_cast<const CompactJob*>(t + L.cjobs);
-  a.rjobs = reinterpret_cast<const BatchRowJob*>(t + L.rjobs);
-  a.items = reinterpret_cast<const LRItem*>(t + L.items);
-  a.nprob = nprob;
-  a.nrjobs = 2 * nprob;
-  a.nrows = L.nrows;
-  a.nunits = L.nunits;
-  a.n_items = L.n_items;
-  a.barrier = reinterpret_cast<unsigned*>(const_cast<char*>(t) + L.barrier);
-  a.status = status;
-  const int64_t want = std::max(std::max(L.nunits, L.n_items), (int64_t)nprob);
-  const unsigned grid = (unsigned)std::min<int64_t>(want, (int64_t)per_sm * sms);
-  CUTQC_CUDA(cudaMemsetAsync(a.barrier, 0, 3 * sizeof(unsigned), s));
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(256);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;   // every block resident: the grid barriers cannot starve
-  attr[0].val.cooperative = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_batch_cc<T>, a));
-  count_launch();
-  check_launch("k_batch_cc");
-}
-
 void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>& cs, int64_t n_items,
                           cudaStream_t s) {
   if (cs.empty()) return;
   const BatchLayout L = batch_layout(cs);
   if (L.n_items != n_items) fail(CUTQC_ERR_ARG, "batch tables do not match the problems");
-  if (!cs[0].status) fail(CUTQC_ERR_ARG, "the batched contraction needs the device status word");
   const char* t = static_cast<const char*>(dev_tables);
+  const auto* rjobs = reinterpret_cast<const BatchRowJob*>(t + L.rjobs);
+  int32_t* pnz = reinterpret_cast<int32_t*>(const_cast<char*>(t) + L.part_nz);
+  float* pmx = reinterpret_cast<float*>(const_cast<char*>(t) + L.part_max);
+  const int np = (int)cs.size();
+  const unsigned g1 = (unsigned)std::min<int64_t>(L.nunits, 152 * 8);
   if (cs[0].dtype == CUTQC_F64)
-    launch_batch_typed<double>(t, L, (int)cs.size(), cs[0].status, s);
+    k_batch_rowstats<double><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nunits, pnz, pmx);
   else
-    launch_batch_typed<float>(t, L, (int)cs.size(), cs[0].status, s);
+    k_batch_rowstats<float><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nunits, pnz, pmx);
+  count_launch();
+  check_launch("k_batch_rowstats");
+  k_batch_compact<<<(unsigned)np, 256, 0, s>>>(reinterpret_cast<const CompactJob*>(t + L.cjobs), rjobs, np, pnz, pmx);
+  count_launch();
+  check_launch("k_batch_compact");
+  if (cs[0].dtype == CUTQC_F64) {
+    LRArgs<double> a{};
+    a.probs = reinterpret_cast<const LRProblem<double>*>(t + L.probs);
+    a.items = reinterpret_cast<const LRItem*>(t + L.items);
+    a.n_items = n_items;
+    k_lowrank<double><<<lr_grid(n_items), 256, 0, s>>>(a);
+  } else {
+    LRArgs<float> a{};
+    a.probs = reinterpret_cast<const LRProblem<float>*>(t + L.probs);
+    a.items = reinterpret_cast<const LRItem*>(t + L.items);
+    a.n_items = n_items;
+    k_lowrank<float><<<lr_grid(n_items), 256, 0, s>>>(a);
+  }
+  count_launch();
+  check_launch("k_lowrank");
 }
 
 void launch_lowrank(const Contraction& c, cudaStream_t s) {
