@@ -548,10 +548,12 @@ def batch_instances(count: int = 64, seed: int = 0, max_width: int = 16) -> List
     dropped), BV with a random secret}, an even width of 16..28 qubits and 2..4
     chain blocks of at most `max_width` qubits, with a cut budget K <= 8 and
     4^K * 2^n <= 2^40 (cut by construction: crossing gates beyond the budget
-    are dropped)."""
+    are dropped).  Draws whose cut has fewer than 2 wires (a single crossing,
+    as an HWEA chain in two blocks has) are drawn again, so every instance has
+    2 <= K <= 8."""
     rng = np.random.default_rng(seed)
     out = []
-    for i in range(count):
+    while len(out) < count:
         fam = ("hwea", "aqft", "bv")[int(rng.integers(3))]
         n = int(rng.integers(8, 15)) * 2
         s = int(rng.integers(2, 5))
@@ -561,6 +563,8 @@ def batch_instances(count: int = 64, seed: int = 0, max_width: int = 16) -> List
         cs = int(rng.integers(1 << 30))
         c = hwea(n, cs) if fam == "hwea" else aqft(n, cs) if fam == "aqft" else bv(n, cs)
         cc = chain_blocks(c, s, max_cuts=kmax, max_width=max_width)
+        if cc.n_cuts < 2:
+            continue
         cc.family = fam  # type: ignore[attr-defined]
         out.append(cc)
     return out
