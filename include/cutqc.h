@@ -144,7 +144,15 @@ typedef struct {
  * rejected with CUTQC_ERR_ARG before anything runs.  Kronecker terms whose
  * factor rows are all zero are skipped (early termination, Sec. 4.2).
  * sum_p: device double [n_problems] receiving sum_x p(x) accumulated in FP64,
- * or NULL.  No host synchronisation. */
+ * or NULL.  No host synchronisation for a single problem.  Several problems
+ * (a batch) run together: the first call with a given set of shapes and
+ * pointers runs eagerly and is captured into a CUDA graph that identical later
+ * calls replay; every final contraction of at most 16 terms runs in one
+ * launch over all such problems; under CUTQC_AUTO the first call times the
+ * CUDA-core and tensor-core forms of every other FP32 problem's final
+ * contraction once (this synchronises the stream) and keeps the faster per
+ * problem structure, also across processes when the environment variable
+ * CUTQC_AUTOTUNE_CACHE names a file (read on first use, appended to). */
 CUTQC_API int cutqc_reconstruct_fd(const cutqc_problem* problems, int32_t n_problems,
                          void* const* out, int32_t algo, double* sum_p,
                          void* stream);

@@ -16,6 +16,8 @@
 #include <cmath>
 #include <functional>
 #include <cstdint>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -957,6 +959,58 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   return base + need;
 }
 
+// Autotuning cache: the measured final form (CUTQC_CC or CUTQC_AUTO, the
+// tensor-core path) per problem structure, kept for the process and, when
+// the environment variable CUTQC_AUTOTUNE_CACHE names a file, read from it on
+// first use and appended to after each new measurement (one "form key" line
+// per structure, keys prefixed by the device's name and SM count).
+static std::unordered_map<std::string, int> g_tuned;
+static bool g_tuned_loaded = false;
+
+static std::string device_tag() {
+  int dev = 0;
+  CUTQC_CUDA(cudaGetDevice(&dev));
+  cudaDeviceProp pr{};
+  CUTQC_CUDA(cudaGetDeviceProperties(&pr, dev));
+  std::string name(pr.name);
+  for (char& ch : name)
+    if (ch == ' ' || ch == '\t') ch = '_';
+  return name + "/" + std::to_string(pr.multiProcessorCount);
+}
+
+static int autotune_lookup(const std::string& key) {
+  if (!g_tuned_loaded) {
+    g_tuned_loaded = true;
+    if (const char* path = std::getenv("CUTQC_AUTOTUNE_CACHE")) {
+      if (FILE* f = std::fopen(path, "r")) {
+        char buf[8192];
+        while (std::fgets(buf, sizeof buf, f)) {
+          std::string line(buf);
+          while (!line.empty() && (line.back() == '\n' || line.back() == '\r')) line.pop_back();
+          const size_t sp = line.find(' ');
+          if (sp == std::string::npos) continue;
+          const int form = std::atoi(line.substr(0, sp).c_str());
+          if (form == CUTQC_CC || form == CUTQC_AUTO) g_tuned[line.substr(sp + 1)] = form;
+        }
+        std::fclose(f);
+      }
+    }
+  }
+  auto it = g_tuned.find(device_tag() + "|" + key);
+  return it == g_tuned.end() ? -1 : it->second;
+}
+
+static void autotune_store(const std::string& key, int form) {
+  const std::string full = device_tag() + "|" + key;
+  g_tuned[full] = form;
+  if (const char* path = std::getenv("CUTQC_AUTOTUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%d %s\n", form, full.c_str());
+      std::fclose(f);
+    }
+  }
+}
+
 // Batched full definition.  Every problem gets its own region of the
 // workspace, so problems are independent and run on parallel stream branches.
 // The first call with a given set of shapes and pointers runs eagerly (and,
@@ -984,10 +1038,18 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
       return t;
     };
   };
-  // autotune the final form once per plan (eager, outside any capture)
+  // autotune the final form once per plan (eager, outside any capture); a
+  // choice measured before (this process, or a cache file named by
+  // CUTQC_AUTOTUNE_CACHE) is reused
   for (int i = 0; i < n; ++i) {
     Plan& P = *plans[i];
     if (algo != CUTQC_AUTO || P.dtype != CUTQC_F32 || P.tuned >= 0) continue;
+    const std::string tkey = fd_key(&problems[i], 0, nullptr, 0);
+    const int cached = autotune_lookup(tkey);
+    if (cached >= 0) {
+      P.tuned = cached;
+      continue;
+    }
     cudaEvent_t e0, e1;
     CUTQC_CUDA(cudaEventCreate(&e0));
     CUTQC_CUDA(cudaEventCreate(&e1));
@@ -1012,6 +1074,7 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     P.tuned = choice == CUTQC_CC ? CUTQC_CC : CUTQC_AUTO;
+    autotune_store(tkey, P.tuned);
   }
   // workspace regions
   std::vector<size_t> off(n + 1, 0);

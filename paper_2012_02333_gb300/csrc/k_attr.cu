@@ -397,10 +397,11 @@ __global__ void k_attr_inits(T* __restrict__ TQ, int64_t inner) {
   }
 }
 
-// Eq. 3 and Eq. 2 in one pass (k_in <= 2, k_out <= 2): one thread per x.
-// For every measurement basis combination mb it loads the 2^KOUT outcomes of
-// all 4^KIN physical inits' variants (16-byte loads when the measured cut
-// qubits are the lowest local bits: consecutive threads, consecutive x), takes
+// Eq. 3 and Eq. 2 in one pass (k_in <= 2, k_out <= 2): one thread per
+// (measurement basis combination mb, x), x fastest.  It loads the 2^KOUT
+// outcomes of all 4^KIN physical inits' variants with basis mb (16-byte loads
+// when the measured cut qubits are the lowest local bits: consecutive threads,
+// consecutive x), takes
 // every signed outcome sum by a butterfly over the slots (Eq. 3), and for
 // each Pauli row b that mb serves combines the inits slot by slot into the
 // Pauli operators (Eq. 2) and stores the 4^KIN entries T[a][b][x].  P is read
@@ -419,10 +420,13 @@ __global__ void k_attr_fused(const T* __restrict__ P, const AttrArgs a, T* __res
   int npow3 = 1;
 #pragma unroll
   for (int j = 0; j < KOUT; ++j) npow3 *= 3;
-  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < nx; x += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx * npow3;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t x = t & (nx - 1);
+    const int mb = (int)(t >> f);
     const uint32_t xl = (uint32_t)x;
     const uint64_t yx = tab_x[0][xl & 255] | tab_x[1][(xl >> 8) & 255] | tab_x[2][(xl >> 16) & 255] | tab_x[3][xl >> 24];
-    for (int mb = 0; mb < npow3; ++mb) {
+    {
       // the outcomes of every init's variant with basis combination mb
       T v[NS][NM];
 #pragma unroll
@@ -510,8 +514,10 @@ __global__ void k_attr_fused(const T* __restrict__ P, const AttrArgs a, T* __res
 template <typename T>
 bool launch_fused(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
   if (a.k_in > 2 || a.k_out > 2) return false;
-  const int64_t nx = int64_t(1) << a.n_eff;
-  int64_t g = (nx + 255) / 256;
+  int64_t pow3 = 1;
+  for (int j = 0; j < a.k_out; ++j) pow3 *= 3;
+  const int64_t nt = (int64_t(1) << a.n_eff) * pow3;
+  int64_t g = (nt + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
   // the measured cut qubits on the lowest local bits (any order): a thread's
   // outcomes are one aligned 16-byte run

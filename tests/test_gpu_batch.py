@@ -69,3 +69,42 @@ def test_batched_64_instances_graph_replay(env, algo):
             assert sums[i].item() == pytest.approx(torch.sum(o, dtype=torch.float64).item(), abs=1e-6)
     # the replays launch no kernels through the host API: one graph launch each
     assert launches[1] == 0 and launches[2] == 0
+
+
+_CACHE_RUN = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, {root!r})
+from oracle import attribution as at
+from paper_2012_02333_gb300 import circuits as C, cutqc
+full = C.batch_instances(64, 0)
+batch = [full[i] for i in (8, 35, 46, 0, 7)]   # three 4-cut pairs (256 terms: the forms are timed) and two chains
+ts = [[torch.tensor(T.reshape(-1).astype(np.float32), device="cuda") for T in at.tensors(cc)] for cc in batch]
+problems = [cutqc.Problem.from_cut(cc, t) for cc, t in zip(batch, ts)]
+outs = [torch.empty(2 ** cc.n, device="cuda") for cc in batch]
+cutqc.cutqc_reconstruct_fd(problems, outs, "auto")
+torch.cuda.synchronize()
+np.save(sys.argv[1], np.concatenate([o[:4096].double().cpu().numpy() for o in outs]))
+"""
+
+
+def test_autotune_cache_file(env, tmp_path):
+    """Under CUTQC_AUTOTUNE_CACHE the batch's measured form choices are written
+    to the named file by one process and read back by the next, which gives
+    the same outputs."""
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    envv = dict(os.environ, CUTQC_AUTOTUNE_CACHE=str(cache))
+    code = _CACHE_RUN.format(root=root)
+    outs = []
+    for k in range(2):
+        f = tmp_path / f"out{k}.npy"
+        r = subprocess.run([sys.executable, "-c", code, str(f)], env=envv, capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-3000:]
+        outs.append(np.load(f))
+        if k == 0:
+            lines = cache.read_text().splitlines()
+            assert lines and all(l.split(" ", 1)[0] in ("0", "1") for l in lines)
+            n_first = len(lines)
+    assert len(cache.read_text().splitlines()) == n_first    # nothing measured again
+    assert np.array_equal(outs[0], outs[1])
