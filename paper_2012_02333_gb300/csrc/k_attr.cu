@@ -15,9 +15,10 @@
 // 1 -> -1), and y(x, m) the subcircuit's local bit string holding the output
 // bits x and the measured cut-qubit outcomes m.
 //
-// With at most two init and two measurement slots one kernel applies both
-// equations in a single pass (k_attr_fused).  Otherwise two streaming passes
-// over memory, no scratch: k_attr_outcomes applies Eq. 3
+// Two streaming passes over memory, no scratch (a single-pass form that
+// applies both equations per output was measured slower: its threads each
+// hold all inits of one basis combination, too few to keep the loads in
+// flight): k_attr_outcomes applies Eq. 3
 // (one thread per (s, b, x): the 2^k_out outcomes of the variant that serves
 // b, read where consecutive threads take consecutive x) and writes the
 // result into the output buffer; k_attr_inits then applies Eq. 2 in place
@@ -397,149 +398,6 @@ __global__ void k_attr_inits(T* __restrict__ TQ, int64_t inner) {
   }
 }
 
-// Eq. 3 and Eq. 2 in one pass (k_in <= 2, k_out <= 2): one thread per
-// (measurement basis combination mb, x), x fastest.  It loads the 2^KOUT
-// outcomes of all 4^KIN physical inits' variants with basis mb (16-byte loads
-// when the measured cut qubits are the lowest local bits: consecutive threads,
-// consecutive x), takes
-// every signed outcome sum by a butterfly over the slots (Eq. 3), and for
-// each Pauli row b that mb serves combines the inits slot by slot into the
-// Pauli operators (Eq. 2) and stores the 4^KIN entries T[a][b][x].  P is read
-// once and T written once: no second pass over the tensor.
-template <typename T, int KIN, int KOUT>
-__global__ void k_attr_fused(const T* __restrict__ P, const AttrArgs a, T* __restrict__ Q, int contig) {
-  __shared__ uint64_t tab_x[4][256];
-  __shared__ uint64_t tab_m[2][256];
-  fill_tables<T>(a, tab_x, tab_m);
-  constexpr int NS = 1 << (2 * KIN), NM = 1 << KOUT;
-  const int f = a.n_eff;
-  const int64_t nx = int64_t(1) << f;
-  uint64_t dm[NM];
-#pragma unroll
-  for (int m = 0; m < NM; ++m) dm[m] = tab_m[0][m];
-  int npow3 = 1;
-#pragma unroll
-  for (int j = 0; j < KOUT; ++j) npow3 *= 3;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nx * npow3;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t x = t & (nx - 1);
-    const int mb = (int)(t >> f);
-    const uint32_t xl = (uint32_t)x;
-    const uint64_t yx = tab_x[0][xl & 255] | tab_x[1][(xl >> 8) & 255] | tab_x[2][(xl >> 16) & 255] | tab_x[3][xl >> 24];
-    {
-      // the outcomes of every init's variant with basis combination mb
-      T v[NS][NM];
-#pragma unroll
-      for (int sv = 0; sv < NS; ++sv) {
-        const T* base = P + ((int64_t)(sv * npow3 + mb) << a.d) + yx;
-        if constexpr (sizeof(T) == 4 && KOUT == 2) {
-          if (contig) {
-            const float4 q = __ldg(reinterpret_cast<const float4*>(base));
-            const float w[4] = {q.x, q.y, q.z, q.w};
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-              T r = w[0];
-#pragma unroll
-              for (int t = 1; t < 4; ++t) r = (int)dm[m] == t ? w[t] : r;
-              v[sv][m] = r;
-            }
-            continue;
-          }
-        }
-#pragma unroll
-        for (int m = 0; m < NM; ++m) v[sv][m] = __ldg(base + dm[m]);
-      }
-      // Eq. 3: v[s][p] = sum_m (-1)^{popc(m & p)} outcome m
-#pragma unroll
-      for (int sv = 0; sv < NS; ++sv)
-#pragma unroll
-        for (int j = 0; j < KOUT; ++j)
-#pragma unroll
-          for (int m = 0; m < NM; ++m)
-            if (!((m >> j) & 1)) {
-              const T u = v[sv][m], w = v[sv][m | (1 << j)];
-              v[sv][m] = u + w;
-              v[sv][m | (1 << j)] = u - w;
-            }
-      int dig[KOUT > 0 ? KOUT : 1];
-      {
-        int r = mb;
-#pragma unroll
-        for (int j = KOUT - 1; j >= 0; --j) {
-          dig[j] = r % 3;
-          r /= 3;
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < NM; ++p) {
-        bool valid = true;
-        uint32_t b = 0;
-#pragma unroll
-        for (int j = 0; j < KOUT; ++j) {
-          int pauli;
-          if (!((p >> j) & 1)) {
-            if (dig[j] != 0) valid = false;
-            pauli = 0;
-          } else {
-            pauli = dig[j] == 0 ? 3 : dig[j];
-          }
-          b = 4 * b + (uint32_t)pauli;
-        }
-        if (!valid) continue;
-        // Eq. 2 over the init slots (slot 0 the most significant base-4 digit)
-        T w[NS];
-#pragma unroll
-        for (int sv = 0; sv < NS; ++sv) w[sv] = v[sv][p];
-#pragma unroll
-        for (int j = 0; j < KIN; ++j) {
-          const int stride = 1 << (2 * (KIN - 1 - j));
-#pragma unroll
-          for (int g = 0; g < NS; ++g) {
-            if ((g / stride) % 4 != 0) continue;
-            const T v0 = w[g], v1 = w[g + stride], v2 = w[g + 2 * stride], v3 = w[g + 3 * stride];
-            const T s01 = v0 + v1;
-            w[g] = s01;
-            w[g + stride] = (v2 + v2) - s01;
-            w[g + 2 * stride] = (v3 + v3) - s01;
-            w[g + 3 * stride] = v0 - v1;
-          }
-        }
-#pragma unroll
-        for (int av = 0; av < NS; ++av) Q[(((int64_t)av << (2 * KOUT)) + b) * nx + x] = snap_small(w[av]);
-      }
-    }
-  }
-}
-
-template <typename T>
-bool launch_fused(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
-  if (a.k_in > 2 || a.k_out > 2) return false;
-  int64_t pow3 = 1;
-  for (int j = 0; j < a.k_out; ++j) pow3 *= 3;
-  const int64_t nt = (int64_t(1) << a.n_eff) * pow3;
-  int64_t g = (nt + 255) / 256;
-  if (g > 152 * 16) g = 152 * 16;
-  // the measured cut qubits on the lowest local bits (any order): a thread's
-  // outcomes are one aligned 16-byte run
-  bool contig = sizeof(T) == 4 && a.k_out == 2 && (reinterpret_cast<uintptr_t>(P) & 15) == 0;
-  for (int j = 0; j < a.k_out; ++j) contig = contig && a.meas_pos[j] < a.k_out;
-  const dim3 gr((unsigned)g), bl(256);
-  switch (a.k_in * 3 + a.k_out) {
-    case 0: k_attr_fused<T, 0, 0><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 1: k_attr_fused<T, 0, 1><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 2: k_attr_fused<T, 0, 2><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 3: k_attr_fused<T, 1, 0><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 4: k_attr_fused<T, 1, 1><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 5: k_attr_fused<T, 1, 2><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 6: k_attr_fused<T, 2, 0><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    case 7: k_attr_fused<T, 2, 1><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-    default: k_attr_fused<T, 2, 2><<<gr, bl, 0, s>>>(P, a, out, contig); break;
-  }
-  count_launch();
-  check_launch("k_attr_fused");
-  return true;
-}
-
 template <typename T>
 void launch_two_pass(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
   const int64_t n_out = (int64_t(1) << (2 * (a.k_in + a.k_out))) << a.n_eff;
@@ -617,9 +475,6 @@ void launch_attribute(const void* P, int dtype, int d, int k_in, const int* meas
   for (int i = 0; i < n_eff; ++i) a.out_pos[i] = d - 1 - out_q[i];
   a.pow3_kout = 1;
   for (int j = 0; j < k_out; ++j) a.pow3_kout *= 3;
-  if (dtype == CUTQC_F64 ? launch_fused(static_cast<const double*>(P), a, static_cast<double*>(tensor), s)
-                        : launch_fused(static_cast<const float*>(P), a, static_cast<float*>(tensor), s))
-    return;
   if (k_in <= 3) {
     if (dtype == CUTQC_F64)
       launch_two_pass(static_cast<const double*>(P), a, static_cast<double*>(tensor), s);

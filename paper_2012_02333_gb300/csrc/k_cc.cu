@@ -653,7 +653,7 @@ struct LRItem {
   int n0;
   int64_t m0;
 };
-constexpr int LR_MB = 64;      // rows per item
+constexpr int LR_MB = 256;     // rows per item
 constexpr int LR_NT = 1024;    // columns per item (256 threads x 4)
 
 template <typename T>
@@ -675,7 +675,7 @@ __device__ __forceinline__ FFs ffs_add(FFs a, float b) {
 }
 
 template <typename T, int KC>
-__device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m0, int n0, T (*As)[16],
+__device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m0, int n0, T (*As)[KC],
                                         uint64_t* gAs) {
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t M = int64_t(1) << p.fA;
@@ -752,9 +752,11 @@ __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m
   __syncthreads();   // the panel is rewritten by the next item
 }
 
-template <typename T>
-__global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
-  __shared__ T As[LR_MB][16];
+// KC = 4 (one cut between the final groups) or 16 (two): the register and
+// shared-memory footprint of the smaller form lets more blocks share an SM
+template <typename T, int KC>
+__global__ __launch_bounds__(256, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)) void k_lowrank(const LRArgs<T> a) {
+  __shared__ T As[LR_MB][KC];
   __shared__ uint64_t gAs[LR_MB];
   for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     LRProblem<T> p;
@@ -770,15 +772,10 @@ __global__ __launch_bounds__(256) void k_lowrank(const LRArgs<T> a) {
       m0 = (it / a.one_tiles_n) * LR_MB;
       n0 = (int)(it % a.one_tiles_n) * LR_NT;
     }
-    const int kc = *p.kcount;
-    if (kc <= 4)
-      lr_item<T, 4>(p, kc, m0, n0, As, gAs);
-    else if (kc <= 8)
-      lr_item<T, 8>(p, kc, m0, n0, As, gAs);
-    else
-      lr_item<T, 16>(p, kc, m0, n0, As, gAs);
+    lr_item<T, KC>(p, *p.kcount, m0, n0, As, gAs);
   }
 }
+
 
 // ---- every low-rank problem of a batch in three launches -----------------
 // k_batch_rowstats: the row non-zero flags and max |.| of every problem's two
@@ -858,14 +855,23 @@ LRProblem<T> lr_problem(const Contraction& c) {
   return p;
 }
 
-int lr_grid(int64_t items) {
+int lr_grid(int64_t items, int per_sm) {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     CUTQC_CUDA(cudaGetDevice(&dev));
     CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  return (int)std::min<int64_t>(items, (int64_t)sms * 4);
+  return (int)std::min<int64_t>(items, (int64_t)sms * per_sm);
+}
+
+// one launch of the low-rank kernel of term class KC (4 or 16)
+template <typename T, int KC>
+void lr_launch(const LRArgs<T>& a, cudaStream_t s) {
+  if (a.n_items == 0) return;
+  k_lowrank<T, KC><<<lr_grid(a.n_items, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)), 256, 0, s>>>(a);
+  count_launch();
+  check_launch("k_lowrank");
 }
 
 }  // namespace
@@ -947,15 +953,22 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
       unit0 += rj.rows * rj.chunks;
       std::memcpy(host.data() + L.rjobs + (2 * i + side) * sizeof(BatchRowJob), &rj, sizeof(BatchRowJob));
     }
-    const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
-    const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
-    for (int64_t tm = 0; tm < tiles_m; ++tm)
-      for (int64_t tn = 0; tn < tiles_n; ++tn) {
-        LRItem item{(int)i, (int)(tn * LR_NT), tm * LR_MB};
-        std::memcpy(host.data() + L.items + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
-        ++it;
-      }
   }
+  // items: the problems of at most 4 terms first (one launch of the small
+  // form), then the rest
+  for (int cls = 0; cls < 2; ++cls)
+    for (size_t i = 0; i < cs.size(); ++i) {
+      const Contraction& c = cs[i];
+      if ((c.kmax <= 4) != (cls == 0)) continue;
+      const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
+      const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
+      for (int64_t tm = 0; tm < tiles_m; ++tm)
+        for (int64_t tn = 0; tn < tiles_n; ++tn) {
+          LRItem item{(int)i, (int)(tn * LR_NT), tm * LR_MB};
+          std::memcpy(host.data() + L.items + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
+          ++it;
+        }
+    }
   *n_items = it;
 }
 
@@ -979,21 +992,28 @@ void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>
   k_batch_compact<<<(unsigned)np, 256, 0, s>>>(reinterpret_cast<const CompactJob*>(t + L.cjobs), rjobs, np, pnz, pmx);
   count_launch();
   check_launch("k_batch_compact");
+  int64_t n4 = 0;
+  for (const Contraction& c : cs)
+    if (c.kmax <= 4) n4 += lowrank_items(c);
   if (cs[0].dtype == CUTQC_F64) {
     LRArgs<double> a{};
     a.probs = reinterpret_cast<const LRProblem<double>*>(t + L.probs);
     a.items = reinterpret_cast<const LRItem*>(t + L.items);
-    a.n_items = n_items;
-    k_lowrank<double><<<lr_grid(n_items), 256, 0, s>>>(a);
+    a.n_items = n4;
+    lr_launch<double, 4>(a, s);
+    a.items += n4;
+    a.n_items = n_items - n4;
+    lr_launch<double, 16>(a, s);
   } else {
     LRArgs<float> a{};
     a.probs = reinterpret_cast<const LRProblem<float>*>(t + L.probs);
     a.items = reinterpret_cast<const LRItem*>(t + L.items);
-    a.n_items = n_items;
-    k_lowrank<float><<<lr_grid(n_items), 256, 0, s>>>(a);
+    a.n_items = n4;
+    lr_launch<float, 4>(a, s);
+    a.items += n4;
+    a.n_items = n_items - n4;
+    lr_launch<float, 16>(a, s);
   }
-  count_launch();
-  check_launch("k_lowrank");
 }
 
 void launch_lowrank(const Contraction& c, cudaStream_t s) {
@@ -1007,16 +1027,20 @@ void launch_lowrank(const Contraction& c, cudaStream_t s) {
     a.one = lr_problem<double>(c);
     a.n_items = items;
     a.one_tiles_n = tiles_n;
-    k_lowrank<double><<<lr_grid(items), 256, 0, s>>>(a);
+    if (c.kmax <= 4)
+      lr_launch<double, 4>(a, s);
+    else
+      lr_launch<double, 16>(a, s);
   } else {
     LRArgs<float> a{};
     a.one = lr_problem<float>(c);
     a.n_items = items;
     a.one_tiles_n = tiles_n;
-    k_lowrank<float><<<lr_grid(items), 256, 0, s>>>(a);
+    if (c.kmax <= 4)
+      lr_launch<float, 4>(a, s);
+    else
+      lr_launch<float, 16>(a, s);
   }
-  count_launch();
-  check_launch("k_lowrank");
   if (c.profile) prof_end(s, ev);
 }
 

@@ -88,9 +88,9 @@ def synthetic_sub(d, k_in, k_out, seed):
                                          (7, 2, 2), (6, 1, 1), (5, 2, 0), (4, 0, 1), (9, 2, 1), (3, 1, 2)])
 def test_attribute_all_kernel_forms(env, d, k_in, k_out):
     """Slot counts that select each form: k_out > 4 (outcome gather), k_in > 3
-    (single kernel), n_eff < 2, the variant-centred two-pass form, and the
-    single-pass form for at most two init and two measurement slots; random
-    layouts of the measured qubits among the local qubits."""
+    (single kernel), n_eff < 2, the variant-centred form for one to four
+    measurement slots and zero to three init slots; random layouts of the
+    measured qubits among the local qubits."""
     torch, cutqc = env
     from oracle import attribution as at
     rng = np.random.default_rng(d * 100 + k_in * 10 + k_out)
