@@ -189,6 +189,30 @@ def job_value(n_out_per_rank, world, ms):
     return world * n_out_per_rank / (ms / 1e3)
 
 
+def kept_terms(cc, tensors):
+    """The algorithmic work: Kronecker terms whose factor rows are all
+    non-zero (early termination, Sec. 4.2), counted on the host."""
+    import numpy as np
+    from itertools import product
+    rows_nz = []
+    for s, t in zip(cc.subs, tensors):
+        v = t.cpu().numpy().reshape(4 ** s.k_in * 4 ** s.k_out, -1)
+        rows_nz.append(np.any(v != 0, axis=1))
+    k_eff = 0
+    for dg in product(range(4), repeat=cc.n_cuts):
+        ok = True
+        for s, nz in zip(cc.subs, rows_nz):
+            a = 0
+            for c in s.in_cut:
+                a = 4 * a + dg[c]
+            b = 0
+            for c in s.out_cut:
+                b = 4 * b + dg[c]
+            ok &= bool(nz[a * 4 ** s.k_out + b])
+        k_eff += ok
+    return k_eff
+
+
 def step_ms(ts):
     """Median, best and mean of per-step times (ms); the median is the figure
     the line reports."""
@@ -326,24 +350,7 @@ def run_ours(args):
     # input preparation (untimed): GPU-simulated FP32 subcircuit tensors
     tensors = cutqc.simulate_tensors(cc, torch.float32, dev)
     host = [t.cpu().pin_memory() for t in tensors]
-    # algorithmic work: Kronecker terms whose factor rows are all non-zero
-    rows_nz = []
-    for s, t in zip(cc.subs, host):
-        v = t.numpy().reshape(4 ** s.k_in * 4 ** s.k_out, -1)
-        rows_nz.append(np.any(v != 0, axis=1))
-    from itertools import product
-    k_eff = 0
-    for dg in product(range(4), repeat=cc.n_cuts):
-        ok = True
-        for s, nz in zip(cc.subs, rows_nz):
-            a = 0
-            for c in s.in_cut:
-                a = 4 * a + dg[c]
-            b = 0
-            for c in s.out_cut:
-                b = 4 * b + dg[c]
-            ok &= bool(nz[a * 4 ** s.k_out + b])
-        k_eff += ok
+    k_eff = kept_terms(cc, host)
     out = torch.empty(n_out, dtype=torch.float32, device=dev)
     sum_p = torch.empty(1, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
@@ -626,6 +633,24 @@ def run_other(args):
                  "expected_cut": float(loss.item()),
                  "cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd([problem], [out], "cc", sp), "cc"),
                  "cc_only": "forward on the FP32 CUDA-core form"}
+        # roofline of the forward step: the slower of the split products at the
+        # BF16 peak and the output plus tensors at the HBM rate
+        cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp)
+        nseg, _ = cutqc.last_split()
+        k_eff = kept_terms(cc, ts)
+        pk, pk_src = peaks()
+        t_tc = nseg * 2.0 * k_eff * 2 ** cc.n / (pk["bf16_tflops"] * 1e12)
+        b_alg = 2 ** cc.n * 4 + sum(t.numel() * 4 for t in ts)
+        t_hbm = b_alg / (pk["hbm_gbs"] * 1e9)
+        if t_tc >= t_hbm:
+            roof = {"bound": "tensor", "achieved": nseg * 2.0 * k_eff * 2 ** cc.n / (ms / 1e3) / 1e12,
+                    "peak": pk["bf16_tflops"], "unit": "TFLOP/s"}
+        else:
+            roof = {"bound": "hbm", "achieved": b_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s"}
+        roof.update({"frac": max(t_tc, t_hbm) / (ms / 1e3), "traffic": None, "split_products": nseg,
+                     "kept_terms": k_eff, "t_roof_us": 1e6 * max(t_tc, t_hbm), "peak_file": pk_src,
+                     "of": "the whole forward step (preparation and contraction)"})
+        extra["roofline"] = roof
         if check:
             cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp)
             cpu, err, _ = oracle_fd_leg(cc, [t.double().cpu().numpy() for t in ts],
@@ -782,6 +807,19 @@ def run_other(args):
         ms = timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto"))
         extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "cc"), "cc"),
                  "cc_only": "one recursion with the final contraction on the FP32 CUDA-core form"}
+        # HBM roofline of one recursion: every tensor read once by the merges,
+        # the merged tensors (rounded sum and compensation, 8 bytes a value)
+        # written once and read once, the 2^30 bins written once
+        merged = 0
+        for sub in cc.subs:
+            a_c = sum(1 for q in sub.out_qubit if roles[q] == 0)
+            merged += (4 ** (sub.k_in + sub.k_out)) * (2 ** a_c) * 8
+        b_alg = sum(t.numel() * 4 for t in ts) + 2 * merged + bins.numel() * 4
+        pk, pk_src = peaks()
+        extra["roofline"] = {"bound": "hbm", "achieved": b_alg / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
+                             "unit": "GB/s", "frac": b_alg / (ms / 1e3) / 1e9 / pk["hbm_gbs"], "traffic": None,
+                             "algorithmic_bytes": b_alg, "peak_file": pk_src,
+                             "of": "one recursion: merges, contraction into the bins, top-32 and FP64 re-ranking"}
         if check:
             from oracle import reconstruct as rc
             top = cutqc.cutqc_reconstruct_dd(problem, roles, bins, 32, "auto")
@@ -865,7 +903,22 @@ def run_peaks(args):
         out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e12
         del a, b, c
     torch.backends.cuda.matmul.allow_tf32 = False
-    print(json.dumps({"peaks": out, "how": "torch.matmul 8192^3, best of %d, CUDA events" % args.steps}), flush=True)
+    # write-only HBM rate (context for kernels whose traffic is all stores):
+    # torch's fill of 4 GiB, best of `steps`
+    buf = torch.empty(1 << 30, dtype=torch.float32, device="cuda")
+    best = 1e30
+    for i in range(max(args.warmup, 3) + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        buf.fill_(float(i))
+        e1.record()
+        torch.cuda.synchronize()
+        if i >= max(args.warmup, 3):
+            best = min(best, e0.elapsed_time(e1))
+    out["write_gbs"] = buf.numel() * 4 / (best / 1e3) / 1e9
+    del buf
+    print(json.dumps({"peaks": out, "how": "torch.matmul 8192^3 and torch fill of 4 GiB, best of %d, CUDA events"
+                      % args.steps}), flush=True)
 
 
 def main():

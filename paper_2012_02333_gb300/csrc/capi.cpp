@@ -1099,10 +1099,10 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
   // Low-rank CUDA-core final contractions are not launched per problem: they
   // are collected (per dtype) and run as one launch over a device work list.
   std::vector<Contraction> lr[2];
-  auto launch_deferred = [&](cudaStream_t st) {
+  auto launch_deferred = [&](cudaStream_t st, const char* group) {
     for (int d = 0; d < 2; ++d) {
       if (lr[d].empty()) continue;
-      const std::string tk = gk + "#lr" + std::to_string(d);
+      const std::string tk = gk + "#lr" + group + std::to_string(d);
       std::vector<char> host;
       int64_t items = 0;
       lowrank_batch_tables(lr[d], host, &items);
@@ -1126,7 +1126,7 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
   };
   // the problems whose final contraction is deferred into the batched
   // low-rank launches (the same decision run_plan takes), and the rest
-  std::vector<int> deferred, others;
+  std::vector<int> deferred, direct, others;
   for (int i = 0; i < n; ++i) {
     const Plan& P = *plans[i];
     const Step& st = P.steps.back();
@@ -1140,11 +1140,15 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     const int a = algo_of(i);
     const bool cc_final = a == CUTQC_CC || (a == CUTQC_AUTO && (lowrank_eligible(c) || P.dtype != CUTQC_F32)) ||
                           !tc_supported(c);
-    (cc_final && lowrank_eligible(c) && !is_host_memory(out[i]) ? deferred : others).push_back(i);
+    const bool defer = cc_final && lowrank_eligible(c) && !is_host_memory(out[i]);
+    // a deferred problem without group builds launches nothing of its own
+    (defer ? (P.steps.size() == 1 ? direct : deferred) : others).push_back(i);
   }
   // eager run of the whole batch on the caller's stream
+  for (int i : direct) run_one(i, s, ws + off[i], true);
+  launch_deferred(s, "a");
   for (int i : deferred) run_one(i, s, ws + off[i], true);
-  launch_deferred(s);
+  launch_deferred(s, "b");
   for (int i : others) run_one(i, s, ws + off[i], false);
   // capture the same launches over parallel branches for later calls
   if (!ds.fork) {
@@ -1161,16 +1165,19 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     CUTQC_CUDA(cudaStreamBeginCapture(ds.branch[0], cudaStreamCaptureModeThreadLocal));
     CUTQC_CUDA(cudaEventRecord(ds.fork, ds.branch[0]));
     for (int b = 1; b < kBranches; ++b) CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[b], ds.fork, 0));
-    // branch 0 runs the batched low-rank launches once the deferred problems'
-    // group builds (on the other branches) are done; the other problems follow
-    // on branches 1.. and run beside it
+    // branch 0 runs the batched low-rank launches: at once for the problems
+    // without group builds, then for the rest once their group builds (on
+    // the other branches) are done; the other problems follow on branches
+    // 1.. and run beside it
+    for (int i : direct) run_one(i, ds.branch[0], ws + off[i], true);
+    launch_deferred(ds.branch[0], "a");
     int k = 0;
     for (int i : deferred) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], true);
     for (int b = 1; b < kBranches; ++b) {
       CUTQC_CUDA(cudaEventRecord(ds.mid[b], ds.branch[b]));
       CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.mid[b], 0));
     }
-    launch_deferred(ds.branch[0]);
+    launch_deferred(ds.branch[0], "b");
     for (int i : others) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], false);
     for (int b = 1; b < kBranches; ++b) {
       CUTQC_CUDA(cudaEventRecord(ds.join[b], ds.branch[b]));
