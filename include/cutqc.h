@@ -101,7 +101,9 @@ typedef enum { CUTQC_F64 = 0, CUTQC_F32 = 1 } cutqc_dtype;
  *                  bytes.  Never chosen by CUTQC_AUTO.
  *  CUTQC_AUTO      FP64 tensors: CUTQC_CC.  FP32 tensors: CUTQC_CC when the
  *                  final contraction has at most 16 Kronecker terms (a
- *                  streaming form whose output stream is all the work),
+ *                  streaming form whose output stream is all the work) and
+ *                  no top bins are asked for (cutqc_reconstruct_dd with
+ *                  topk > 0 keeps them in the tensor-core epilogue),
  *                  otherwise the tensor-core path when the shape allows it
  *                  (else CUTQC_CC), with the
  *                  number of products chosen on the device per call from

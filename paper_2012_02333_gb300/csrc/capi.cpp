@@ -797,11 +797,14 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
   }
   // decide the algorithm of the final step: under CUTQC_AUTO a contraction
   // of at most 16 kept terms takes the streaming CUDA-core form (its output
-  // stream is all the work; measured faster than the tensor-core form), the
-  // rest of FP32 the tensor-core form where the shape allows it
+  // stream is all the work; measured faster than the tensor-core form) unless
+  // the caller wants the top bins, which the tensor-core epilogue keeps while
+  // writing them (a separate scan of 2^30 bins costs more); the rest of FP32
+  // the tensor-core form where the shape allows it
+  const bool want_topk = topk_nlists && topk_back_off != SIZE_MAX;
   int final_algo = algo;
   if (final_algo == CUTQC_AUTO)
-    final_algo = (P.dtype == CUTQC_F32 && !lowrank_eligible(cs.back())) ? CUTQC_TC_BF16X3 : CUTQC_CC;
+    final_algo = (P.dtype == CUTQC_F32 && (!lowrank_eligible(cs.back()) || want_topk)) ? CUTQC_TC_BF16X3 : CUTQC_CC;
   if (algo == CUTQC_AUTO && final_algo == CUTQC_CC) algo = CUTQC_CC;
   const bool tc_algo = final_algo == CUTQC_TC_BF16X3 || final_algo == CUTQC_TC_BF16X6 || final_algo == CUTQC_TC_TF32X3;
   if (tc_algo && P.dtype != CUTQC_F32) fail(CUTQC_ERR_ARG, "the tensor-core forms need FP32 tensors");
