@@ -687,9 +687,11 @@ __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m
   const int32_t* ra = p.crow;
   const int32_t* rb = p.crow + p.kmax;
   // the A panel and the rows' output offsets
+  // the panel carries the scale 2^-K (a power of two: exact)
+  const T sc = (T)p.scale;
   for (int idx = tid; idx < LR_MB * KC; idx += 256) {
     const int i = idx % LR_MB, k = idx / LR_MB;
-    As[i][k] = (k < kc && m0 + i < M) ? p.A[(int64_t)ra[k] * M + m0 + i] : T(0);
+    As[i][k] = (k < kc && m0 + i < M) ? p.A[(int64_t)ra[k] * M + m0 + i] * sc : T(0);
   }
   for (int i = tid; i < LR_MB; i += 256) gAs[i] = m0 + i < M ? deposit(p.depA, p.nbA, (uint64_t)(m0 + i)) : 0;
   // this thread's 4 columns of the kc B rows
@@ -719,20 +721,31 @@ __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m
   }
   const uint64_t gB = deposit(p.depB, p.nbB, (uint64_t)n);
   __syncthreads();
-  const T sc = (T)p.scale;
   FFs acc{0.0f, 0.0f};
   double acc64 = 0.0;
   const int rows = (int)((M - m0) < LR_MB ? (M - m0) : LR_MB);
   for (int i = rs; i < rows; i += rpp) {
     T v[4] = {T(0), T(0), T(0), T(0)};
+    // the row's panel values, 16 bytes per shared-memory read (zero beyond kc)
 #pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      const T a = As[i][k];   // zero beyond kc
+    for (int k0 = 0; k0 < KC; k0 += 16 / (int)sizeof(T)) {
+      T a[16 / sizeof(T)];
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = *reinterpret_cast<const float4*>(&As[i][k0]);
+        a[0] = q.x;
+        a[1] = q.y;
+        a[2] = q.z;
+        a[3] = q.w;
+      } else {
+        const double2 q = *reinterpret_cast<const double2*>(&As[i][k0]);
+        a[0] = q.x;
+        a[1] = q.y;
+      }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) v[j] = fma(a, b[k][j], v[j]);
+      for (int kk = 0; kk < 16 / (int)sizeof(T); ++kk)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = fma(a[kk], b[k0 + kk][j], v[j]);
     }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] *= sc;
     T* dst = p.out + gAs[i] + gB;
     if constexpr (sizeof(T) == 4) {
       __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
@@ -756,7 +769,7 @@ __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m
 // shared-memory footprint of the smaller form lets more blocks share an SM
 template <typename T, int KC>
 __global__ __launch_bounds__(256, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)) void k_lowrank(const LRArgs<T> a) {
-  __shared__ T As[LR_MB][KC];
+  __shared__ __align__(16) T As[LR_MB][KC];
   __shared__ uint64_t gAs[LR_MB];
   for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
     LRProblem<T> p;
