@@ -289,3 +289,28 @@ def test_single_row_operands_of_long_rows(env, algo):
     out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
     assert np.abs(out.double().cpu().numpy() - ref).max() <= TOL32
     assert float(sp.item()) == pytest.approx(ref.sum(), abs=TOL32)
+
+
+@pytest.mark.parametrize("algo", ["tc_bf16x3", "tc_tf32x3", "tc_bf16x6"])
+def test_qaoa30_forward_full_size(env, algo):
+    """The 30-qubit QAOA workload's forward (2^30 outputs, 32768 tiles: 215
+    per CTA, the epilogue restaged through shared memory) in every split form:
+    4096 sampled outputs against the oracle's plain sum (oracle-simulated
+    tensors rounded to FP32), and the fused FP64 sum against the sum of the
+    outputs."""
+    torch, cutqc = env
+    from oracle import reconstruct as rc
+    from paper_2012_02333_gb300 import circuits as C
+    cc, Ts = oracle_case("qaoa30", lambda: C.qaoa_2cluster(15, 0))
+    T32 = [T.astype(np.float32) for T in Ts]
+    out, sp = cutqc.reconstruct_fd(cc, to_dev(torch, T32, torch.float32), algo=algo)
+    assert cutqc.last_algo() == cutqc.ALGOS[algo]
+    rng = np.random.default_rng(30)
+    xs = sorted(set(int(x) for x in rng.integers(0, 2 ** cc.n, 4096)) | {0, 2 ** cc.n - 1})
+    got = out[torch.tensor(xs, device="cuda")].double().cpu().numpy()
+    want = rc.fd_entries(cc.subs, [T.astype(np.float64) for T in T32], cc.n, cc.n_cuts, xs)
+    err = np.abs(got - want).max()
+    assert err <= TOL32, f"max abs err {err:.3e}"
+    assert float(sp.item()) == pytest.approx(torch.sum(out, dtype=torch.float64).item(), abs=1e-6)
+    del out
+    torch.cuda.empty_cache()
