@@ -159,7 +159,7 @@ struct Step {
   int vecB = 1;
   size_t off_rows = 0, off_depA = 0, off_depB = 0;   // in the plan's device block
   size_t ws_crow = 0, ws_kcount = 0;                 // in the workspace
-  size_t ws_bound = 0, ws_nseg = 0, ws_counter = 0;
+  size_t ws_bound = 0, ws_nseg = 0, ws_counter = 0, ws_look = 0;
 };
 
 struct DdSubPlan {
@@ -508,6 +508,8 @@ static void finalize_plan(Plan& P) {
     w = align_up(w + 4);
     st.ws_counter = w;
     w = align_up(w + 4);
+    st.ws_look = w;   // barrier, kept-term mask and bound products of the operand preparation
+    w = align_up(w + (st.batch == 1 && st.kmax <= 4096 ? (size_t)st.kmax * 8 : 0));
   }
   P.ws_bytes = w;
 }
@@ -890,6 +892,7 @@ static char* run_plan(DeviceState& ds, Plan& P, size_t front, size_t back,
       fstats.rmaxA = reinterpret_cast<float*>(base + P.ws_rmax[st.a]);
       fstats.rmaxB = reinterpret_cast<float*>(base + P.ws_rmax[st.b]);
       fstats.barrier = reinterpret_cast<unsigned*>(base + st.ws_counter);
+      fstats.look = reinterpret_cast<unsigned*>(base + st.ws_look);
       fused_stats = true;
     } else if (last_step && use_tc_final && both_new && st.kmax <= 4096) {
       // the last row-statistics block compacts the terms and picks the split

@@ -192,15 +192,20 @@ void launch_wait_selftest(int* status, int limit_us, cudaStream_t s);
 bool tc_supported(const Contraction& c);
 // With `fused`, the row statistics of both operands (non-zero flags and row
 // max |.| into the given arrays), the compaction and the operand preparation
-// run as one cooperative launch with a grid barrier (kmax <= 4096; `barrier`
-// is a device counter the launch zeroes first); otherwise the statistics come
-// from an earlier launch.
+// run as one cooperative launch with a grid barrier (kmax <= 4096): for BF16
+// pieces and at least 128 terms one block per term reads its two rows once
+// (`look`: 8 * kmax bytes for the barrier counter, a kept-term mask and the
+// bound products; the launch zeroes the counter and the mask first), else the
+// statistics run over rows and the preparation over tiles (`barrier`, a
+// device counter the launch zeroes first); without `fused` the statistics
+// come from an earlier launch.
 struct TcFusedStats {
   int32_t* nzA;
   int32_t* nzB;
   float* rmaxA;
   float* rmaxB;
   unsigned* barrier;
+  unsigned* look;
 };
 void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStream_t s,
                       const TcFusedStats* fused = nullptr);

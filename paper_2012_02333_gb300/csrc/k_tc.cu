@@ -4,22 +4,25 @@
 // A[e][m] B[e][n], runs on the 5th-generation tensor cores.  Each FP32
 // operand x is split into x_hi = bf16(x) and x_lo = bf16(x - x_hi), and
 //   A.B ~= A_hi.B_hi + A_hi.B_lo + A_lo.B_hi
-// (the lo.lo term is ~2^-16 relative).  The pieces are stored K-major in
-// bf16 and each pipeline stage holds every piece of one 32-wide k step, so
+// (the lo.lo term is ~2^-16 relative).  The bf16 pieces are stored MN-major
+// (one row of M or N values per kept term, the layout the tensors already
+// have) and each pipeline stage holds every piece of one 32-wide k step, so
 // one stage feeds all the products (hh, hm, mh; the x6 form splits into three
 // pieces and adds hl, lh, mm for FP32-level accuracy).  The number of
 // products is read on the device (chosen from an a-priori bound while the
 // operands are prepared) so no host round trip is needed.
 //
-// k_prep (operand preparation, both operands in one launch): finds the
-// non-zero Kronecker terms (early termination, Sec. 4.2) and the split count,
-// gathers the kept rows, transposes them to K-major through shared memory and
-// writes the splits.
+// Operand preparation finds the non-zero Kronecker terms (early termination,
+// Sec. 4.2) and the split count, and writes the split pieces of the kept
+// rows: k_pair_prep in one pass (one block per term, a look-back over the
+// other terms' flags for its compacted row), k_stats_prep in two phases
+// around a grid barrier (fewer terms than blocks, or TF32), k_prep when the
+// statistics come from an earlier launch.
 //
 // k_tc_gemm: persistent, one CTA per SM, 192 threads:
-//   warp 0     TMA producer: the split pieces of 128x32 A tiles and 256x32
-//              B tiles (64-byte swizzle) into a 4-stage (x3) or 3-stage (x6)
-//              shared-memory ring;
+//   warp 0     TMA producer: the split pieces of 32x128 A tiles and 32x256
+//              B tiles (k x M / N, 128-byte swizzle, 64-element chunks) into
+//              a 4-stage (x3) or 3-stage (x6) shared-memory ring;
 //   warp 1     allocates 512 TMEM columns (two 128x256 FP32 accumulators)
 //              and one thread issues tcgen05.mma (M=128, N=256, K=16);
 //   warps 2-5  epilogue (one per TMEM lane quarter; EPI_WARPS = 8 splits the
@@ -40,8 +43,8 @@
 // tcgen05.mma kind::tf32 (K = 8).  TF32 has FP32's exponent range, so no
 // scaling of the lo piece is needed; the dropped lo*lo term and the rounding
 // of the lo piece bound the error per product by about 3 * 2^-22 |a||b|.  A
-// stage then holds 16 k of each piece: 64-byte rows, the same shared-memory
-// geometry as the BF16 stages.
+// stage then holds 16 k of each piece, K-major (TF32 pieces are kept in the
+// K-major layout, 64-byte rows of 16 k), the same stage sizes as BF16.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -62,6 +65,8 @@ namespace {
 constexpr int BM = 128, BN = 256;
 constexpr int BK = 64;                        // operand preparation works in 64-wide k blocks
 constexpr int KS = 32;                        // one pipeline stage: 32 k = 64 bytes = one 64-byte swizzle row
+constexpr int MN_CHUNK = 64;                  // MN-major bf16 stages: 64-element (128-byte) rows of one k
+constexpr int MN_CHUNK_BYTES = MN_CHUNK * KS * 2;   // one chunk: 32 k rows of 128 bytes
 constexpr int A_PIECE = BM * KS * 2;          // 8 KiB per split piece of A
 constexpr int B_PIECE = BN * KS * 2;          // 16 KiB per split piece of B
 constexpr int MAX_STAGES = 4;
@@ -76,6 +81,12 @@ constexpr int EPI_BUF = 16 * EPI_LD * 4;
 constexpr size_t SMEM_BYTES = size_t(STAGE_AREA) + 1024 + 256 + size_t(EPI_WARPS) * EPI_BUF;
 static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 constexpr long long WAIT_CYCLES = 4000000000ll;   // ~2 s at 2 GHz
+// the one-pass preparation runs one block per Kronecker term, with both rows
+// in registers: below this many terms the two-phase launch (statistics over
+// rows, then tiles) keeps more SMs busy; rows longer than 4096 values, or
+// more terms than resident blocks, go to the two-phase launch as well (a
+// streamed one-pass form measured slower there)
+constexpr int PAIR_PREP_MIN_TERMS = 128;
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
   unsigned v;
@@ -125,9 +136,34 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// out[piece][m][k] = piece of T[row(k)][m] for the k-th kept term (0 for
-// kcount <= k < Kp): pieces h and m for the x3 form, h, m and l for x6; each
-// piece K-major with row pitch Kp.  One launch for
+// the three BF16 pieces of 4 FP32 values, each packed as 4 consecutive bf16
+// (8 bytes): h = bf16(x), m = bf16(x - h), l = bf16(x - h - m); both
+// differences are exact in FP32
+__device__ __forceinline__ void split3_bf16x4(const float4 v, uint2 (&pc)[3]) {
+  const float x[4] = {v.x, v.y, v.z, v.w};
+  __nv_bfloat16 h[4], m[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    h[j] = __float2bfloat16_rn(x[j]);
+    const float r1 = x[j] - __bfloat162float(h[j]);
+    m[j] = __float2bfloat16_rn(r1);
+    l[j] = __float2bfloat16_rn(r1 - __bfloat162float(m[j]));
+  }
+  auto pack = [](const __nv_bfloat16 (&b)[4]) {
+    uint2 u;
+    u.x = (uint32_t)__bfloat16_as_ushort(b[0]) | ((uint32_t)__bfloat16_as_ushort(b[1]) << 16);
+    u.y = (uint32_t)__bfloat16_as_ushort(b[2]) | ((uint32_t)__bfloat16_as_ushort(b[3]) << 16);
+    return u;
+  };
+  pc[0] = pack(h);
+  pc[1] = pack(m);
+  pc[2] = pack(l);
+}
+
+// The pieces of T[row(k)][m] for the k-th kept term (0 for kcount <= k <
+// Kp): h and m for the x3 form, h, m and l for x6.  BF16 pieces are
+// MN-major, out[piece][k][m] with row pitch cols; TF32 pieces K-major,
+// out[piece][m][k] with row pitch Kp.  One launch for
 // both operands: blocks [0, blocks0) prepare A, the rest B.  When `fused`,
 // every block finds its own compacted rows (a block-wide stable scan of the
 // row pairs: early termination, Sec. 4.2) and the split count from the bound
@@ -222,22 +258,22 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
   const int kc = kc_s, nseg = nseg_s;
   // the contraction reads k < 32 * ceil(kc / 32): tiles past that write nothing
   if (k0 >= (kc + 31) / 32 * 32) return;
-  {
-    // all 16 loads first (read-only path), then the shared-memory stores: a
-    // load interleaved with stores through a generic pointer would wait for
-    // each of them in turn
-    float ld[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int kk = i * 4 + tid / 64, mm = tid % 64, k = k0 + kk;
-      ld[i] = (k < kc) ? __ldg(T + (int64_t)rowsel[kk] * cols + m0 + mm) : 0.0f;
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) s[i * 4 + tid / 64][tid % 64] = ld[i];
-  }
-  __syncthreads();
-  const int ml = tid / 4, kq = (tid % 4) * 16;
   if constexpr (TF32) {
+    {
+      // all 16 loads first (read-only path), then the shared-memory stores: a
+      // load interleaved with stores through a generic pointer would wait for
+      // each of them in turn
+      float ld[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        const int kk = i * 4 + tid / 64, mm = tid % 64, k = k0 + kk;
+        ld[i] = (k < kc) ? __ldg(T + (int64_t)rowsel[kk] * cols + m0 + mm) : 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < 16; ++i) s[i * 4 + tid / 64][tid % 64] = ld[i];
+    }
+    __syncthreads();
+    const int ml = tid / 4, kq = (tid % 4) * 16;
     __align__(16) float part[2][16];
 #pragma unroll
     for (int j = 0; j < 16; ++j) {
@@ -254,30 +290,28 @@ __device__ __forceinline__ void prep_tile(const PrepArgs& a, const int bx, const
 #pragma unroll
       for (int q = 0; q < 4; ++q) dst[q] = src[q];
     }
-    return;
-  }
-  __align__(16) __nv_bfloat16 part[3][16];
+  } else {
+    // BF16 pieces, MN-major (out[piece][k][m], rows of `cols`): no transpose;
+    // thread (kr, mq) takes 4 consecutive m of k rows kr, kr + 16, ...
+    const int mq = (tid & 15) * 4, kr = tid >> 4;
+    float4 ld[4];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    const float v = s[kq + j][ml];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(mid);
-    part[0][j] = h;
-    part[1][j] = mid;
-    part[2][j] = __float2bfloat16_rn(r2);
-  }
-  __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.out[which]);
-  const int npieces = nseg == 3 ? 2 : 3;
-  // unrolled over the three possible pieces so `part` stays in registers
+    for (int p = 0; p < 4; ++p) {
+      const int kk = p * 16 + kr;
+      ld[p] = (k0 + kk < kc) ? __ldg(reinterpret_cast<const float4*>(T + (int64_t)rowsel[kk] * cols + m0 + mq))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __nv_bfloat16* out = static_cast<__nv_bfloat16*>(a.out[which]);
+    const int npieces = nseg == 3 ? 2 : 3;
 #pragma unroll
-  for (int pc = 0; pc < 3; ++pc) {
-    if (pc < npieces) {
-      const uint4* src = reinterpret_cast<const uint4*>(part[pc]);
-      uint4* dst = reinterpret_cast<uint4*>(out + ((int64_t)pc * cols + m0 + ml) * a.Kp + k0 + kq);
-      dst[0] = src[0];
-      dst[1] = src[1];
+    for (int p = 0; p < 4; ++p) {
+      uint2 pc4[3];
+      split3_bf16x4(ld[p], pc4);
+      const int64_t row = k0 + p * 16 + kr;
+#pragma unroll
+      for (int pc = 0; pc < 3; ++pc)
+        if (pc < npieces)
+          *reinterpret_cast<uint2*>(out + ((int64_t)pc * a.Kp + row) * cols + m0 + mq) = pc4[pc];
     }
   }
 }
@@ -390,6 +424,224 @@ __global__ void __launch_bounds__(256) k_stats_prep(const PrepArgs a, const Stat
     prep_tile<TF32>(a, t % sa.tilesX, t / sa.tilesX, true, pre_r0, pre_r1);
 }
 
+// ---- operand preparation reading each row once (BF16 pieces, MN-major) ---
+// One block per Kronecker term t (a cooperative launch, so every block is
+// resident; rows of at most 4096 values): phase 1 reads row rows[t] of A and
+// row rows[kmax + t] of B into registers, finds whether both are non-zero
+// (early termination, Sec. 4.2) and their max |.|, sets bit t of a kept-term
+// mask and the product max|A| max|B| of a kept term, and splits the rows
+// into their pieces while one bounded grid barrier completes (one counter,
+// polled by one thread per block).  Phase 2: every block reads the mask and
+// the products (a few hundred bytes, one round trip), so it knows the kept
+// count before its term, the total, and the bound S = scale * sum_kept
+// max|A| max|B| (summed in the same fixed order in every block, so all agree
+// on the split count), and stores the pieces of a kept term to row
+// `kept before t` of every piece matrix, or zero rows at
+// kmax - 1 - (terms dropped before t) for a dropped term, written only where
+// the contraction's last stage reads (rows below the kept count rounded up
+// to a stage, zero rows past kmax included).
+struct PairArgs {
+  const float* T[2];
+  int64_t cols[2];            // at most 4096 each
+  int kmax, Kp;
+  const int32_t* rows;        // [2][kmax] row pairs
+  int32_t* nz[2];             // row flags and maxima (the row statistics of the plan)
+  float* rmax[2];
+  unsigned* barrier;          // zero before the launch
+  unsigned* bits;             // [ceil(kmax / 32)], zero before the launch
+  float* prod;                // [kmax]
+  double scale, split_tol;
+  int nseg_fixed;
+  int32_t* kcount;
+  int32_t* nseg;
+  double* bound;
+  double* sum_zero;
+  int* status;
+  __nv_bfloat16* out[2];      // [piece][Kp][cols]
+};
+
+__global__ void __launch_bounds__(256) k_pair_prep(const PairArgs a) {
+  CUTQC_PDL_LAUNCH();   // the contraction may launch and set itself up
+  __shared__ float red_m[2][8];
+  __shared__ int red_z[2][8];
+  __shared__ float red_s[8];
+  __shared__ unsigned wsm[128];   // the kept-term mask (kmax <= 4096)
+  __shared__ int pre_s[128];      // kept terms before each mask word
+  __shared__ int pass, nseg_s, kend_s;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int t = blockIdx.x;
+  if ((int)gridDim.x != a.kmax) {   // one term per block, or the barrier count is wrong
+    if (t == 0 && tid == 0) atomicExch(a.status, (int)DEV_BAD_INDEX);
+    return;
+  }
+  const int r0 = __ldg(a.rows + t), r1 = __ldg(a.rows + a.kmax + t);
+  // thread j holds 8 consecutive values (2 float4) at j and j + 256 of each
+  // row, and later their pieces, 16 bytes each
+  const float4* row[2] = {reinterpret_cast<const float4*>(a.T[0] + (int64_t)r0 * a.cols[0]),
+                          reinterpret_cast<const float4*>(a.T[1] + (int64_t)r1 * a.cols[1])};
+  const int nv[2] = {(int)(a.cols[0] / 4), (int)(a.cols[1] / 4)};
+  float4 v[2][2][2];
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = tid + 256 * u;
+      const bool in = 2 * j < nv[w];
+      v[w][u][0] = in ? __ldg(row[w] + 2 * j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      v[w][u][1] = in ? __ldg(row[w] + 2 * j + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  float mx[2] = {0.0f, 0.0f};
+  int nz[2] = {0, 0};
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float4 x = v[w][u][h];
+        nz[w] |= (x.x != 0.f) | (x.y != 0.f) | (x.z != 0.f) | (x.w != 0.f);
+        mx[w] = fmaxf(mx[w], fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+      }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      mx[w] = fmaxf(mx[w], __shfl_xor_sync(0xffffffffu, mx[w], o));
+      nz[w] |= __shfl_xor_sync(0xffffffffu, nz[w], o);
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      red_m[w][warp] = mx[w];
+      red_z[w][warp] = nz[w];
+    }
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll
+    for (int w = 0; w < 2; ++w)
+#pragma unroll
+      for (int j = 1; j < 8; ++j) {
+        mx[w] = fmaxf(mx[w], red_m[w][j]);
+        nz[w] |= red_z[w][j];
+      }
+    const int keep = nz[0] && nz[1];
+    a.prod[t] = keep ? mx[0] * mx[1] : 0.0f;
+    if (keep) atomicOr(a.bits + (t >> 5), 1u << (t & 31));
+    // arrive (release: the product and the mask bit are visible to whoever
+    // sees the count), then split while the barrier completes
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(a.barrier) : "memory");
+  }
+  uint4 pcs[2][2][3];
+#pragma unroll
+  for (int w = 0; w < 2; ++w)
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      uint2 lo[3], hi[3];
+      split3_bf16x4(v[w][u][0], lo);
+      split3_bf16x4(v[w][u][1], hi);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) pcs[w][u][p] = make_uint4(lo[p].x, lo[p].y, hi[p].x, hi[p].y);
+    }
+  // grid barrier, bounded: a timeout sets the status word and ends the block
+  if (tid == 0) {
+    const uint64_t t0 = gtimer();
+    int ok = 1;
+    while (ld_acquire(a.barrier) < gridDim.x) {
+      if (gtimer() - t0 > 2000000000ull) {   // 2 s
+        ok = 0;
+        atomicExch(a.status, (int)DEV_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+    }
+    pass = ok;
+    a.nz[0][r0] = nz[0];   // the row statistics for later launches, off the path to the barrier
+    a.rmax[0][r0] = mx[0];
+    a.nz[1][r1] = nz[1];
+    a.rmax[1][r1] = mx[1];
+  }
+  __syncthreads();
+  if (!pass) return;
+  // the mask and the products, through L2 (written by other blocks)
+  const int nw = (a.kmax + 31) >> 5;
+  float sacc = 0.0f;
+  for (int j = tid; j < a.kmax; j += 256) sacc += __ldcg(a.prod + j);
+  if (tid < nw) wsm[tid] = __ldcg(a.bits + tid);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+  if (lane == 0) red_s[warp] = sacc;
+  __syncthreads();
+  if (warp == 0) {
+    // exclusive scan of the word counts, 4 words per lane
+    int c[4], tot = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = lane * 4 + u;
+      c[u] = i < nw ? __popc(wsm[i]) : 0;
+      tot += c[u];
+    }
+    int incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    int run = incl - tot;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = lane * 4 + u;
+      if (i < nw) pre_s[i] = run;
+      run += c[u];
+    }
+    const int kc = __shfl_sync(0xffffffffu, incl, 31);
+    if (lane == 0) {
+      float Sf = 0.0f;
+      for (int j = 0; j < 8; ++j) Sf += red_s[j];
+      // FP32 accumulation error is far below 1e-4 relative: inflate so S stays an upper bound
+      const double S = (double)Sf * a.scale * (1.0 + 1e-4);
+      // BF16 x3 drops terms of at most ~3 * 2^-18 |a||b| per product
+      const int ns = a.nseg_fixed ? a.nseg_fixed : (3.0 * 3.814697265625e-06 * S <= a.split_tol ? 3 : 6);
+      nseg_s = ns;
+      kend_s = (kc + KS - 1) / KS * KS;
+      if (t == 0) {
+        *a.kcount = kc;
+        *a.nseg = ns;
+        *a.bound = S;
+        if (a.sum_zero) *a.sum_zero = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+  const int npieces = nseg_s == 3 ? 2 : 3;
+  const int kend = kend_s;   // the contraction reads rows 0 .. kend - 1
+  const unsigned wbits = wsm[t >> 5];
+  const int keep = (wbits >> (t & 31)) & 1;
+  const int prefix = pre_s[t >> 5] + __popc(wbits & ((1u << (t & 31)) - 1u));
+  const int64_t slot = keep ? prefix : a.kmax - 1 - (t - prefix);
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    __nv_bfloat16* o = a.out[w];
+    const int64_t cols = a.cols[w];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int j = tid + 256 * u;
+      if (2 * j < nv[w]) {
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          if (p < npieces) {
+            if (slot < kend)   // a kept row, or a zero row the last stage reads
+              *reinterpret_cast<uint4*>(o + ((int64_t)p * a.Kp + slot) * cols + 8 * j) =
+                  keep ? pcs[w][u][p] : make_uint4(0u, 0u, 0u, 0u);
+            // zero rows past kmax that the last stage reads
+            for (int64_t rr = (int64_t)a.kmax + t; rr < kend; rr += a.kmax)
+              *reinterpret_cast<uint4*>(o + ((int64_t)p * a.Kp + rr) * cols + 8 * j) = make_uint4(0u, 0u, 0u, 0u);
+          }
+        }
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -436,6 +688,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+// shared-memory matrix descriptor: MN-major, 128-byte swizzle.  The operand
+// tile is 64-element (128-byte) chunks along M (or N), each chunk 32 k rows
+// of 128 bytes (4096 bytes); the leading byte offset is the distance between
+// chunks along M / N, the stride byte offset between groups of 8 k rows
+__device__ __forceinline__ uint64_t mn128_desc(const void* p) {
+  const uint32_t a = smem_u32(p);
+  uint64_t d = (uint64_t)((a & 0x3FFFF) >> 4);
+  d |= (uint64_t)(MN_CHUNK_BYTES >> 4) << 16;   // leading byte offset: next 64-element chunk along M / N
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset: next 8 k rows
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  d |= (uint64_t)2 << 61;                       // SWIZZLE_128B
+  return d;
+}
 // shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 32 bf16),
 // 8-row groups 512 bytes apart
 __device__ __forceinline__ uint64_t sw64_desc(const void* p) {
@@ -447,9 +718,11 @@ __device__ __forceinline__ uint64_t sw64_desc(const void* p) {
   d |= (uint64_t)4 << 61;                  // SWIZZLE_64B
   return d;
 }
-// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both K-major
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+// instruction descriptor: kind::f16, BF16 x BF16 -> FP32, both MN-major
+// (bits 15 and 16: A and B transposed)
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(m >> 4) << 24);
 }
 // instruction descriptor: kind::tf32, TF32 x TF32 -> FP32, both K-major
 __host__ __device__ constexpr uint32_t idesc_tf32(int m, int n) {
@@ -670,9 +943,16 @@ __global__ void __launch_bounds__(THREADS, 1)
           uint8_t* st = smem + stage * stage_bytes;
           mbar_expect_tx(&full[stage], item_bytes);
           for (int pc = 0; pc < npieces; ++pc) {
-            tma_load_2d(st + pc * A_PIECE, &tmA, kb * KSS, pc * a.M + it.tm * BM, &full[stage]);
-            tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, mapB, kb * KSS, pc * a.N + it.tn * BN + it.n0,
-                        &full[stage]);
+            if constexpr (TF32) {
+              tma_load_2d(st + pc * A_PIECE, &tmA, kb * KSS, pc * a.M + it.tm * BM, &full[stage]);
+              tma_load_2d(st + npieces * A_PIECE + pc * B_PIECE, mapB, kb * KSS, pc * a.N + it.tn * BN + it.n0,
+                          &full[stage]);
+            } else {
+              // k rows pc * Kp + kb * 32 .. + 31, 64-element chunks of M / N
+              tma_load_3d(st + pc * A_PIECE, &tmA, 0, pc * a.Kp + kb * KSS, it.tm * (BM / MN_CHUNK), &full[stage]);
+              tma_load_3d(st + npieces * A_PIECE + pc * B_PIECE, mapB, 0, pc * a.Kp + kb * KSS,
+                          (it.tn * BN + it.n0) / MN_CHUNK, &full[stage]);
+            }
           }
         }
         __syncwarp();
@@ -692,7 +972,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     bool ok = true;
     TcItem it;
     for (int i = 0; ok && tc_item(a, i, it); ++i) {
-      const uint32_t idesc = TF32 ? idesc_tf32(BM, it.w) : idesc_bf16(BM, it.w);
+      const uint32_t idesc = TF32 ? idesc_tf32(BM, it.w) : idesc_bf16_mn(BM, it.w);
       ok = __all_sync(0xffffffffu, mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag));
       if (!ok) break;
       tc_fence_after();
@@ -704,15 +984,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) {
           uint8_t* st = smem + stage * stage_bytes;
           for (int sg = 0; sg < nseg; ++sg) {
-            const uint64_t ad = sw64_desc(st + kPartA[sg] * A_PIECE);
-            const uint64_t bd = sw64_desc(st + npieces * A_PIECE + kPartB[sg] * B_PIECE);
-            // two MMAs per product and stage (K = 16 bf16 or 8 TF32: 32 bytes each)
+            // two MMAs per product and stage: K = 8 TF32 (K-major, 32 bytes
+            // further along the row) or K = 16 bf16 (MN-major, 16 rows of 128
+            // bytes further)
+            if constexpr (TF32) {
+              const uint64_t ad = sw64_desc(st + kPartA[sg] * A_PIECE);
+              const uint64_t bd = sw64_desc(st + npieces * A_PIECE + kPartB[sg] * B_PIECE);
 #pragma unroll
-            for (int k = 0; k < 2; ++k) {
-              if constexpr (TF32)
-                mma_tf32(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
-              else
-                mma_bf16(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+              for (int k = 0; k < 2; ++k) mma_tf32(d_tmem, ad + 2 * k, bd + 2 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
+            } else {
+              const uint64_t ad = mn128_desc(st + kPartA[sg] * A_PIECE);
+              const uint64_t bd = mn128_desc(st + npieces * A_PIECE + kPartB[sg] * B_PIECE);
+#pragma unroll
+              for (int k = 0; k < 2; ++k)
+                mma_bf16(d_tmem, ad + 128 * k, bd + 128 * k, idesc, (kb | sg | k) != 0 ? 1u : 0u);
             }
           }
           mma_commit(&empty[stage]);
@@ -1001,6 +1286,22 @@ CUtensorMap make_map(const void* base, uint64_t rows, uint64_t inner, uint32_t b
   return m;
 }
 
+// BF16 pieces, MN-major: [rows = pieces * Kp][cols] viewed as (64 elements
+// of a chunk, k row, chunk of 64 along cols), box 64 x 32 k rows x `chunks`:
+// in shared memory the chunks lie 4096 bytes apart, 128-byte rows within each
+CUtensorMap make_map_mn(const void* base, uint64_t rows, uint64_t cols, uint32_t chunks) {
+  CUtensorMap m;
+  const cuuint64_t dims[3] = {MN_CHUNK, rows, cols / MN_CHUNK};
+  const cuuint64_t strides[2] = {cols * 2, MN_CHUNK * 2};
+  const cuuint32_t box[3] = {MN_CHUNK, (cuuint32_t)KS, chunks};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(CUTQC_ERR_CUDA, "cuTensorMapEncodeTiled failed (MN-major operand map)");
+  return m;
+}
+
 int kpad(const Contraction& c) { return (c.kmax + BK - 1) / BK * BK; }
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
@@ -1060,7 +1361,59 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
   pa.sum_zero = c.sum;
   pa.out[0] = Ab;
   pa.out[1] = Bb;
-  if (fused) {
+  static int pair_blocks = -1;   // resident blocks of the one-pass preparation on the device
+  if (pair_blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    CUTQC_CUDA(cudaGetDevice(&dev));
+    CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_prep, 256, 0));
+    pair_blocks = per_sm * sms;
+  }
+  if (fused && !tf32 && c.kmax >= PAIR_PREP_MIN_TERMS && c.kmax <= pair_blocks && M <= 4096 && N <= 4096) {
+    if (c.kmax > 4096) fail(CUTQC_ERR_UNSUPPORTED, "fused row statistics need kmax <= 4096");
+    if (!fused->look) fail(CUTQC_ERR_ARG, "the preparation needs its barrier and mask words");
+    PairArgs pr{};
+    pr.T[0] = pa.T[0];
+    pr.T[1] = pa.T[1];
+    pr.cols[0] = M;
+    pr.cols[1] = N;
+    pr.kmax = c.kmax;
+    pr.Kp = Kp;
+    pr.rows = c.rows;
+    pr.nz[0] = fused->nzA;
+    pr.nz[1] = fused->nzB;
+    pr.rmax[0] = fused->rmaxA;
+    pr.rmax[1] = fused->rmaxB;
+    const int nw = (c.kmax + 31) / 32;
+    pr.barrier = fused->look;
+    pr.bits = fused->look + 1;
+    pr.prod = reinterpret_cast<float*>(fused->look + 1 + nw);
+    pr.scale = c.scale;
+    pr.split_tol = c.split_tol;
+    pr.nseg_fixed = pa.nseg_fixed;
+    pr.kcount = c.kcount;
+    pr.nseg = c.nseg;
+    pr.bound = c.bound;
+    pr.sum_zero = c.sum;
+    pr.status = status;
+    pr.out[0] = static_cast<__nv_bfloat16*>(Ab);
+    pr.out[1] = static_cast<__nv_bfloat16*>(Bb);
+    const unsigned grid = (unsigned)c.kmax;   // one block per term
+    CUTQC_CUDA(cudaMemsetAsync(fused->look, 0, sizeof(unsigned) * (size_t)(1 + nw), s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;   // every block resident: the grid barrier cannot starve
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CUTQC_CUDA(cudaLaunchKernelEx(&cfg, k_pair_prep, pr));
+    count_launch();
+    check_launch("k_pair_prep");
+  } else if (fused) {
     if (c.kmax > 4096) fail(CUTQC_ERR_UNSUPPORTED, "fused row statistics need kmax <= 4096");
     pa.fused = 1;
     pa.nzA = fused->nzA;
@@ -1122,12 +1475,14 @@ void launch_tc_bf16x3(const Contraction& c, void* ws, size_t ws_bytes, cudaStrea
     check_launch("k_prep");
   }
 
-  // the pieces of each operand stacked along rows: [piece * rows + row][k]
-  // (three bf16 pieces, or two TF32 pieces)
-  const uint64_t np = tf32 ? 2 : 3;
-  const CUtensorMap tmA = make_map(Ab, (uint64_t)M * np, (uint64_t)Kp, BM, tf32);
-  const CUtensorMap tmB = make_map(Bb, (uint64_t)N * np, (uint64_t)Kp, BN, tf32);
-  const CUtensorMap tmBh = make_map(Bb, (uint64_t)N * np, (uint64_t)Kp, BN / 2, tf32);
+  // TF32: the pieces of each operand stacked along rows, [piece * rows +
+  // row][k]; BF16: [piece * Kp + k][row] (MN-major)
+  const CUtensorMap tmA = tf32 ? make_map(Ab, (uint64_t)M * 2, (uint64_t)Kp, BM, true)
+                               : make_map_mn(Ab, (uint64_t)Kp * 3, (uint64_t)M, BM / MN_CHUNK);
+  const CUtensorMap tmB = tf32 ? make_map(Bb, (uint64_t)N * 2, (uint64_t)Kp, BN, true)
+                               : make_map_mn(Bb, (uint64_t)Kp * 3, (uint64_t)N, BN / MN_CHUNK);
+  const CUtensorMap tmBh = tf32 ? make_map(Bb, (uint64_t)N * 2, (uint64_t)Kp, BN / 2, true)
+                                : make_map_mn(Bb, (uint64_t)Kp * 3, (uint64_t)N, BN / 2 / MN_CHUNK);
   TcArgs a;
   a.Kp = Kp;
   a.M = (int)M;
