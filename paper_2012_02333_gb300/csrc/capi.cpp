@@ -175,6 +175,7 @@ struct DdSubPlan {
   size_t ws_part = 0;                  // partial sums of split runs (contiguous-run merge)
   bool run = false;                    // merged qubits are the lowest output bits
   bool dense = false;                  // ... and the active qubits the bits directly above them
+  uint64_t blk = 0;                    // active bits below the highest merged one (block form of the merge)
 };
 
 struct Plan {
@@ -677,6 +678,7 @@ static void build_dd_plan(Plan& P, const cutqc_problem* p, const int8_t* role) {
       uint64_t am = 0;
       for (uint64_t v : act_val) am |= v;
       d.dense = d.run && am == (((uint64_t(1) << d.a) - 1) << d.mg);
+      d.blk = d.run ? 0 : dd_merge_block(mm, d.mg, am, d.zoom);
     }
     d.ws_merged = front;
     front = align_up(front + (size_t)d.rows * ((size_t)1 << d.a) * es);
@@ -1221,7 +1223,7 @@ static std::function<std::vector<const void*>(char*)> dd_merge_pre(const Plan& P
       launch_dd_merge(p->sub[c].tensor, P.dtype, d.rows, d.f, d.a, d.mg,
                       reinterpret_cast<const uint64_t*>(ddtab + d.off_act),
                       reinterpret_cast<const uint64_t*>(ddtab + d.off_mrg), d.zoom, d.run, d.dense,
-                      front + d.ws_merged, reinterpret_cast<float*>(front + d.ws_mc), front + d.ws_part, s);
+                      front + d.ws_merged, reinterpret_cast<float*>(front + d.ws_mc), front + d.ws_part, s, d.blk);
       t[c] = front + d.ws_merged;
     }
     return t;
@@ -1403,7 +1405,7 @@ int cutqc_attribute_merged(const void* variant_probs, int32_t d, int32_t k_in, c
                           reinterpret_cast<uint64_t*>(w + o_mrg), s);
     launch_dd_merge(variant_probs, dtype, rows, d, a, mg, reinterpret_cast<const uint64_t*>(w + o_act),
                     reinterpret_cast<const uint64_t*>(w + o_mrg), zoom, run, dense, w + o_q,
-                    reinterpret_cast<float*>(w + o_mc), w + o_part, s);
+                    reinterpret_cast<float*>(w + o_mc), w + o_part, s, run ? 0 : dd_merge_block(mm, mg, am, zoom));
     // the merged distributions' local qubits are `kept`, in order
     std::vector<int> pos(d, -1);
     for (int i = 0; i < a; ++i) pos[kept[i]] = i;

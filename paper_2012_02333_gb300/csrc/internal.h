@@ -240,9 +240,14 @@ int dd_merge_chunks(int64_t rows, int a, int mg);
 // index bit i, least significant first), built on the device: no host copy
 void launch_deposit_tables(const uint64_t* act, int na, const uint64_t* mrg, int nm, uint64_t* tab_act,
                            uint64_t* tab_mrg, cudaStream_t s);
+// blk: the active index bits below the highest merged bit, when every bit
+// below it is merged or active, none is zoomed and at most two are active
+// (dd_merge_block; 0 = not that layout): the block form then sums each
+// contiguous block of 2^(mg + popcount(blk)) values into its outputs
 void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
                      const uint64_t* depMrg, uint64_t zoom, bool run, bool dense_bits, void* M, float* MC,
-                     void* part, cudaStream_t s);
+                     void* part, cudaStream_t s, uint64_t blk = 0);
+uint64_t dd_merge_block(uint64_t merged_mask, int mg, uint64_t active_mask, uint64_t zoom);
 size_t topk_workspace_bytes(int64_t n);
 void launch_topk(const void* bins, int dtype, int64_t n, void* ws, float* out_v, int64_t* out_i, cudaStream_t s);
 // merge nlists lists of 32 (value, index) candidates, laid out like launch_topk's workspace

@@ -31,6 +31,9 @@
 // (they are rounding residue of terms that vanish exactly).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -274,26 +277,47 @@ __global__ void k_attr_variants(const T* __restrict__ P, const AttrArgs a, T* __
   for (int k = 0; k < 4; ++k) dlow[k] = tab_x[0][k];
 #pragma unroll
   for (int m = 0; m < NM; ++m) dm[m] = tab_m[0][m];
-  for (int64_t og = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; og < n_grp;
-       og += (int64_t)gridDim.x * blockDim.x) {
+  // the first outcome of group g (4 consecutive x of one variant row)
+  auto group_base = [&](int64_t g) {
+    const uint32_t gx = (uint32_t)(g & ((int64_t(1) << lg_xg) - 1)) << 2;
+    const uint64_t yx =
+        tab_x[0][gx & 255] | tab_x[1][(gx >> 8) & 255] | tab_x[2][(gx >> 16) & 255] | tab_x[3][gx >> 24];
+    return P + ((int64_t)(g >> lg_xg) << a.d) + yx;
+  };
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t og = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  // CONTIG: the next group's 2^KOUT 16-byte loads are in flight while the
+  // current one is processed (the grid is one wave of resident blocks, so a
+  // thread takes several groups)
+  float4 nxt[CONTIG ? NM : 1];
+  if constexpr (CONTIG) {
+    if (og < n_grp) {
+      const float4* b4 = reinterpret_cast<const float4*>(group_base(og));
+#pragma unroll
+      for (int j = 0; j < NM; ++j) nxt[j] = __ldg(b4 + j);
+    }
+  }
+  for (; og < n_grp; og += stride) {
     const uint32_t x = (uint32_t)(og & ((int64_t(1) << lg_xg) - 1)) << 2;
     const uint32_t rest = (uint32_t)(og >> lg_xg);          // s * 3^KOUT + mb
     const uint32_t sv = rest / (uint32_t)a.pow3_kout, mb = rest - sv * (uint32_t)a.pow3_kout;
-    const uint64_t yx = tab_x[0][x & 255] | tab_x[1][(x >> 8) & 255] | tab_x[2][(x >> 16) & 255] | tab_x[3][x >> 24];
-    const T* base = P + ((int64_t)rest << a.d) + yx;
     T v[NM][4];
     if constexpr (CONTIG) {
       // entry e of the 4 * NM contiguous values is measured offset e % NM
       // (dm[m] for outcome m) of output x + e / NM
       T w[4 * NM];
-      const float4* b4 = reinterpret_cast<const float4*>(base);
 #pragma unroll
       for (int j = 0; j < NM; ++j) {
-        const float4 q = __ldg(b4 + j);
+        const float4 q = nxt[j];
         w[4 * j] = q.x;
         w[4 * j + 1] = q.y;
         w[4 * j + 2] = q.z;
         w[4 * j + 3] = q.w;
+      }
+      if (og + stride < n_grp) {
+        const float4* b4 = reinterpret_cast<const float4*>(group_base(og + stride));
+#pragma unroll
+        for (int j = 0; j < NM; ++j) nxt[j] = __ldg(b4 + j);
       }
 #pragma unroll
       for (int m = 0; m < NM; ++m) {
@@ -307,6 +331,7 @@ __global__ void k_attr_variants(const T* __restrict__ P, const AttrArgs a, T* __
         }
       }
     } else {
+      const T* base = group_base(og);
 #pragma unroll
       for (int m = 0; m < NM; ++m)
 #pragma unroll
@@ -398,6 +423,28 @@ __global__ void k_attr_inits(T* __restrict__ TQ, int64_t inner) {
   }
 }
 
+// blocks of 256 threads for n threads of work, at most one wave of resident
+// blocks of `fn` on the device
+unsigned resident_grid(const void* fn, int64_t n) {
+  static std::mutex mu;
+  static std::map<const void*, int> cap;
+  int c;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cap.find(fn);
+    if (it == cap.end()) {
+      int dev = 0, sms = 0, per = 0;
+      CUTQC_CUDA(cudaGetDevice(&dev));
+      CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      CUTQC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0));
+      it = cap.emplace(fn, std::max(per, 1) * sms).first;
+    }
+    c = it->second;
+  }
+  const int64_t g = (n + 255) / 256;
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>(g, c));
+}
+
 template <typename T>
 void launch_two_pass(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
   const int64_t n_out = (int64_t(1) << (2 * (a.k_in + a.k_out))) << a.n_eff;
@@ -416,10 +463,15 @@ void launch_two_pass(const T* P, const AttrArgs& a, T* out, cudaStream_t s) {
     for (int j = 0; j < a.k_out; ++j) contig = contig && a.meas_pos[j] < a.k_out;
     if constexpr (sizeof(T) == 4) {
       if (contig) {
+        // one wave of resident blocks (the loads are pipelined across a
+        // thread's groups, and each block fills its tables once)
+        auto go = [&](auto kern) {
+          kern<<<resident_grid(reinterpret_cast<const void*>(kern), n_grp), 256, 0, s>>>(P, a, out, n_grp, snap);
+        };
         switch (a.k_out) {
-          case 0: k_attr_variants<T, 0, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-          case 1: k_attr_variants<T, 1, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
-          default: k_attr_variants<T, 2, true><<<grid(n_grp), 256, 0, s>>>(P, a, out, n_grp, snap); break;
+          case 0: go(k_attr_variants<T, 0, true>); break;
+          case 1: go(k_attr_variants<T, 1, true>); break;
+          default: go(k_attr_variants<T, 2, true>); break;
         }
       }
     }

@@ -237,6 +237,85 @@ __global__ void k_dd_merge_run(const float* __restrict__ Tin, int64_t cols, int 
   }
 }
 
+// Merged qubits below index bit T with R = 1 or 2 kept bits among them (T =
+// mg + R; e.g. a subcircuit's measured cut qubits between merged outputs, or
+// just below them): the 2^R outputs that differ only in those kept bits sum
+// the values of one contiguous block of 2^T values, output l taking the
+// values whose kept bits below T read l.  A group of G = min(32, 2^(T - 2))
+// lanes owns such a unit and reads its block with 16-byte loads (lane j takes
+// float4 j, j + G, ..., 8 in flight).  Within a float4 the kept bits among
+// index bits 0-1 (`lo`) pair its components into one, two or four partial
+// sums; the kept bits at or above bit 2 are bits `hb0`, `hb1` of the float4's
+// index (-1: none) and pick the output; every output keeps its own
+// compensated sum (TwoSum), adding zero where a partial sum is another
+// output's (exact), as in the contiguous-run form.
+template <int R>
+__global__ void k_dd_merge_blk(const float* __restrict__ Tin, int64_t cols, int a, int T, int lo, int hb0, int hb1,
+                               const uint64_t* __restrict__ depAct, int nbA, uint64_t zoom, float* __restrict__ out,
+                               float* __restrict__ outc, int64_t n_units) {
+  constexpr int NO = 1 << R;
+  const int64_t F = int64_t(1) << (T - 2);      // float4 per block
+  const int G = F < 32 ? (int)F : 32;
+  const int64_t per = F / G;                    // float4 per lane
+  const int lane = threadIdx.x & 31, gl = lane & (G - 1), gi = lane / G, upw = 32 / G;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint64_t amask = (uint64_t(1) << a) - 1;
+  const int nlo = __popc(lo);                   // kept bits among index bits 0-1
+  // every lane of a warp runs the same number of steps (shuffles below)
+  for (int64_t ub = warp * upw; ub < n_units; ub += nwarps * upw) {
+    const int64_t u = ub + gi;
+    const bool ok = u < n_units;
+    const int64_t o0 = (ok ? u : 0) << R;       // the unit's first output (its R lowest kept bits zero)
+    const uint64_t xa = (uint64_t)o0 & amask;
+    const float4* p =
+        reinterpret_cast<const float4*>(Tin + (o0 >> a) * cols + (dep_tab(depAct, nbA, xa) | zoom)) + gl;
+    FF acc[NO];
+#pragma unroll
+    for (int l = 0; l < NO; ++l) acc[l] = FF{0.0f, 0.0f};
+    if (ok) {
+      for (int64_t j0 = 0; j0 < per; j0 += 8) {
+        float4 q[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) q[e] = j0 + e < per ? __ldcs(p + (j0 + e) * G) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t f = gl + (j0 + e) * G;  // the float4's index in the block
+          const int lh = (hb0 >= 0 ? (int)((f >> hb0) & 1) : 0) | (hb1 >= 0 ? (int)((f >> hb1) & 1) << 1 : 0);
+          FF ps[4];
+          if (lo == 0) {
+            ps[0] = sum4(q[e]);
+          } else if (lo == 1) {        // index bit 0 kept: (x, z) and (y, w)
+            ps[0] = ff_add(FF{q[e].x, 0.0f}, FF{q[e].z, 0.0f});
+            ps[1] = ff_add(FF{q[e].y, 0.0f}, FF{q[e].w, 0.0f});
+          } else if (lo == 2) {        // index bit 1 kept: (x, y) and (z, w)
+            ps[0] = ff_add(FF{q[e].x, 0.0f}, FF{q[e].y, 0.0f});
+            ps[1] = ff_add(FF{q[e].z, 0.0f}, FF{q[e].w, 0.0f});
+          } else {                     // both kept: one output per component
+            ps[0] = FF{q[e].x, 0.0f};
+            ps[1] = FF{q[e].y, 0.0f};
+            ps[2] = FF{q[e].z, 0.0f};
+            ps[3] = FF{q[e].w, 0.0f};
+          }
+#pragma unroll
+          for (int k = 0; k < NO; ++k) {
+            // output k takes partial sum k mod 2^nlo when its higher kept bits read lh
+            const int i = k & ((1 << nlo) - 1);
+            const FF v = ps[i < (1 << nlo) ? i : 0];
+            acc[k] = ff_add(acc[k], (k >> nlo) == lh ? v : FF{0.0f, 0.0f});
+          }
+        }
+      }
+    }
+    for (int off = 1; off < G; off <<= 1)
+#pragma unroll
+      for (int l = 0; l < NO; ++l) acc[l] = ff_add(acc[l], ff_shfl_xor(acc[l], off));
+    if (ok && gl == 0)
+#pragma unroll
+      for (int l = 0; l < NO; ++l) store_merged(out, outc, o0 + l, acc[l]);
+  }
+}
+
 // warp per output: lanes take chunks lane, lane + 32, ... of its partial sums
 __global__ void k_dd_merge_finish(const float2* __restrict__ part, int lnch, float* __restrict__ out,
                                   float* __restrict__ outc, int64_t n_out) {
@@ -532,6 +611,18 @@ void launch_deposit_tables(const uint64_t* act, int na, const uint64_t* mrg, int
   check_launch("k_deposit_tables");
 }
 
+uint64_t dd_merge_block(uint64_t merged_mask, int mg, uint64_t active_mask, uint64_t zoom) {
+  if (mg <= 0 || merged_mask == 0) return 0;
+  const int T = 64 - __builtin_clzll(merged_mask);   // the highest merged bit + 1
+  if (T > 40) return 0;
+  const uint64_t below = (uint64_t(1) << T) - 1;
+  const uint64_t kept = active_mask & below;
+  const int R = __builtin_popcountll(kept);
+  // every bit below T merged or kept, none zoomed, at most two kept
+  if (R < 1 || R > 2 || (zoom & below) || ((merged_mask | kept) != below) || T != mg + R) return 0;
+  return kept;
+}
+
 int dd_merge_chunks(int64_t rows, int a, int mg) {
   if (mg < 2) return 0;
   const int64_t ng = int64_t(1) << (mg - 2), G = std::min<int64_t>(32, ng), n_out = rows << a;
@@ -540,14 +631,38 @@ int dd_merge_chunks(int64_t rows, int a, int mg) {
   return lnch;
 }
 
-void launch_dd_merge(const void* T, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
+void launch_dd_merge(const void* T_, int dtype, int64_t rows, int f, int a, int mg, const uint64_t* depAct,
                      const uint64_t* depMrg, uint64_t zoom, bool run, bool dense_bits, void* M, float* MC,
-                     void* part, cudaStream_t s) {
+                     void* part, cudaStream_t s, uint64_t blk) {
+  const void* T = T_;
   const int64_t n_out = rows << a;
   const int64_t cols = int64_t(1) << f;
   const int nbA = (a + 7) / 8, nbM = (mg + 7) / 8;
   run = run && dtype == CUTQC_F32 && mg >= 2 && (reinterpret_cast<uintptr_t>(T) & 15) == 0;
-  if (run) {
+  // the block form needs its kept bits below T described (`blk`), whole
+  // float4 blocks and enough units to fill the GPU (otherwise the warp form
+  // below, a warp per output)
+  const int R = blk ? __builtin_popcountll(blk) : 0;
+  const int TB = mg + R;   // log2 of the block
+  bool block = !run && (R == 1 || R == 2) && dtype == CUTQC_F32 && TB >= 2 && TB <= 40 &&
+               (reinterpret_cast<uintptr_t>(T_) & 15) == 0 &&
+               (n_out >> R) * std::min<int64_t>(32, int64_t(1) << (TB - 2)) >= 152 * 256;
+  if (block) {
+    const int64_t n_units = n_out >> R;
+    const int64_t lanes = n_units * std::min<int64_t>(32, int64_t(1) << (TB - 2));
+    const int lo = (int)(blk & 3);
+    int hb[2] = {-1, -1}, nh = 0;
+    for (int bit = 2; bit < TB; ++bit)
+      if ((blk >> bit) & 1) hb[nh++] = bit - 2;
+    const float* Tf = static_cast<const float*>(T_);
+    float* Mf = static_cast<float*>(M);
+    if (R == 2)
+      k_dd_merge_blk<2><<<grid_for(lanes, 256), 256, 0, s>>>(Tf, cols, a, TB, lo, hb[0], hb[1], depAct, nbA, zoom, Mf,
+                                                             MC, n_units);
+    else
+      k_dd_merge_blk<1><<<grid_for(lanes, 256), 256, 0, s>>>(Tf, cols, a, TB, lo, hb[0], hb[1], depAct, nbA, zoom, Mf,
+                                                             MC, n_units);
+  } else if (run) {
     const int lnch = dd_merge_chunks(rows, a, mg);
     const int dense = dense_bits ? 1 : 0;
     const float* Tf = static_cast<const float*>(T);

@@ -152,6 +152,10 @@ def _synthetic_sub(d, k_in, k_out):
 MERGE_FORMS = {
     "run_dense": [0] * 6 + [1] * 4,            # merged = the lowest 4 index bits, kept bits right above
     "run_zoomed": [0, 0, 3, 0, 2, 0, 1, 1, 1, 1],
+    # block form: every index bit below the highest merged one merged or kept, at most two kept
+    "block_low2": [0, 0, 0, 0, 1, 1, 1, 1, 0, 0],      # merged 2-5, kept 0-1
+    "block_zoom": [0, 3, 0, 0, 0, 1, 1, 1, 0, 1],      # merged 0, 2-4, kept 1, bit 8 zoomed
+    "block_split": [0, 0, 0, 1, 0, 1, 1, 1, 0, 1],     # merged 0, 2-4, 6, kept 1 and 5
     "warp": [0, 1, 1, 1, 0, 1, 1, 1, 0, 0],    # 6 merged values, not on the lowest bits
     "thread": [0, 1, 0, 0, 2, 0, 1, 0, 0, 0],  # 2 merged values
     "zoom_only": [0, 3, 0, 2, 0, 0, 3, 0, 0, 0],
@@ -161,9 +165,11 @@ MERGE_FORMS = {
 
 @pytest.mark.parametrize("form", list(MERGE_FORMS))
 def test_attribute_merged_forms(env, form):
-    """Every merge form (contiguous runs, warp and thread per output, zoom
-    only, nothing merged) against the oracle's attribute-then-merge, FP64 and
-    FP32, on seeded random variant distributions."""
+    """Every merge form (contiguous runs, blocks with one or two kept bits
+    among the merged ones, warp and thread per output, zoom only, nothing
+    merged) against
+    the oracle's attribute-then-merge, FP64 and FP32, on seeded random variant
+    distributions."""
     torch, cutqc = env
     from oracle import attribution as at
     sub = _synthetic_sub(12, 2, 2)
