@@ -141,14 +141,16 @@ def test_misaligned_output_is_rejected(env, sup):
 _sup_ref = {}
 
 
-@pytest.mark.parametrize("algo", ["cc", "auto", "tc_bf16x3", "tc_tf32x3"])
+@pytest.mark.parametrize("algo", ["cc", "auto", "tc_bf16x3", "tc_bf16x6", "tc_tf32x3"])
 def test_supremacy_4x6_full_size(env, sup, algo):
     """Full size (2^24 outputs, the launch configuration the benchmark times):
     every output against the oracle's plain FP64 sum over all 256 Kronecker
     terms on the same FP32 tensors, plus the FP64 sum against the closed form
-    over the FP32 tensors.  On this shape the tensor-core contraction cuts its
-    last round of tiles into 128-column halves over more CTAs; those outputs
-    are among the ones compared."""
+    over the FP32 tensors.  On this shape the bf16 forms prepare their
+    operands in one pass (one block per term, 176 of 256 kept, zero rows up to
+    the end of the last stage) and the contraction cuts its last round of
+    tiles into 128-column halves over more CTAs; those outputs are among the
+    ones compared."""
     torch, cutqc = env
     from oracle import reconstruct as rc
     cc, T32 = sup
