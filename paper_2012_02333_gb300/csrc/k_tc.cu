@@ -1088,11 +1088,20 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint64_t dpass1 = deposit(a.depA, 1, 16ull);   // row bit 4: second pass
     int acc = 0;
     uint32_t acc_phase = 0;
-    TcItem it;
-    for (int i = 0; tc_item(a, i, it); ++i) {
-      // this thread's row: tm*128 + 32q + lane; columns tn*256 + n0 + 32c + j
-      const uint64_t gbase = deposit(a.depA, a.nbA, (uint64_t)it.tm * BM + 32 * q) +
-                             deposit(a.depB, a.nbB, (uint64_t)it.tn * BN + it.n0);
+    // this thread's row of item it: tm*128 + 32q + lane; columns tn*256 + n0 +
+    // 32c + j.  The item's output base comes from the deposit tables in
+    // global memory (dependent round trips to L2), so the next item's is
+    // loaded while this one drains.
+    auto item_base = [&](const TcItem& t) {
+      return deposit(a.depA, a.nbA, (uint64_t)t.tm * BM + 32 * q) + deposit(a.depB, a.nbB, (uint64_t)t.tn * BN + t.n0);
+    };
+    TcItem it, itn;
+    bool have = tc_item(a, 0, it);
+    uint64_t gnext = have ? item_base(it) : 0;
+    for (int i = 0; have; ++i, it = itn) {
+      const uint64_t gbase = gnext;
+      have = tc_item(a, i + 1, itn);
+      if (have) gnext = item_base(itn);
       if (nkb > 0) {
         const bool ok = mbar_wait(&tfull[acc], acc_phase, abort_flag);
         if (!__all_sync(0xffffffffu, ok)) break;
