@@ -47,7 +47,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM traffic (read + write bytes) of one k_tc_gemm launch on this workload from
 # the ncu capture summarised in profiles/k_tc_gemm_supremacy_4x6_k4.md, valid while
 # the kernel source is unchanged (first 16 hex digits of its SHA-256)
-TRAFFIC_TC = {"sha256_16": "f0c5390dd04b69df", "bytes": 10.290e6}
+TRAFFIC_TC = {"sha256_16": "c250ed940ba927e3", "bytes": 10.288e6}
 # Library peaks of the machine's GB300 beside the driver's BF16 and copy figures,
 # measured with `python bench.py --workload peaks --steps 10 --warmup 3`
 # (torch.matmul 8192^3, best of 10): TF32 tensor cores, FP32 without TF32

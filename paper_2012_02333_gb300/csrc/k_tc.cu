@@ -31,7 +31,8 @@
 //              scale by 2^-K, deposit (m, n) into the output index with the
 //              additive per-bit tables held in registers, restage 16 x 32
 //              blocks through shared memory so 16-byte streaming stores go
-//              out in output-address order, FP64 partial sums; it drains one
+//              out in output-address order, compensated FP32 partial sums
+//              (FP64 across threads); it drains one
 //              accumulator while the MMA fills the other.
 // Every wait on an mbarrier is bounded (2 s); on timeout the kernel raises an
 // abort flag, records a status word, lets in-flight copies land and frees TMEM.
@@ -1023,7 +1024,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int hf = (warp - 2) / 4;
     constexpr int CPW = BN / 32 / (EPI_WARPS / 4);   // 32-column chunks per warp
     static_assert(CPW % 4 == 0, "chunks go in pairs, also in half-width items");
-    double local = 0.0;
+    // this thread's share of the FP64 sum, accumulated in FP32 with TwoSum
+    // (sum + compensation, about 48 bits; no FP64 instruction per chunk on
+    // this part's narrow FP64 pipe)
+    float lsum = 0.0f, lcomp = 0.0f;
     // the deposit is additive over disjoint index bits, so a row's output
     // address is dep(row base) + dep(lane) + dep(chunk column base) +
     // dep(column within the chunk); the per-thread parts live in registers
@@ -1114,7 +1118,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       };
       auto process = [&](const int c, uint32_t (&r)[32]) {
         // sum of this 32-column row piece: pairwise in FP32 (error <= 5 * 2^-24 *
-        // sum |v|), then one FP64 add (the FP64 pipe is narrow on this part)
+        // sum |v|), then one compensated FP32 add into the thread's share
         float v[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]) * a.scale;
@@ -1125,7 +1129,12 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int w = 8; w > 0; w >>= 1)
 #pragma unroll
           for (int j = 0; j < w; ++j) t16[j] += t16[j + w];
-        local += (double)t16[0];
+        {
+          const float t = lsum + t16[0];
+          const float bb = t - lsum;
+          lcomp += (lsum - (t - bb)) + (t16[0] - bb);
+          lsum = t;
+        }
         uint64_t dc = 0;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dc = (k == c) ? dcol[k] : dc;
@@ -1221,6 +1230,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     if (a.sum) {
 #pragma unroll
+      double local = (double)lsum + (double)lcomp;
       for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
       if (lane == 0) atomicAdd(a.sum, local);
     }
