@@ -1632,8 +1632,11 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
         const std::string key = fd_key(p, 2, nullptr, 0) + "#bwd" + std::to_string(c);
         plans[c] = &get_plan(ds, key, [&](Plan& P) { build_bwd_plan(P, p, c); });
         const Step& st = plans[c]->steps.back();
+        // per-row sums of both sides, then room for both sides' keys (f <= 24)
+        auto key_room = [](int f) { return f <= 24 ? align_up(size_t(2) << f) : size_t(0); };
         const size_t back = maxcut ? align_up((size_t)(2 + 16) * plans[c]->nodes[st.a].rows() * 8) +
-                                         align_up((size_t)(2 + 16) * plans[c]->nodes[st.b].rows() * 8)
+                                         align_up((size_t)(2 + 16) * plans[c]->nodes[st.b].rows() * 8) +
+                                         key_room(plans[c]->nodes[st.a].f()) + key_room(plans[c]->nodes[st.b].f())
                                    : 0;
         size_t b = 0;
         run_plan(ds, *plans[c], 0, back, [](char*) { return std::vector<const void*>(); }, nullptr, nullptr,
@@ -1663,11 +1666,19 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
         if (maxcut) {
           const Sides sd = split_edges(A, B);
           double* sumsC = reinterpret_cast<double*>(back);
-          double* sumsR = reinterpret_cast<double*>(back + align_up((size_t)(2 + 16) * A.rows() * 8));
-          launch_bwd_rowsums(p->sub[c].tensor, P.dtype, A.rows(), A.f(), sd.inA, sd.brA, sumsC, s);
-          launch_bwd_rowsums(TR, P.dtype, B.rows(), B.f(), sd.inB, sd.brB, sumsR, s);
+          const size_t offR = align_up((size_t)(2 + 16) * A.rows() * 8);
+          double* sumsR = reinterpret_cast<double*>(back + offR);
+          char* kbase = back + offR + align_up((size_t)(2 + 16) * B.rows() * 8);
+          const size_t kbA = bwd_keys_bytes(A.f(), sd.inA, sd.brA), kbB = bwd_keys_bytes(B.f(), sd.inB, sd.brB);
+          uint16_t* keysC = kbA ? reinterpret_cast<uint16_t*>(kbase) : nullptr;
+          uint16_t* keysR = kbB ? reinterpret_cast<uint16_t*>(kbase + (A.f() <= 24 ? align_up(size_t(2) << A.f()) : 0))
+                                : nullptr;
+          if (keysC) launch_bwd_keys(A.f(), sd.inA, sd.brA, keysC, s);
+          if (keysR) launch_bwd_keys(B.f(), sd.inB, sd.brB, keysR, s);
+          launch_bwd_rowsums(p->sub[c].tensor, P.dtype, A.rows(), A.f(), sd.inA, sd.brA, sumsC, s, keysC);
+          launch_bwd_rowsums(TR, P.dtype, B.rows(), B.f(), sd.inB, sd.brB, sumsR, s, keysR);
           launch_bwd_maxcut_grad(rowC, rowR, st.kmax, A.f(), sd.inA, sd.brA, sumsR, B.rows(), scale, grad_tensor[c],
-                                 P.dtype, s);
+                                 P.dtype, s, keysC);
           if (c == 0 && loss_value)
             launch_bwd_maxcut_loss(rowC, rowR, st.kmax, sumsC, A.rows(), sumsR, B.rows(), sd.brA.n, scale,
                                    loss_value, s);
@@ -1736,13 +1747,18 @@ int cutqc_reconstruct_backward(const cutqc_problem* problem, const void* grad_ou
       }
       const size_t bytesA = align_up((size_t)(2 + brA.n) * rowsA * 8);
       const size_t bytesB = align_up((size_t)(2 + brB.n) * rowsB * 8);
-      char* ws = static_cast<char*>(workspace(ds, bytesA + bytesB));
+      const size_t kbA = bwd_keys_bytes(fA, inA, brA), kbB = bwd_keys_bytes(fB, inB, brB);
+      char* ws = static_cast<char*>(workspace(ds, bytesA + bytesB + kbA + kbB));
       double* sumsA = reinterpret_cast<double*>(ws);
       double* sumsB = reinterpret_cast<double*>(ws + bytesA);
-      launch_bwd_rowsums(TA, P.dtype, rowsA, fA, inA, brA, sumsA, s);
-      launch_bwd_rowsums(TB, P.dtype, rowsB, fB, inB, brB, sumsB, s);
-      launch_bwd_maxcut_grad(rowA, rowB, st.kmax, fA, inA, brA, sumsB, rowsB, scale, dA, P.dtype, s);
-      launch_bwd_maxcut_grad(rowB, rowA, st.kmax, fB, inB, brB, sumsA, rowsA, scale, dB, P.dtype, s);
+      uint16_t* keysA = kbA ? reinterpret_cast<uint16_t*>(ws + bytesA + bytesB) : nullptr;
+      uint16_t* keysB = kbB ? reinterpret_cast<uint16_t*>(ws + bytesA + bytesB + kbA) : nullptr;
+      if (keysA) launch_bwd_keys(fA, inA, brA, keysA, s);
+      if (keysB) launch_bwd_keys(fB, inB, brB, keysB, s);
+      launch_bwd_rowsums(TA, P.dtype, rowsA, fA, inA, brA, sumsA, s, keysA);
+      launch_bwd_rowsums(TB, P.dtype, rowsB, fB, inB, brB, sumsB, s, keysB);
+      launch_bwd_maxcut_grad(rowA, rowB, st.kmax, fA, inA, brA, sumsB, rowsB, scale, dA, P.dtype, s, keysA);
+      launch_bwd_maxcut_grad(rowB, rowA, st.kmax, fB, inB, brB, sumsA, rowsA, scale, dB, P.dtype, s, keysB);
       if (loss_value)
         launch_bwd_maxcut_loss(rowA, rowB, st.kmax, sumsA, rowsA, sumsB, rowsB, brA.n, scale, loss_value, s);
     } else {

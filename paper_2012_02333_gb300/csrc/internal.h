@@ -265,11 +265,19 @@ struct BwdBits {
   int n;
   int p[16];
 };
+// The MaxCut adjoint through a per-output key (cut count and bridge bits of
+// each output index, 2 bytes per output): bwd_keys_bytes is the workspace the
+// keys of one side need, 0 when the shape does not take them (f outside
+// 3..24, or more than 4096 (count, bits) combinations); launch_bwd_keys builds
+// them.  With keys the row sums of FP32 tensors run in compensated FP32 and
+// the gradient is a table lookup per output (the same values as without).
+size_t bwd_keys_bytes(int f, const BwdEdges& internal, const BwdBits& sel);
+void launch_bwd_keys(int f, const BwdEdges& internal, const BwdBits& sel, uint16_t* keys, cudaStream_t s);
 void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const BwdEdges& internal, const BwdBits& sel,
-                        double* out, cudaStream_t s);
+                        double* out, cudaStream_t s, const uint16_t* keys = nullptr);
 void launch_bwd_maxcut_grad(const int32_t* rowX, const int32_t* rowY, int kmax, int fX, const BwdEdges& internal,
                             const BwdBits& bitX, const double* sumsY, int64_t rowsY, double scale, void* dX, int dtype,
-                            cudaStream_t s);
+                            cudaStream_t s, const uint16_t* keys = nullptr);
 void launch_bwd_maxcut_loss(const int32_t* rowA, const int32_t* rowB, int kmax, const double* sA, int64_t rowsA,
                             const double* sB, int64_t rowsB, int nbridge, double scale, double* loss, cudaStream_t s);
 void launch_bwd_cc(const void* Y, const void* G, const int32_t* rowX, const int32_t* rowY, int kmax, int fX, int fY,

@@ -94,6 +94,123 @@ __global__ void k_bwd_maxcut_grad(const int32_t* __restrict__ rowX, const int32_
   }
 }
 
+// ---- MaxCut through a per-output key ------------------------------------
+// key[m] = C(m) * 2^nsel + (bridge-endpoint bits of m, bit k = sel.p[k]): the
+// only two things of m that the row sums and the gradient depend on.  Built
+// once per side (2 bytes per output), it replaces the per-element edge loop.
+__global__ void k_bwd_keys(int64_t cols, BwdEdges internal, BwdBits sel, uint16_t* __restrict__ keys) {
+  for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < cols; m += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t b = 0;
+    for (int k = 0; k < sel.n; ++k) b |= (uint32_t)(((uint64_t)m >> sel.p[k]) & 1) << k;
+    keys[m] = (uint16_t)(((uint32_t)cut_count((uint64_t)m, internal) << sel.n) | b);
+  }
+}
+
+// compensated FP32 running sum (TwoSum; the error of each add is carried in c)
+struct BF {
+  float s, c;
+};
+__device__ __forceinline__ BF bf_add(BF a, float b) {
+  const float t = a.s + b;
+  const float bb = t - a.s;
+  return {t, a.c + ((a.s - (t - bb)) + (b - bb))};
+}
+
+// FP32 row sums through the keys, one block per row: S, W and Sel in
+// compensated FP32 (W adds v * C with the product's rounding error recovered
+// exactly by an FMA), 4 outputs per step; FP64 only for the reduction across
+// threads.  The FP64 pipe is narrow on this part, so no FP64 instruction is
+// spent per element.
+__global__ void k_bwd_rowsums_keys(const float* __restrict__ X, int64_t cols, int64_t rows, int nsel,
+                                   const uint16_t* __restrict__ keys, double* __restrict__ out) {
+  __shared__ double red[8][2 + 16];
+  const int64_t row = blockIdx.x;
+  const float4* r = reinterpret_cast<const float4*>(X + row * cols);
+  const ushort4* kk = reinterpret_cast<const ushort4*>(keys);
+  BF S{0.0f, 0.0f}, W{0.0f, 0.0f}, sb[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sb[k] = BF{0.0f, 0.0f};
+  for (int64_t j = threadIdx.x; j < cols / 4; j += blockDim.x) {
+    const float4 v4 = __ldg(r + j);
+    const ushort4 k4 = __ldg(kk + j);
+    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
+    const uint32_t key[4] = {k4.x, k4.y, k4.z, k4.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      S = bf_add(S, v[u]);
+      const float c = (float)(key[u] >> nsel);
+      const float p = v[u] * c;
+      W = bf_add(W, p);
+      W.c += fmaf(v[u], c, -p);   // the exact rounding error of the product
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < nsel) sb[k] = bf_add(sb[k], ((key[u] >> k) & 1) ? v[u] : 0.0f);
+    }
+  }
+  double t[2 + 16];
+  t[0] = (double)S.s + (double)S.c;
+  t[1] = (double)W.s + (double)W.c;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) t[2 + k] = k < nsel ? (double)sb[k].s + (double)sb[k].c : 0.0;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < 2 + 16; ++i) {
+    if (i >= 2 + nsel) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < 2 + 16; ++i)
+      if (i < 2 + nsel) red[wid][i] = t[i];
+  __syncthreads();
+  if (threadIdx.x < 2 + nsel) {
+    double a = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) a += red[i][threadIdx.x];
+    out[(int64_t)threadIdx.x * rows + row] = a;
+  }
+}
+
+// The gradient through the keys: for row e, dX[rowX(e)][m] depends on m only
+// through key[m], so each block first evaluates the (C_max + 1) * 2^nsel
+// values in FP64, in the order k_bwd_maxcut_grad uses, rounded once to T, and
+// then writes table[key[m]] for its share of the row (4 outputs per step):
+// the results equal k_bwd_maxcut_grad's bit for bit.  Grid: rows x chunks.
+template <typename T>
+__global__ void k_bwd_maxcut_grad_keys(const int32_t* __restrict__ rowX, const int32_t* __restrict__ rowY, int kmax,
+                                       int64_t cols, int nchunk, int ntab, int nsel,
+                                       const uint16_t* __restrict__ keys, const double* __restrict__ sumsY,
+                                       int64_t rowsY, double scale, T* __restrict__ dX) {
+  __shared__ T tab[4096];
+  const int e = (int)(blockIdx.x / nchunk), ch = (int)(blockIdx.x % nchunk);
+  if (e >= kmax) return;
+  const int64_t ry = rowY[e];
+  const double S = sumsY[ry], W = sumsY[rowsY + ry];
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) {
+    const int c = i >> nsel;
+    double g = c * S + W;
+    for (int k = 0; k < nsel; ++k) {
+      const double s1 = sumsY[(2 + k) * rowsY + ry];
+      g += ((i >> k) & 1) ? (S - s1) : s1;
+    }
+    tab[i] = (T)(g * scale);
+  }
+  __syncthreads();
+  const int64_t per = cols / 4 / nchunk;   // groups of 4 outputs in this block's chunk
+  const int64_t j0 = (int64_t)ch * per;
+  T* drow = dX + (int64_t)rowX[e] * cols;
+  const ushort4* kk = reinterpret_cast<const ushort4*>(keys);
+  for (int64_t j = j0 + threadIdx.x; j < j0 + per; j += blockDim.x) {
+    const ushort4 k4 = __ldg(kk + j);
+    if constexpr (sizeof(T) == 4) {
+      reinterpret_cast<float4*>(drow)[j] = make_float4(tab[k4.x], tab[k4.y], tab[k4.z], tab[k4.w]);
+    } else {
+      reinterpret_cast<double2*>(drow)[2 * j] = make_double2(tab[k4.x], tab[k4.y]);
+      reinterpret_cast<double2*>(drow)[2 * j + 1] = make_double2(tab[k4.z], tab[k4.w]);
+    }
+  }
+}
+
 // L = s * sum_e [W_A S_B + S_A W_B + sum_k (Sel_A1 (S_B - Sel_B1) + (S_A - Sel_A1) Sel_B1)]
 __global__ void k_bwd_maxcut_loss(const int32_t* __restrict__ rowA, const int32_t* __restrict__ rowB, int kmax,
                                   const double* __restrict__ sA, int64_t rowsA, const double* __restrict__ sB,
@@ -209,9 +326,28 @@ unsigned grid_for(int64_t work) {
 
 }  // namespace
 
-void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const BwdEdges& internal,
-                        const BwdBits& sel, double* out, cudaStream_t s) {
+size_t bwd_keys_bytes(int f, const BwdEdges& internal, const BwdBits& sel) {
+  if (f < 3 || f > 24 || ((int64_t)(internal.n + 1) << sel.n) > 4096) return 0;
+  return ((size_t(2) << f) + 255) / 256 * 256;
+}
+
+void launch_bwd_keys(int f, const BwdEdges& internal, const BwdBits& sel, uint16_t* keys, cudaStream_t s) {
+  if (!bwd_keys_bytes(f, internal, sel)) fail(CUTQC_ERR_UNSUPPORTED, "no key table for this shape");
   const int64_t cols = int64_t(1) << f;
+  k_bwd_keys<<<grid_for(cols), 256, 0, s>>>(cols, internal, sel, keys);
+  count_launch();
+  check_launch("k_bwd_keys");
+}
+
+void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const BwdEdges& internal,
+                        const BwdBits& sel, double* out, cudaStream_t s, const uint16_t* keys) {
+  const int64_t cols = int64_t(1) << f;
+  if (keys && dtype == CUTQC_F32 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
+    k_bwd_rowsums_keys<<<(unsigned)rows, 256, 0, s>>>(static_cast<const float*>(X), cols, rows, sel.n, keys, out);
+    count_launch();
+    check_launch("k_bwd_rowsums_keys");
+    return;
+  }
   if (dtype == CUTQC_F64)
     k_bwd_rowsums<double><<<(unsigned)rows, 256, 0, s>>>(static_cast<const double*>(X), cols, rows, internal, sel, out);
   else
@@ -222,8 +358,24 @@ void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const Bwd
 
 void launch_bwd_maxcut_grad(const int32_t* rowX, const int32_t* rowY, int kmax, int fX, const BwdEdges& internal,
                             const BwdBits& bitX, const double* sumsY, int64_t rowsY, double scale, void* dX, int dtype,
-                            cudaStream_t s) {
+                            cudaStream_t s, const uint16_t* keys) {
   const int64_t cols = int64_t(1) << fX;
+  if (keys && (reinterpret_cast<uintptr_t>(dX) & 15) == 0) {
+    // chunks of at least 1024 outputs, enough blocks to fill the GPU
+    int nchunk = 1;
+    while ((int64_t)kmax * nchunk < 152 * 8 && cols / 4 / (nchunk * 2) >= 256) nchunk *= 2;
+    const int ntab = (internal.n + 1) << bitX.n;
+    const unsigned g = (unsigned)((int64_t)kmax * nchunk);
+    if (dtype == CUTQC_F64)
+      k_bwd_maxcut_grad_keys<double><<<g, 256, 0, s>>>(rowX, rowY, kmax, cols, nchunk, ntab, bitX.n, keys, sumsY,
+                                                        rowsY, scale, static_cast<double*>(dX));
+    else
+      k_bwd_maxcut_grad_keys<float><<<g, 256, 0, s>>>(rowX, rowY, kmax, cols, nchunk, ntab, bitX.n, keys, sumsY,
+                                                       rowsY, scale, static_cast<float*>(dX));
+    count_launch();
+    check_launch("k_bwd_maxcut_grad_keys");
+    return;
+  }
   const unsigned g = grid_for((int64_t)kmax * cols);
   if (dtype == CUTQC_F64)
     k_bwd_maxcut_grad<double><<<g, 256, 0, s>>>(rowX, rowY, kmax, cols, internal, bitX, sumsY, rowsY, scale,

@@ -288,6 +288,18 @@ struct CCArgs {
 // Block tile BM x BN, inner step BK, 256 threads as 16 x 16, each thread a
 // (TM x TN) micro-tile split in two halves per dimension (rows ty*TM/2 + i
 // and BM/2 + ty*TM/2 + i), so shared-memory reads are conflict-free float4s.
+// compensated FP32 running sum (TwoSum: the rounding error of each add is
+// recovered exactly and carried in c); the FP64 pipe is narrow on this part,
+// so per-row sums of FP32 outputs avoid FP64 instructions
+struct FFs {
+  float s, c;
+};
+__device__ __forceinline__ FFs ffs_add(FFs a, float b) {
+  const float s = a.s + b;
+  const float bb = s - a.s;
+  return {s, a.c + ((a.s - (s - bb)) + (b - bb))};
+}
+
 template <typename T, int BM, int BN, int BK>
 __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
   constexpr int TM = BM / 16, TN = BN / 16, HM = TM / 2, HN = TN / 2;
@@ -400,7 +412,9 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
   }
 
   // epilogue: scale, deposit into the output index; the sum accumulates each
-  // row's TN values pairwise in T, then in FP64 (the FP64 pipe is narrow)
+  // row's TN values pairwise in T, then across rows compensated (FP32 tensors)
+  // or in FP64
+  FFs lsum{0.0f, 0.0f};
   double local = 0.0;
   T* out = a.out + (uint64_t)batch * a.out_batch_stride;
   uint64_t gB[TN];
@@ -423,7 +437,10 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
     for (int w = TN / 2; w > 0; w >>= 1)
 #pragma unroll
       for (int j = 0; j < w; ++j) rowv[j] += rowv[j + w];
-    local += (double)rowv[0];
+    if constexpr (sizeof(T) == 4)
+      lsum = ffs_add(lsum, (float)rowv[0]);
+    else
+      local += (double)rowv[0];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       if (a.vecB >= HN && okB[h * HN + HN - 1] && (HN == 2 || HN == 4)) {
@@ -448,6 +465,7 @@ __global__ __launch_bounds__(256) void k_cc_gemm(const CCArgs<T> a) {
     }
   }
   if (a.sum) {
+    if constexpr (sizeof(T) == 4) local = (double)lsum.s + (double)lsum.c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((tid & 31) == 0) red[tid >> 5] = local;
@@ -510,6 +528,7 @@ __global__ __launch_bounds__(256) void k_cc_skinny(const CCArgs<T> a, int swap) 
       }
     }
   }
+  FFs lsum{0.0f, 0.0f};
   double local = 0.0;
   if (m0 < ML) {
     T* out = a.out + (uint64_t)batch * a.out_batch_stride;
@@ -532,10 +551,14 @@ __global__ __launch_bounds__(256) void k_cc_skinny(const CCArgs<T> a, int swap) 
       for (int h = NS / 2; h > 0; h >>= 1)
 #pragma unroll
         for (int n = 0; n < h; ++n) v[n] += v[n + h];
-      local += (double)v[0];
+      if constexpr (sizeof(T) == 4)
+        lsum = ffs_add(lsum, (float)v[0]);
+      else
+        local += (double)v[0];
     }
   }
   if (a.sum) {
+    if constexpr (sizeof(T) == 4) local = (double)lsum.s + (double)lsum.c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
     if ((tid & 31) == 0) red[tid >> 5] = local;
@@ -665,14 +688,6 @@ struct LRArgs {
   int64_t one_tiles_n;
 };
 
-struct FFs {
-  float s, c;
-};
-__device__ __forceinline__ FFs ffs_add(FFs a, float b) {
-  const float s = a.s + b;
-  const float bb = s - a.s;
-  return {s, a.c + ((a.s - (s - bb)) + (b - bb))};
-}
 
 template <typename T, int KC>
 __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m0, int n0, T (*As)[KC],
