@@ -651,6 +651,13 @@ def run_other(args):
                      "kept_terms": k_eff, "t_roof_us": 1e6 * max(t_tc, t_hbm), "peak_file": pk_src,
                      "of": "the whole forward step (preparation and contraction)"})
         extra["roofline"] = roof
+        # the adjoint's HBM roofline: both tensors read once, both gradients
+        # written once (the row sums, keys and tables are a few MB in L2)
+        b_bwd = 2 * sum(t.numel() * 4 for t in ts)
+        extra["adjoint_roofline"] = {"bound": "hbm", "achieved": b_bwd / (ms_bwd / 1e3) / 1e9,
+                                     "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                     "frac": b_bwd / (ms_bwd / 1e3) / 1e9 / pk["hbm_gbs"],
+                                     "algorithmic_bytes": b_bwd, "traffic": None, "peak_file": pk_src}
         if check:
             cutqc.cutqc_reconstruct_fd([problem], [out], "auto", sp)
             cpu, err, _ = oracle_fd_leg(cc, [t.double().cpu().numpy() for t in ts],

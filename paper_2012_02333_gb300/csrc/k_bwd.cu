@@ -116,53 +116,64 @@ __device__ __forceinline__ BF bf_add(BF a, float b) {
   return {t, a.c + ((a.s - (t - bb)) + (b - bb))};
 }
 
-// FP32 row sums through the keys, one block per row: S, W and Sel in
-// compensated FP32 (W adds v * C with the product's rounding error recovered
-// exactly by an FMA), 4 outputs per step; FP64 only for the reduction across
-// threads.  The FP64 pipe is narrow on this part, so no FP64 instruction is
-// spent per element.
-__global__ void k_bwd_rowsums_keys(const float* __restrict__ X, int64_t cols, int64_t rows, int nsel,
-                                   const uint16_t* __restrict__ keys, double* __restrict__ out) {
-  __shared__ double red[8][2 + 16];
+// FP32 row sums through the keys, one block of 512 threads per row: S, W and
+// Sel in compensated FP32 (W adds v * C with the product's rounding error
+// recovered exactly by an FMA), four 16-byte loads in flight per thread; FP64
+// only for the reduction across threads.  The FP64 pipe is narrow on this
+// part, so no FP64 instruction is spent per element.  NS >= the number of
+// bridge bits (registers for exactly that many Sel sums).
+template <int NS>
+__global__ void __launch_bounds__(512) k_bwd_rowsums_keys(const float* __restrict__ X, int64_t cols, int64_t rows,
+                                                          int nsel, const uint16_t* __restrict__ keys,
+                                                          double* __restrict__ out) {
+  constexpr int NV = 2 + NS;
+  __shared__ double red[16][NV];
   const int64_t row = blockIdx.x;
   const float4* r = reinterpret_cast<const float4*>(X + row * cols);
   const ushort4* kk = reinterpret_cast<const ushort4*>(keys);
-  BF S{0.0f, 0.0f}, W{0.0f, 0.0f}, sb[16];
+  BF S{0.0f, 0.0f}, W{0.0f, 0.0f}, sb[NS > 0 ? NS : 1];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) sb[k] = BF{0.0f, 0.0f};
-  for (int64_t j = threadIdx.x; j < cols / 4; j += blockDim.x) {
-    const float4 v4 = __ldg(r + j);
-    const ushort4 k4 = __ldg(kk + j);
-    const float v[4] = {v4.x, v4.y, v4.z, v4.w};
-    const uint32_t key[4] = {k4.x, k4.y, k4.z, k4.w};
+  for (int k = 0; k < NS; ++k) sb[k] = BF{0.0f, 0.0f};
+  const int64_t n4 = cols / 4;
+  for (int64_t j0 = threadIdx.x; j0 < n4; j0 += 4 * (int64_t)blockDim.x) {
+    float4 v4[4];
+    ushort4 k4[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      S = bf_add(S, v[u]);
-      const float c = (float)(key[u] >> nsel);
-      const float p = v[u] * c;
-      W = bf_add(W, p);
-      W.c += fmaf(v[u], c, -p);   // the exact rounding error of the product
+      const int64_t j = j0 + u * (int64_t)blockDim.x;
+      v4[u] = j < n4 ? __ldg(r + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      k4[u] = j < n4 ? __ldg(kk + j) : make_ushort4(0, 0, 0, 0);
+    }
 #pragma unroll
-      for (int k = 0; k < 16; ++k)
-        if (k < nsel) sb[k] = bf_add(sb[k], ((key[u] >> k) & 1) ? v[u] : 0.0f);
+    for (int u = 0; u < 4; ++u) {
+      const float v[4] = {v4[u].x, v4[u].y, v4[u].z, v4[u].w};
+      const uint32_t key[4] = {k4[u].x, k4[u].y, k4[u].z, k4[u].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        S = bf_add(S, v[e]);
+        const float c = (float)(key[e] >> nsel);
+        const float p = v[e] * c;
+        W = bf_add(W, p);
+        W.c += fmaf(v[e], c, -p);   // the exact rounding error of the product
+#pragma unroll
+        for (int k = 0; k < NS; ++k)
+          if (k < nsel) sb[k] = bf_add(sb[k], ((key[e] >> k) & 1) ? v[e] : 0.0f);
+      }
     }
   }
-  double t[2 + 16];
+  double t[NV];
   t[0] = (double)S.s + (double)S.c;
   t[1] = (double)W.s + (double)W.c;
 #pragma unroll
-  for (int k = 0; k < 16; ++k) t[2 + k] = k < nsel ? (double)sb[k].s + (double)sb[k].c : 0.0;
+  for (int k = 0; k < NS; ++k) t[2 + k] = (double)sb[k].s + (double)sb[k].c;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int i = 0; i < 2 + 16; ++i) {
-    if (i >= 2 + nsel) break;
+  for (int i = 0; i < NV; ++i)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t[i] += __shfl_xor_sync(0xffffffffu, t[i], o);
-  }
   if (lane == 0)
 #pragma unroll
-    for (int i = 0; i < 2 + 16; ++i)
-      if (i < 2 + nsel) red[wid][i] = t[i];
+    for (int i = 0; i < NV; ++i) red[wid][i] = t[i];
   __syncthreads();
   if (threadIdx.x < 2 + nsel) {
     double a = 0.0;
@@ -343,7 +354,13 @@ void launch_bwd_rowsums(const void* X, int dtype, int64_t rows, int f, const Bwd
                         const BwdBits& sel, double* out, cudaStream_t s, const uint16_t* keys) {
   const int64_t cols = int64_t(1) << f;
   if (keys && dtype == CUTQC_F32 && (reinterpret_cast<uintptr_t>(X) & 15) == 0) {
-    k_bwd_rowsums_keys<<<(unsigned)rows, 256, 0, s>>>(static_cast<const float*>(X), cols, rows, sel.n, keys, out);
+    const float* Xf = static_cast<const float*>(X);
+    if (sel.n <= 2)
+      k_bwd_rowsums_keys<2><<<(unsigned)rows, 512, 0, s>>>(Xf, cols, rows, sel.n, keys, out);
+    else if (sel.n <= 4)
+      k_bwd_rowsums_keys<4><<<(unsigned)rows, 512, 0, s>>>(Xf, cols, rows, sel.n, keys, out);
+    else
+      k_bwd_rowsums_keys<16><<<(unsigned)rows, 512, 0, s>>>(Xf, cols, rows, sel.n, keys, out);
     count_launch();
     check_launch("k_bwd_rowsums_keys");
     return;
