@@ -589,8 +589,29 @@ def run_other(args):
         bytes_alg = sum(o.numel() * 4 for o in outs) + sum(t.numel() * 4 for ts in tss for t in ts)
         pk, pk_src = peaks()
         gbs = bytes_alg / (ms / 1e3) / 1e9
+        # the instances whose final contraction takes the tensor cores (a
+        # single call in the automatic form chooses them), as a batch of their
+        # own: the split-precision form against the FP32 CUDA-core form
+        tc_idx = []
+        for i, (p, o) in enumerate(zip(problems, outs)):
+            cutqc.cutqc_reconstruct_fd([p], [o], "auto", sums[i:i + 1])
+            if cutqc.last_algo() != cutqc.CUTQC_CC:
+                tc_idx.append(i)
+        tp, to = [problems[i] for i in tc_idx], [outs[i] for i in tc_idx]
+        tc_sub = {}
+        if tc_idx:
+            tc_sub = {"instances": tc_idx, "n_outputs": sum(2 ** batch[i].n for i in tc_idx),
+                      "split_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(tp, to, "auto", sums[:len(tp)]),
+                                        "tc_subset"),
+                      "cc_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(tp, to, "cc", sums[:len(tp)]),
+                                     "tc_subset_cc"),
+                      "what": "the instances whose final contraction has more than 16 kept terms (the "
+                              "tensor-core form), as one graph-captured batch: automatic split-precision "
+                              "form against every contraction on the FP32 CUDA-core form"}
+            tc_sub["speedup_vs_cc"] = tc_sub["cc_ms"] / tc_sub["split_ms"]
         extra = {"cc_only_ms": timed(lambda: cutqc.cutqc_reconstruct_fd(problems, outs, "cc", sums), "cc"),
                  "cc_only": "every instance on the FP32 CUDA-core form, same graph replay",
+                 "tensor_core_subset": tc_sub,
                  "roofline": {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                               "frac": gbs / pk["hbm_gbs"], "traffic": None, "algorithmic_bytes": bytes_alg,
                               "peak_file": pk_src}}

@@ -1134,7 +1134,8 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
   };
   // the problems whose final contraction is deferred into the batched
   // low-rank launches (the same decision run_plan takes), and the rest
-  std::vector<int> deferred, direct, others;
+  std::vector<int> direct;
+  std::vector<char> is_deferred(n, 0);
   for (int i = 0; i < n; ++i) {
     const Plan& P = *plans[i];
     const Step& st = P.steps.back();
@@ -1150,14 +1151,42 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
                           !tc_supported(c);
     const bool defer = cc_final && lowrank_eligible(c) && !is_host_memory(out[i]);
     // a deferred problem without group builds launches nothing of its own
-    (defer ? (P.steps.size() == 1 ? direct : deferred) : others).push_back(i);
+    if (defer && P.steps.size() == 1)
+      direct.push_back(i);
+    else
+      is_deferred[i] = defer;
   }
-  // eager run of the whole batch on the caller's stream
+  // the other problems over the side branches, largest output first onto
+  // the least loaded branch; each branch runs its deferred problems' group
+  // builds, then one batched low-rank launch of their final contractions,
+  // then its other problems, so no branch waits for another's group builds
+  // (the large low-rank launches of different branches, of different term
+  // classes, then run beside each other and beside the short launches)
+  std::vector<int> rest;
+  for (int i = 0; i < n; ++i)
+    if (std::find(direct.begin(), direct.end(), i) == direct.end()) rest.push_back(i);
+  std::stable_sort(rest.begin(), rest.end(), [&](int x, int y) { return plans[x]->n_out > plans[y]->n_out; });
+  std::vector<std::vector<int>> on(kBranches);
+  std::vector<double> load(kBranches, 0.0);
+  for (int i : rest) {
+    int bmin = 1;
+    for (int b = 2; b < kBranches; ++b)
+      if (load[b] < load[bmin]) bmin = b;
+    on[bmin].push_back(i);
+    load[bmin] += std::ldexp(1.0, plans[i]->n_out);
+  }
+  auto run_branch = [&](int b, cudaStream_t st) {
+    for (int i : on[b])
+      if (is_deferred[i]) run_one(i, st, ws + off[i], true);
+    launch_deferred(st, ("b" + std::to_string(b)).c_str());
+    for (int i : on[b])
+      if (!is_deferred[i]) run_one(i, st, ws + off[i], false);
+  };
+  // eager run of the whole batch on the caller's stream (it also uploads the
+  // work lists that the captured launches reuse)
   for (int i : direct) run_one(i, s, ws + off[i], true);
   launch_deferred(s, "a");
-  for (int i : deferred) run_one(i, s, ws + off[i], true);
-  launch_deferred(s, "b");
-  for (int i : others) run_one(i, s, ws + off[i], false);
+  for (int b = 1; b < kBranches; ++b) run_branch(b, s);
   // capture the same launches over parallel branches for later calls
   if (!ds.fork) {
     for (int b = 0; b < kBranches; ++b) {
@@ -1173,20 +1202,11 @@ static void run_batch(DeviceState& ds, const cutqc_problem* problems, int n, voi
     CUTQC_CUDA(cudaStreamBeginCapture(ds.branch[0], cudaStreamCaptureModeThreadLocal));
     CUTQC_CUDA(cudaEventRecord(ds.fork, ds.branch[0]));
     for (int b = 1; b < kBranches; ++b) CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[b], ds.fork, 0));
-    // branch 0 runs the batched low-rank launches: at once for the problems
-    // without group builds, then for the rest once their group builds (on
-    // the other branches) are done; the other problems follow on branches
-    // 1.. and run beside it
+    // branch 0: the batched low-rank launch of the problems without group
+    // builds, at once; branches 1..: the rest, beside it
     for (int i : direct) run_one(i, ds.branch[0], ws + off[i], true);
     launch_deferred(ds.branch[0], "a");
-    int k = 0;
-    for (int i : deferred) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], true);
-    for (int b = 1; b < kBranches; ++b) {
-      CUTQC_CUDA(cudaEventRecord(ds.mid[b], ds.branch[b]));
-      CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.mid[b], 0));
-    }
-    launch_deferred(ds.branch[0], "b");
-    for (int i : others) run_one(i, ds.branch[1 + (k++ % (kBranches - 1))], ws + off[i], false);
+    for (int b = 1; b < kBranches; ++b) run_branch(b, ds.branch[b]);
     for (int b = 1; b < kBranches; ++b) {
       CUTQC_CUDA(cudaEventRecord(ds.join[b], ds.branch[b]));
       CUTQC_CUDA(cudaStreamWaitEvent(ds.branch[0], ds.join[b], 0));

@@ -151,6 +151,8 @@ struct RowStatsJobs {   // up to two tensors whose rows get non-zero flags and m
   int32_t* flags[2];
   float* rmax[2];
   int chunks[2];          // blocks per row (set by the launcher; long rows of few-row tensors are split)
+  int warp[2];            // 1: rows of at most 2048 values, reduced by warps (set by the launcher)
+  int64_t blocks0;        // blocks of tensor 0 (set by the launcher)
   CompactJob cj;
 };
 void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s);

@@ -153,9 +153,80 @@ __device__ void compact_block(const CompactJob& cj) {
   }
 }
 
-// one block per row of up to two tensors: row 0 .. rows0-1 of job 0, then job
-// 1; with a compaction job, the block that finishes last (an atomic count
-// after a fence: every other block's statistics are then visible) compacts
+// Rows of at most 2048 values (tensors with many cut rows: 4^8 rows of 64
+// values occur) are reduced by warps, not blocks: a warp task is one row, or
+// for rows of at most 32 vectors one 32-vector chunk of consecutive rows,
+// read with one coalesced vector load per lane and reduced over the lanes of
+// each row by shuffles.  8 warp tasks per block.
+template <typename T>
+__device__ __forceinline__ void row_stats_warp(const T* __restrict__ t, int64_t rows, int64_t cols, int64_t task,
+                                               int32_t* __restrict__ flags, float* __restrict__ rmax) {
+  using V = typename Vec<T>::type;
+  constexpr int W = Vec<T>::W;
+  const int lane = (int)threadIdx.x & 31;
+  float m = 0.0f;
+  int nz = 0;
+  auto take = [&](const V& v) {
+    const T* x = reinterpret_cast<const T*>(&v);
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      nz |= (x[w] != T(0));
+      if constexpr (sizeof(T) == 4)
+        m = fmaxf(m, fabsf(x[w]));
+      else
+        m = fmaxf(m, (float)fabs(x[w]));
+    }
+  };
+  const int64_t nv = cols / W;   // vectors per row
+  if (nv <= 32) {
+    // one chunk of 32 vectors holds 32 / nv whole rows
+    const int64_t e = task * 32 + lane;          // vector index
+    const int64_t row = e / nv;
+    if (row < rows) take(__ldg(reinterpret_cast<const V*>(t) + e));
+    for (int o = 1; o < (int)nv; o <<= 1) {
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      nz |= __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    if (row < rows && (lane % (int)nv) == 0) {
+      flags[row] = nz;
+      rmax[row] = m;
+    }
+  } else {
+    const int64_t row = task;
+    if (row < rows) {
+      const V* rv = reinterpret_cast<const V*>(t + row * cols);
+      for (int64_t i = lane; i < nv; i += 128) {
+        V v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i + 32 * u < nv) v[u] = __ldg(rv + i + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i + 32 * u < nv) take(v[u]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      nz |= __shfl_xor_sync(0xffffffffu, nz, o);
+    }
+    if (row < rows && lane == 0) {
+      flags[row] = nz;
+      rmax[row] = m;
+    }
+  }
+}
+
+// warp tasks of a tensor in the warp form
+__host__ __device__ __forceinline__ int64_t row_stats_tasks(int64_t rows, int64_t cols, int W) {
+  const int64_t nv = cols / W;
+  return nv <= 32 ? (rows * nv + 31) / 32 : rows;
+}
+
+// up to two tensors: the blocks of job 0, then those of job 1 (one per row,
+// per chunk of a long row, or per 8 warp tasks); with a compaction job, the
+// block that finishes last (an atomic count after a fence: every other
+// block's statistics are then visible) compacts
 template <typename T>
 __global__ void k_row_stats(RowStatsJobs jobs) {
   CUTQC_PDL_LAUNCH();   // the operand preparation may launch and wait on this grid
@@ -164,8 +235,8 @@ __global__ void k_row_stats(RowStatsJobs jobs) {
   __shared__ float part_max;
   int j = 0;
   int64_t u = blockIdx.x;
-  if (u >= jobs.rows[0] * jobs.chunks[0]) {
-    u -= jobs.rows[0] * jobs.chunks[0];
+  if (u >= jobs.blocks0) {
+    u -= jobs.blocks0;
     j = 1;
   }
   const T* t = static_cast<const T*>(jobs.t[j]);
@@ -174,7 +245,11 @@ __global__ void k_row_stats(RowStatsJobs jobs) {
   const int64_t cols = j ? jobs.cols[1] : jobs.cols[0];
   int32_t* flags = j ? jobs.flags[1] : jobs.flags[0];
   float* rmax = j ? jobs.rmax[1] : jobs.rmax[0];
-  if (chunks == 1) {
+  const int warp_form = j ? jobs.warp[1] : jobs.warp[0];
+  if (warp_form) {
+    const int64_t rows = j ? jobs.rows[1] : jobs.rows[0];
+    row_stats_warp<T>(t, rows, cols, u * 8 + (threadIdx.x >> 5), flags, rmax);
+  } else if (chunks == 1) {
     row_stats_block<T>(t + u * cols, cols, flags + u, rmax + u);
   } else {
     // a chunk of a long row: combined into the row's cleared flag and maximum
@@ -647,16 +722,21 @@ void launch_typed(const Contraction& c, cudaStream_t s) {
 
 // ---- low-rank contraction (at most 16 kept terms) --------------------------
 // P[m][n] = scale * sum_{k < kc} A[ra[k]][m] B[rb[k]][n] for kc <= 16, the
-// shape of circuits cut by one or two wires (4 or 16 terms) whose outputs run
-// to 2^26 .. 2^28: the work is a few FMAs per output and the output stream is
-// everything, so a thread keeps 4 consecutive columns of the kc B rows in
-// registers and walks rows m, staging each item's A panel (64 rows x kc) in
-// shared memory, and every output goes out as one 16-byte streaming store
-// (FP32; two for FP64) of 4 consecutive outputs (the N side owns the two
-// lowest output bits).  The FP64 sum is carried per thread in compensated
-// FP32 (FP32 tensors) and added once per warp and item.  Work items (problem,
-// 64 rows, up to 1024 columns) come from a device list over many problems, so
-// every low-rank final contraction of a batch is one launch.
+// shape of circuits cut by one or two wires (4 or 16 terms) and of a
+// disconnected subcircuit joined as an outer product (1 term), whose outputs
+// run to 2^26 .. 2^28: the work is a few FMAs per output and the output
+// stream is everything.  A thread keeps 4 consecutive columns of the kc B
+// rows in registers (the N side owns the two lowest output bits) and walks
+// the rows of 256-row panels of A staged in shared memory with the rows'
+// output offsets; every 4 outputs go out as one 16-byte streaming store
+// (FP32; two for FP64), four rows per unrolled step.  Work items are
+// (problem, 256 rows, up to 1024 columns), listed per problem column-tile
+// by column-tile; block b takes items b, b + G, b + 2G, ... (measured faster
+// than contiguous ranges per block: the blocks then write neighbouring
+// items at any time), and the next item's A panel is copied into the other
+// half of a double-buffered panel while the current one is written (no DRAM
+// round trip between items).  The FP64 sum is carried per thread in
+// compensated FP32 (FP32 tensors) and added once per warp and problem.
 template <typename T>
 struct LRProblem {
   const T* A;
@@ -676,7 +756,7 @@ struct LRItem {
   int n0;
   int64_t m0;
 };
-constexpr int LR_MB = 256;     // rows per item
+constexpr int LR_MB = 256;     // rows per item (one staged panel)
 constexpr int LR_NT = 1024;    // columns per item (256 threads x 4)
 
 template <typename T>
@@ -685,63 +765,108 @@ struct LRArgs {
   const LRItem* items;
   int64_t n_items;
   LRProblem<T> one;
-  int64_t one_tiles_n;
+  int64_t one_tiles_m;         // single problem: item it is column tile it / tiles_m, row tile it % tiles_m
 };
 
-
+// blocks per SM of each term class (register budget of the B columns)
 template <typename T, int KC>
-__device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m0, int n0, T (*As)[KC],
-                                        uint64_t* gAs) {
-  const int tid = threadIdx.x, lane = tid & 31;
+constexpr int lr_min_blocks() {
+  return sizeof(T) == 8 ? (KC == 16 ? 1 : 2) : (KC == 16 ? 2 : (KC == 4 ? 4 : 6));
+}
+// two A panels, the output offsets of the low 8 row bits
+template <typename T, int KC>
+constexpr size_t lr_smem_bytes() {
+  return 2 * (size_t)LR_MB * KC * sizeof(T) + 256 * sizeof(uint64_t);
+}
+
+__device__ __forceinline__ void lr_cp_async(void* smem, const void* gmem, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void lr_cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void lr_cp_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// the thread's row of an item's A panel, copied to shared memory without
+// passing through registers (so the copy stays in flight while the current
+// item is written); zero beyond kc and beyond the last row
+template <typename T, int KC>
+__device__ __forceinline__ void lr_fetch(const LRProblem<T>& p, int kc, int64_t m0, T (*As)[KC]) {
   const int64_t M = int64_t(1) << p.fA;
+  const int64_t m = m0 + threadIdx.x;
+  const bool ok = m < M;
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    if (k < kc && ok)
+      lr_cp_async(&As[threadIdx.x][k], p.A + (int64_t)__ldg(p.crow + k) * M + m, (int)sizeof(T));
+    else
+      As[threadIdx.x][k] = T(0);
+  }
+  lr_cp_commit();
+}
+
+// output offset of the rows m0 .. m0 + 255 beyond their low 8 bits (m0 is a
+// multiple of 256, so the low byte of row m0 + i is i)
+template <typename T>
+__device__ __forceinline__ uint64_t lr_base(const LRProblem<T>& p, int64_t m0) {
+  uint64_t g = 0;
+  for (int b = 1; b < p.nbA; ++b) g += __ldg(p.depA + b * 256 + ((m0 >> (8 * b)) & 255));
+  return g;
+}
+
+// this thread's 4 columns of the kc B rows, scaled by 2^-K (a power of two:
+// exact), and their output offset
+template <typename T, int KC>
+__device__ __forceinline__ void lr_load_b(const LRProblem<T>& p, int kc, int n0, T (&b)[KC][4], uint64_t& gB) {
   const int N = 1 << p.fB;
   const int cols = N < LR_NT ? N : LR_NT;
-  const int tpr = cols / 4;                 // threads per row
-  const int rpp = 256 / tpr;                // rows per pass
-  const int c4 = 4 * (tid % tpr), rs = tid / tpr;
-  const int32_t* ra = p.crow;
+  const int n = n0 + 4 * ((int)threadIdx.x % (cols / 4));
   const int32_t* rb = p.crow + p.kmax;
-  // the A panel and the rows' output offsets
-  // the panel carries the scale 2^-K (a power of two: exact)
   const T sc = (T)p.scale;
-  for (int idx = tid; idx < LR_MB * KC; idx += 256) {
-    const int i = idx % LR_MB, k = idx / LR_MB;
-    As[i][k] = (k < kc && m0 + i < M) ? p.A[(int64_t)ra[k] * M + m0 + i] * sc : T(0);
-  }
-  for (int i = tid; i < LR_MB; i += 256) gAs[i] = m0 + i < M ? deposit(p.depA, p.nbA, (uint64_t)(m0 + i)) : 0;
-  // this thread's 4 columns of the kc B rows
-  T b[KC][4];
-  const int n = n0 + c4;
 #pragma unroll
   for (int k = 0; k < KC; ++k) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) b[k][j] = T(0);
-    if (k < kc && rs < rpp) {
-      const T* src = p.B + (int64_t)rb[k] * N + n;
+    if (k < kc) {
+      const T* src = p.B + (int64_t)__ldg(rb + k) * N + n;
       if constexpr (sizeof(T) == 4) {
         const float4 v = __ldg(reinterpret_cast<const float4*>(src));
-        b[k][0] = v.x;
-        b[k][1] = v.y;
-        b[k][2] = v.z;
-        b[k][3] = v.w;
+        b[k][0] = v.x * sc;
+        b[k][1] = v.y * sc;
+        b[k][2] = v.z * sc;
+        b[k][3] = v.w * sc;
       } else {
         const double2 v0 = __ldg(reinterpret_cast<const double2*>(src));
         const double2 v1 = __ldg(reinterpret_cast<const double2*>(src) + 1);
-        b[k][0] = v0.x;
-        b[k][1] = v0.y;
-        b[k][2] = v1.x;
-        b[k][3] = v1.y;
+        b[k][0] = v0.x * sc;
+        b[k][1] = v0.y * sc;
+        b[k][2] = v1.x * sc;
+        b[k][3] = v1.y * sc;
       }
     }
   }
-  const uint64_t gB = deposit(p.depB, p.nbB, (uint64_t)n);
-  __syncthreads();
-  FFs acc{0.0f, 0.0f};
-  double acc64 = 0.0;
-  const int rows = (int)((M - m0) < LR_MB ? (M - m0) : LR_MB);
-  for (int i = rs; i < rows; i += rpp) {
-    T v[4] = {T(0), T(0), T(0), T(0)};
-    // the row's panel values, 16 bytes per shared-memory read (zero beyond kc)
+  gB = deposit(p.depB, p.nbB, (uint64_t)n);
+}
+
+template <typename T>
+struct LRAcc {
+  FFs f{0.0f, 0.0f};
+  double d = 0.0;
+};
+
+// one output row of 4 columns: the row's panel values (16 bytes per
+// shared-memory read, zero beyond kc), the store and the running sum
+template <typename T, int KC>
+__device__ __forceinline__ void lr_row(T* __restrict__ out, const T (*As)[KC], const uint64_t* tab0, uint64_t base,
+                                       int i, const T (&b)[KC][4], uint64_t gB, LRAcc<T>& acc) {
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if constexpr (KC == 1) {
+    const T a0 = As[i][0];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = a0 * b[0][j];
+  } else {
 #pragma unroll
     for (int k0 = 0; k0 < KC; k0 += 16 / (int)sizeof(T)) {
       T a[16 / sizeof(T)];
@@ -761,49 +886,125 @@ __device__ __forceinline__ void lr_item(const LRProblem<T>& p, int kc, int64_t m
 #pragma unroll
         for (int j = 0; j < 4; ++j) v[j] = fma(a[kk], b[k0 + kk][j], v[j]);
     }
-    T* dst = p.out + gAs[i] + gB;
-    if constexpr (sizeof(T) == 4) {
-      __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
-      acc = ffs_add(acc, (v[0] + v[1]) + (v[2] + v[3]));
-    } else {
-      __stcs(reinterpret_cast<double2*>(dst), make_double2(v[0], v[1]));
-      __stcs(reinterpret_cast<double2*>(dst) + 1, make_double2(v[2], v[3]));
-      acc64 += (v[0] + v[1]) + (v[2] + v[3]);
-    }
   }
-  if (p.sum) {
-    double t = sizeof(T) == 4 ? (double)acc.s + (double)acc.c : acc64;
+  T* dst = out + (base + tab0[i] + gB);
+  if constexpr (sizeof(T) == 4) {
+    __stcs(reinterpret_cast<float4*>(dst), make_float4(v[0], v[1], v[2], v[3]));
+    acc.f = ffs_add(acc.f, (v[0] + v[1]) + (v[2] + v[3]));
+  } else {
+    __stcs(reinterpret_cast<double2*>(dst), make_double2(v[0], v[1]));
+    __stcs(reinterpret_cast<double2*>(dst) + 1, make_double2(v[2], v[3]));
+    acc.d += (v[0] + v[1]) + (v[2] + v[3]);
+  }
+}
+
+// the rows of one item from a staged panel, four rows per step
+template <typename T, int KC>
+__device__ __forceinline__ void lr_rows(const LRProblem<T>& p, int64_t m0, const T (*As)[KC], const uint64_t* tab0,
+                                        uint64_t base, const T (&b)[KC][4], uint64_t gB, LRAcc<T>& acc) {
+  const int64_t M = int64_t(1) << p.fA;
+  const int N = 1 << p.fB;
+  const int cols = N < LR_NT ? N : LR_NT;
+  const int tpr = cols / 4;                 // threads per row
+  const int rpp = 256 / tpr;                // rows per pass
+  const int rs = (int)threadIdx.x / tpr;
+  const int rows = (int)((M - m0) < LR_MB ? (M - m0) : LR_MB);
+  T* __restrict__ out = p.out;
+  int i = rs;
+  for (; i + 3 * rpp < rows; i += 4 * rpp) {
+    lr_row<T, KC>(out, As, tab0, base, i, b, gB, acc);
+    lr_row<T, KC>(out, As, tab0, base, i + rpp, b, gB, acc);
+    lr_row<T, KC>(out, As, tab0, base, i + 2 * rpp, b, gB, acc);
+    lr_row<T, KC>(out, As, tab0, base, i + 3 * rpp, b, gB, acc);
+  }
+  for (; i < rows; i += rpp) lr_row<T, KC>(out, As, tab0, base, i, b, gB, acc);
+}
+
+// the warp's share of the FP64 sum, added to the problem's sum
+template <typename T>
+__device__ __forceinline__ void lr_flush(double* sum, LRAcc<T>& acc) {
+  if (sum) {
+    double t = sizeof(T) == 4 ? (double)acc.f.s + (double)acc.f.c : acc.d;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0 && t != 0.0) atomicAdd(p.sum, t);
+    if ((threadIdx.x & 31) == 0 && t != 0.0) atomicAdd(sum, t);
   }
-  __syncthreads();   // the panel is rewritten by the next item
+  acc = LRAcc<T>{};
 }
 
-// KC = 4 (one cut between the final groups) or 16 (two): the register and
-// shared-memory footprint of the smaller form lets more blocks share an SM
+// KC = 1 (an outer product), 4 (one cut between the final groups) or 16
+// (two): the register and shared-memory footprint of the smaller forms lets
+// more blocks share an SM
 template <typename T, int KC>
-__global__ __launch_bounds__(256, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)) void k_lowrank(const LRArgs<T> a) {
-  __shared__ __align__(16) T As[LR_MB][KC];
-  __shared__ uint64_t gAs[LR_MB];
-  for (int64_t it = blockIdx.x; it < a.n_items; it += gridDim.x) {
-    LRProblem<T> p;
-    int64_t m0;
-    int n0;
-    if (a.probs) {
-      const LRItem item = a.items[it];
-      p = a.probs[item.prob];
-      m0 = item.m0;
-      n0 = item.n0;
+__global__ __launch_bounds__(256, lr_min_blocks<T, KC>()) void k_lowrank(const LRArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char lr_smem[];
+  __shared__ LRProblem<T> sp;
+  T(*As)[LR_MB][KC] = reinterpret_cast<T(*)[LR_MB][KC]>(lr_smem);
+  uint64_t* tab0 = reinterpret_cast<uint64_t*>(lr_smem + 2 * (size_t)LR_MB * KC * sizeof(T));
+  const int64_t it0 = blockIdx.x, it1 = a.n_items, step = gridDim.x;
+  if (it0 >= it1) return;
+  auto item_of = [&](int64_t it, int& prob, int64_t& m0, int& n0) {
+    if (a.items) {
+      const LRItem x = a.items[it];
+      prob = x.prob;
+      m0 = x.m0;
+      n0 = x.n0;
     } else {
-      p = a.one;
-      m0 = (it / a.one_tiles_n) * LR_MB;
-      n0 = (int)(it % a.one_tiles_n) * LR_NT;
+      prob = 0;
+      m0 = (it % a.one_tiles_m) * LR_MB;
+      n0 = (int)(it / a.one_tiles_m) * LR_NT;
     }
-    lr_item<T, KC>(p, *p.kcount, m0, n0, As, gAs);
+  };
+  // the problem's parameters and its low-byte output offsets into shared memory
+  auto begin_problem = [&](int prob) {
+    if (threadIdx.x == 0) sp = a.probs ? a.probs[prob] : a.one;
+    __syncthreads();
+    tab0[threadIdx.x] = __ldg(sp.depA + threadIdx.x);
+    __syncthreads();
+  };
+  int prob, n0;
+  int64_t m0;
+  item_of(it0, prob, m0, n0);
+  begin_problem(prob);
+  int kc = *sp.kcount;
+  lr_fetch<T, KC>(sp, kc, m0, As[0]);
+  T b[KC][4];
+  uint64_t gB;
+  lr_load_b<T, KC>(sp, kc, n0, b, gB);
+  uint64_t base = lr_base(sp, m0);
+  LRAcc<T> acc;
+  lr_cp_wait();
+  __syncthreads();
+  int buf = 0;
+  for (int64_t it = it0; it < it1; it += step) {
+    const bool more = it + step < it1;
+    int nprob = prob, nn0 = n0;
+    int64_t nm0 = m0;
+    if (more) item_of(it + step, nprob, nm0, nn0);
+    const bool same = more && nprob == prob;
+    // the next item's panel goes to the other buffer (last read before the
+    // previous barrier) while this item is written
+    if (same) lr_fetch<T, KC>(sp, kc, nm0, As[buf ^ 1]);
+    lr_rows<T, KC>(sp, m0, As[buf], tab0, base, b, gB, acc);
+    if (!same) lr_flush<T>(sp.sum, acc);
+    if (more) {
+      if (!same) {
+        __syncthreads();   // every thread is done with the old problem's parameters
+        begin_problem(nprob);
+        kc = *sp.kcount;
+        lr_fetch<T, KC>(sp, kc, nm0, As[buf ^ 1]);
+      }
+      if (!same || nn0 != n0) lr_load_b<T, KC>(sp, kc, nn0, b, gB);
+      base = lr_base(sp, nm0);
+      prob = nprob;
+      m0 = nm0;
+      n0 = nn0;
+    }
+    lr_cp_wait();
+    __syncthreads();
+    buf ^= 1;
   }
 }
-
 
 // ---- every low-rank problem of a batch in three launches -----------------
 // k_batch_rowstats: the row non-zero flags and max |.| of every problem's two
@@ -817,8 +1018,10 @@ __global__ __launch_bounds__(256, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)) void k
 struct BatchRowJob {
   const void* T;
   int64_t rows, cols;
-  int64_t first;               // the job's first unit (row chunk) in the global unit order
+  int64_t first;               // the job's first partial slot (row chunk) in the global slot order
+  int64_t bfirst;              // the job's first block unit
   int chunks;                  // column chunks per row
+  int warp;                    // rows of at most 2048 values: 8 warp tasks per block unit, one slot per row
   int32_t* flags;
   float* rmax;
 };
@@ -826,16 +1029,23 @@ constexpr int64_t BATCH_CHUNK = int64_t(1) << 16;   // columns per row chunk
 
 template <typename T>
 __global__ __launch_bounds__(256) void k_batch_rowstats(const BatchRowJob* __restrict__ rjobs, int nrjobs,
-                                                        int64_t nunits, int32_t* __restrict__ part_nz,
+                                                        int64_t nblocks, int32_t* __restrict__ part_nz,
                                                         float* __restrict__ part_max) {
-  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+  for (int64_t u = blockIdx.x; u < nblocks; u += gridDim.x) {
     int j = 0;
-    while (j + 1 < nrjobs && rjobs[j + 1].first <= u) ++j;
+    while (j + 1 < nrjobs && rjobs[j + 1].bfirst <= u) ++j;
     const BatchRowJob& rj = rjobs[j];
-    const int64_t row = (u - rj.first) / rj.chunks, ch = (u - rj.first) % rj.chunks;
-    const int64_t cc = rj.cols / rj.chunks;
-    row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols + ch * cc, cc, part_nz + u, part_max + u);
-    __syncthreads();   // the block's shared reduction buffer is reused by the next unit
+    if (rj.warp) {
+      row_stats_warp<T>(static_cast<const T*>(rj.T), rj.rows, rj.cols, (u - rj.bfirst) * 8 + (threadIdx.x >> 5),
+                        part_nz + rj.first, part_max + rj.first);
+    } else {
+      const int64_t unit = u - rj.bfirst;
+      const int64_t row = unit / rj.chunks, ch = unit % rj.chunks;
+      const int64_t cc = rj.cols / rj.chunks;
+      row_stats_block<T>(static_cast<const T*>(rj.T) + row * rj.cols + ch * cc, cc, part_nz + rj.first + unit,
+                         part_max + rj.first + unit);
+      __syncthreads();   // the block's shared reduction buffer is reused by the next unit
+    }
   }
 }
 
@@ -883,21 +1093,34 @@ LRProblem<T> lr_problem(const Contraction& c) {
   return p;
 }
 
-int lr_grid(int64_t items, int per_sm) {
+int lr_sms() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
     CUTQC_CUDA(cudaGetDevice(&dev));
     CUTQC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   }
-  return (int)std::min<int64_t>(items, (int64_t)sms * per_sm);
+  return sms;
 }
 
-// one launch of the low-rank kernel of term class KC (4 or 16)
+int lr_grid(int64_t items, int per_sm) { return (int)std::min<int64_t>(items, (int64_t)lr_sms() * per_sm); }
+
+// one launch of the low-rank kernel of term class KC (1, 4 or 16): as many
+// blocks as fit, at most one per item (each walks several items, the next
+// item's panel in flight; one block per item was measured slower in the
+// batch, 3.25 against 3.08 ms of GPU time)
 template <typename T, int KC>
 void lr_launch(const LRArgs<T>& a, cudaStream_t s) {
   if (a.n_items == 0) return;
-  k_lowrank<T, KC><<<lr_grid(a.n_items, KC == 4 ? 4 : (sizeof(T) == 8 ? 1 : 2)), 256, 0, s>>>(a);
+  constexpr size_t smem = lr_smem_bytes<T, KC>();
+  if constexpr (smem > 48 * 1024) {
+    static bool set = false;
+    if (!set) {
+      CUTQC_CUDA(cudaFuncSetAttribute(k_lowrank<T, KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      set = true;
+    }
+  }
+  k_lowrank<T, KC><<<lr_grid(a.n_items, lr_min_blocks<T, KC>()), 256, smem, s>>>(a);
   count_launch();
   check_launch("k_lowrank");
 }
@@ -908,27 +1131,42 @@ bool lowrank_eligible(const Contraction& c) {
   return c.batch == 1 && c.kmax <= 16 && c.fB >= 2 && c.fB <= 30 && c.vecB >= 4 && c.fA <= 40;
 }
 
-int64_t lowrank_items(const Contraction& c) {
-  const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
-  const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
-  return tiles_n * tiles_m;
-}
+static int64_t lr_tiles_n(const Contraction& c) { return c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1; }
+static int64_t lr_tiles_m(const Contraction& c) { return ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB; }
 
-// device tables of a batch: [problems][compaction jobs][row jobs][items][chunk flags][chunk maxima]
+int64_t lowrank_items(const Contraction& c) { return lr_tiles_n(c) * lr_tiles_m(c); }
+
+// term class of a low-rank contraction: 0 (one term), 1 (up to 4), 2 (up to 16)
+static int lr_class(const Contraction& c) { return c.kmax <= 1 ? 0 : (c.kmax <= 4 ? 1 : 2); }
+
+
+// device tables of a batch: [problems][compaction jobs][row jobs][items]
+// [chunk flags][chunk maxima]
 struct BatchLayout {
   size_t probs, cjobs, rjobs, items, part_nz, part_max, bytes;
-  int64_t n_items, nunits;
+  int64_t n_items, nunits, nblocks;
+  int64_t cls_items[3];
 };
 static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 static int64_t row_chunks(int64_t cols) { return std::max<int64_t>(1, cols / BATCH_CHUNK); }
 
+// the row-statistics geometry of one operand of a batch: warp form for rows
+// of at most 2048 values, else a block per row chunk
+static bool batch_warp_form(int64_t cols, int W) { return cols >= W && cols <= 2048; }
+static int64_t batch_blocks(int64_t rows, int64_t cols, int W) {
+  return batch_warp_form(cols, W) ? (row_stats_tasks(rows, cols, W) + 7) / 8 : rows * row_chunks(cols);
+}
+
 static BatchLayout batch_layout(const std::vector<Contraction>& cs) {
   BatchLayout L{};
   const size_t P = cs.size();
   for (const Contraction& c : cs) {
+    const int W = c.dtype == CUTQC_F64 ? 2 : 4;
     L.n_items += lowrank_items(c);
+    L.cls_items[lr_class(c)] += lowrank_items(c);
     L.nunits += (int64_t)c.rowsA * row_chunks(int64_t(1) << c.fA) + (int64_t)c.rowsB * row_chunks(int64_t(1) << c.fB);
+    L.nblocks += batch_blocks(c.rowsA, int64_t(1) << c.fA, W) + batch_blocks(c.rowsB, int64_t(1) << c.fB, W);
   }
   L.probs = 0;
   L.cjobs = up256(P * std::max(sizeof(LRProblem<float>), sizeof(LRProblem<double>)));
@@ -947,7 +1185,7 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
   const bool f64 = !cs.empty() && cs[0].dtype == CUTQC_F64;
   const size_t psz = f64 ? sizeof(LRProblem<double>) : sizeof(LRProblem<float>);
   host.assign(L.bytes, 0);
-  int64_t it = 0, unit0 = 0;
+  int64_t it = 0, unit0 = 0, block0 = 0;
   for (size_t i = 0; i < cs.size(); ++i) {
     const Contraction& c = cs[i];
     if ((c.dtype == CUTQC_F64) != f64) fail(CUTQC_ERR_ARG, "one dtype per low-rank batch");
@@ -975,23 +1213,24 @@ void lowrank_batch_tables(const std::vector<Contraction>& cs, std::vector<char>&
       rj.rows = side ? c.rowsB : c.rowsA;
       rj.cols = int64_t(1) << (side ? c.fB : c.fA);
       rj.first = unit0;
+      rj.bfirst = block0;
       rj.chunks = (int)row_chunks(rj.cols);
+      rj.warp = batch_warp_form(rj.cols, f64 ? 2 : 4) ? 1 : 0;
       rj.flags = const_cast<int32_t*>(side ? c.nzB : c.nzA);
       rj.rmax = const_cast<float*>(side ? c.rmaxB : c.rmaxA);
       unit0 += rj.rows * rj.chunks;
+      block0 += batch_blocks(rj.rows, rj.cols, f64 ? 2 : 4);
       std::memcpy(host.data() + L.rjobs + (2 * i + side) * sizeof(BatchRowJob), &rj, sizeof(BatchRowJob));
     }
   }
-  // items: the problems of at most 4 terms first (one launch of the small
-  // form), then the rest
-  for (int cls = 0; cls < 2; ++cls)
+  // items by term class (one launch each), per problem column tile by
+  // column tile
+  for (int cls = 0; cls < 3; ++cls)
     for (size_t i = 0; i < cs.size(); ++i) {
       const Contraction& c = cs[i];
-      if ((c.kmax <= 4) != (cls == 0)) continue;
-      const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
-      const int64_t tiles_m = ((int64_t(1) << c.fA) + LR_MB - 1) / LR_MB;
-      for (int64_t tm = 0; tm < tiles_m; ++tm)
-        for (int64_t tn = 0; tn < tiles_n; ++tn) {
+      if (lr_class(c) != cls) continue;
+      for (int64_t tn = 0; tn < lr_tiles_n(c); ++tn)
+        for (int64_t tm = 0; tm < lr_tiles_m(c); ++tm) {
           LRItem item{(int)i, (int)(tn * LR_NT), tm * LR_MB};
           std::memcpy(host.data() + L.items + (size_t)it * sizeof(LRItem), &item, sizeof(LRItem));
           ++it;
@@ -1010,65 +1249,55 @@ void launch_lowrank_batch(const void* dev_tables, const std::vector<Contraction>
   int32_t* pnz = reinterpret_cast<int32_t*>(const_cast<char*>(t) + L.part_nz);
   float* pmx = reinterpret_cast<float*>(const_cast<char*>(t) + L.part_max);
   const int np = (int)cs.size();
-  const unsigned g1 = (unsigned)std::min<int64_t>(L.nunits, 152 * 8);
+  const unsigned g1 = (unsigned)std::min<int64_t>(L.nblocks, 152 * 8);
   if (cs[0].dtype == CUTQC_F64)
-    k_batch_rowstats<double><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nunits, pnz, pmx);
+    k_batch_rowstats<double><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nblocks, pnz, pmx);
   else
-    k_batch_rowstats<float><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nunits, pnz, pmx);
+    k_batch_rowstats<float><<<g1, 256, 0, s>>>(rjobs, 2 * np, L.nblocks, pnz, pmx);
   count_launch();
   check_launch("k_batch_rowstats");
   k_batch_compact<<<(unsigned)np, 256, 0, s>>>(reinterpret_cast<const CompactJob*>(t + L.cjobs), rjobs, np, pnz, pmx);
   count_launch();
   check_launch("k_batch_compact");
-  int64_t n4 = 0;
-  for (const Contraction& c : cs)
-    if (c.kmax <= 4) n4 += lowrank_items(c);
-  if (cs[0].dtype == CUTQC_F64) {
-    LRArgs<double> a{};
-    a.probs = reinterpret_cast<const LRProblem<double>*>(t + L.probs);
-    a.items = reinterpret_cast<const LRItem*>(t + L.items);
-    a.n_items = n4;
-    lr_launch<double, 4>(a, s);
-    a.items += n4;
-    a.n_items = n_items - n4;
-    lr_launch<double, 16>(a, s);
-  } else {
-    LRArgs<float> a{};
-    a.probs = reinterpret_cast<const LRProblem<float>*>(t + L.probs);
-    a.items = reinterpret_cast<const LRItem*>(t + L.items);
-    a.n_items = n4;
-    lr_launch<float, 4>(a, s);
-    a.items += n4;
-    a.n_items = n_items - n4;
-    lr_launch<float, 16>(a, s);
-  }
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    LRArgs<T> a{};
+    a.probs = reinterpret_cast<const LRProblem<T>*>(t + L.probs);
+    const LRItem* items = reinterpret_cast<const LRItem*>(t + L.items);
+    for (int cls = 0; cls < 3; ++cls) {
+      a.items = items;
+      a.n_items = L.cls_items[cls];
+      if (cls == 0) lr_launch<T, 1>(a, s);
+      if (cls == 1) lr_launch<T, 4>(a, s);
+      if (cls == 2) lr_launch<T, 16>(a, s);
+      items += L.cls_items[cls];
+    }
+  };
+  if (cs[0].dtype == CUTQC_F64)
+    run(double{});
+  else
+    run(float{});
 }
 
 void launch_lowrank(const Contraction& c, cudaStream_t s) {
   if (!lowrank_eligible(c)) fail(CUTQC_ERR_UNSUPPORTED, "shape not supported by the low-rank contraction");
-  const int64_t items = lowrank_items(c);
-  const int64_t tiles_n = c.fB >= 10 ? (int64_t(1) << (c.fB - 10)) : 1;
   cudaEvent_t ev = nullptr;
   if (c.profile) prof_begin(s, &ev);
-  if (c.dtype == CUTQC_F64) {
-    LRArgs<double> a{};
-    a.one = lr_problem<double>(c);
-    a.n_items = items;
-    a.one_tiles_n = tiles_n;
-    if (c.kmax <= 4)
-      lr_launch<double, 4>(a, s);
-    else
-      lr_launch<double, 16>(a, s);
-  } else {
-    LRArgs<float> a{};
-    a.one = lr_problem<float>(c);
-    a.n_items = items;
-    a.one_tiles_n = tiles_n;
-    if (c.kmax <= 4)
-      lr_launch<float, 4>(a, s);
-    else
-      lr_launch<float, 16>(a, s);
-  }
+  auto run = [&](auto tag) {
+    using T = decltype(tag);
+    LRArgs<T> a{};
+    a.one = lr_problem<T>(c);
+    a.n_items = lowrank_items(c);
+    a.one_tiles_m = lr_tiles_m(c);
+    const int cls = lr_class(c);
+    if (cls == 0) lr_launch<T, 1>(a, s);
+    if (cls == 1) lr_launch<T, 4>(a, s);
+    if (cls == 2) lr_launch<T, 16>(a, s);
+  };
+  if (c.dtype == CUTQC_F64)
+    run(double{});
+  else
+    run(float{});
   if (c.profile) prof_end(s, ev);
 }
 
@@ -1076,19 +1305,35 @@ void launch_row_stats(const RowStatsJobs& jobs, int dtype, cudaStream_t s) {
   RowStatsJobs j = jobs;
   if (j.n < 2) j.rows[1] = 0;
   // tensors with fewer rows than SMs and long rows: a block per chunk of
-  // 2^16 columns, combined with atomics into outputs cleared first
+  // 2^16 columns, combined with atomics into outputs cleared first; rows of
+  // at most 2048 values (of vector-aligned tensors): 8 warp tasks per block;
+  // other rows: a block each
+  const int W = dtype == CUTQC_F64 ? 2 : 4;
   int64_t blocks = 0;
+  bool block_rows = false;
   for (int k = 0; k < 2; ++k) {
     j.chunks[k] = 1;
+    j.warp[k] = 0;
+    int64_t bk = 0;
     if (k < j.n && j.rows[k] < 152 && j.cols[k] > (int64_t(1) << 18)) {
       j.chunks[k] = (int)(j.cols[k] >> 16);
       CUTQC_CUDA(cudaMemsetAsync(j.flags[k], 0, (size_t)j.rows[k] * sizeof(int32_t), s));
       CUTQC_CUDA(cudaMemsetAsync(j.rmax[k], 0, (size_t)j.rows[k] * sizeof(float), s));
+      bk = j.rows[k] * j.chunks[k];
+      block_rows = true;
+    } else if (k < j.n && j.cols[k] >= W && j.cols[k] <= 2048 &&
+               reinterpret_cast<uintptr_t>(j.t[k]) % (4 * (size_t)W) == 0) {
+      j.warp[k] = 1;
+      bk = (row_stats_tasks(j.rows[k], j.cols[k], W) + 7) / 8;
+    } else {
+      bk = j.rows[k];
+      if (k < j.n && j.rows[k] > 0) block_rows = true;
     }
-    blocks += j.rows[k] * j.chunks[k];
+    if (k == 0) j.blocks0 = bk;
+    blocks += bk;
   }
   const int64_t cmax = std::max(j.cols[0], j.n > 1 ? j.cols[1] : int64_t(0));
-  const int threads = cmax >= 256 ? 256 : 32;
+  const int threads = (cmax >= 256 || j.warp[0] || j.warp[1] || !block_rows) ? 256 : 32;
   if (dtype == CUTQC_F64)
     k_row_stats<double><<<(unsigned)blocks, threads, 0, s>>>(j);
   else
@@ -1118,7 +1363,9 @@ void launch_compact(const Contraction& c, cudaStream_t s) {
   check_launch("k_compact");
 }
 
-bool cc_is_skinny(int fA, int fB) { return std::min(fA, fB) <= 3 && std::max(fA, fB) >= 9; }
+// a short side of at most 8 outputs: the matrix-vector form (its long side
+// needs at least one vector of 4 FP32 / 2 FP64 values per row)
+bool cc_is_skinny(int fA, int fB) { return std::min(fA, fB) <= 3 && std::max(fA, fB) >= 2; }
 
 void launch_cc_gemm(const Contraction& c, cudaStream_t s) {
   if (cc_is_skinny(c.fA, c.fB)) {
@@ -1130,6 +1377,8 @@ void launch_cc_gemm(const Contraction& c, cudaStream_t s) {
   }
   if (c.dtype == CUTQC_F64)
     launch_typed<double, 64, 64, 8>(c, s);
+  else if (std::min(c.fA, c.fB) <= 6)
+    launch_typed<float, 64, 64, 16>(c, s);   // a side of at most 64 outputs: a quarter of the idle tile
   else
     launch_typed<float, 128, 128, 8>(c, s);
 }
