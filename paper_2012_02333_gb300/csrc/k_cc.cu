@@ -956,17 +956,19 @@ __global__ __launch_bounds__(256, lr_min_blocks<T, KC>()) void k_lowrank(const L
     }
   };
   // the problem's parameters and its low-byte output offsets into shared memory
+  // (the kept-term count is loaded beside the table)
+  int kc;
   auto begin_problem = [&](int prob) {
     if (threadIdx.x == 0) sp = a.probs ? a.probs[prob] : a.one;
     __syncthreads();
     tab0[threadIdx.x] = __ldg(sp.depA + threadIdx.x);
+    kc = *sp.kcount;
     __syncthreads();
   };
   int prob, n0;
   int64_t m0;
   item_of(it0, prob, m0, n0);
   begin_problem(prob);
-  int kc = *sp.kcount;
   lr_fetch<T, KC>(sp, kc, m0, As[0]);
   T b[KC][4];
   uint64_t gB;
@@ -991,7 +993,6 @@ __global__ __launch_bounds__(256, lr_min_blocks<T, KC>()) void k_lowrank(const L
       if (!same) {
         __syncthreads();   // every thread is done with the old problem's parameters
         begin_problem(nprob);
-        kc = *sp.kcount;
         lr_fetch<T, KC>(sp, kc, nm0, As[buf ^ 1]);
       }
       if (!same || nn0 != n0) lr_load_b<T, KC>(sp, kc, nn0, b, gB);
