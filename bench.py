@@ -693,28 +693,32 @@ def run_other(args):
         # in complex FP64, attributed (Eq. 3, Eq. 2) into the FP32 tensors
         cc = circuits.supremacy_4x6(0)
         outs = [torch.empty((4 ** s.k_in) * (4 ** s.k_out) * (2 ** s.n_eff), device=dev) for s in cc.subs]
-        n_gate_passes = 0
-        state_bytes = 0
-        pass_bytes = 0
+        # FP64 work as applied: the init variants (4^k_in states of 2^d
+        # amplitudes) go through every gate (dense complex matrices: 14 flops
+        # per amplitude for a 1-qubit gate, 30 for a 2-qubit one), then each
+        # of the 3^k_out measurement bases rotates its X- and Y-measured
+        # qubits (14 flops per amplitude each); the attribution's few flops
+        # per output are not counted
+        flops = 0
         for sub in cc.subs:
-            nvar = (4 ** sub.k_in) * (3 ** sub.k_out)
-            st = nvar * (2 ** sub.d) * 16
-            state_bytes += st
-            n_gate_passes += len(sub.gates)
-            pass_bytes += 2 * st * len(sub.gates)
+            nv, dim = 4 ** sub.k_in, 2 ** sub.d
+            per = sum(30 if len(g.qubits) == 2 else 14 for g in sub.gates)
+            rot = sub.k_out * 2 * 3 ** max(sub.k_out - 1, 0)
+            flops += nv * dim * (per + 14 * rot)
 
         def sim_step():
             for sub, o in zip(cc.subs, outs):
                 cutqc.cutqc_simulate_subcircuit(sub, torch.float32, dev, out=o)
         ms = timed(sim_step)
         units, unit, dtype = sum(o.numel() for o in outs), "tensor entries/s", "complex f64 state, f32 tensors"
-        pk, pk_src = peaks()
-        extra = {"gates": n_gate_passes, "state_bytes_all_variants": state_bytes,
-                 "roofline": {"bound": "hbm", "achieved": pass_bytes / (ms / 1e3) / 1e9, "peak": pk["hbm_gbs"],
-                              "unit": "GB/s", "frac": pass_bytes / (ms / 1e3) / 1e9 / pk["hbm_gbs"],
-                              "traffic": None, "algorithmic_bytes": pass_bytes, "peak_file": pk_src,
-                              "note": "the states (57 and 25 MB) stay in L2 between gate passes"},
-                 "gate_pass_bytes": "each gate reads and writes the state of every variant (16 B per amplitude)"}
+        extra = {"gates": sum(len(sub.gates) for sub in cc.subs),
+                 "roofline": {"bound": "alu", "achieved": flops / (ms / 1e3) / 1e12,
+                              "peak": LIBRARY_PEAKS["fp64_tflops"], "unit": "TFLOP/s",
+                              "frac": flops / (ms / 1e3) / 1e12 / LIBRARY_PEAKS["fp64_tflops"],
+                              "traffic": None, "algorithmic_flops": flops,
+                              "peak_file": "measured FP64 (torch.matmul, LIBRARY_PEAKS)",
+                              "note": "complex FP64 arithmetic of the dense gate matrices as applied; the "
+                                      "states (2 and 0.5 MB) stay in L2"}}
         cfg = {"workload": "sim_supremacy4x6_fp64_state", "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff]
                                                                           for s in cc.subs],
                "step": "simulate every variant of both subcircuits and attribute (input preparation; each call "

@@ -10,8 +10,9 @@
 // result is the tensor T[a][b][x] of the ABI.
 //
 // State layout: [variant][2^d] complex doubles, local qubit 0 = most
-// significant bit of the index.  One kernel launch per gate over all
-// variants of a chunk.  Attribution accumulates in FP64, entries below
+// significant bit of the index.  One kernel launch per run of consecutive
+// gates over at most 10 index bits (k_gates_tile), over all variants of a
+// chunk.  Attribution accumulates in FP64, entries below
 // 2^-40 in magnitude are set to 0, then the tensor is cast to its dtype.
 #include <cuda_runtime.h>
 
@@ -26,6 +27,7 @@ namespace {
 
 constexpr int kMaxSlots = 12;
 constexpr int kMaxMeasSim = 8;   // measured cut qubits per subcircuit in the simulator
+constexpr int kMaxRotSim = 4;    // ... whose basis changes the attribution applies itself
 constexpr int kMaxOut = 40;
 
 struct SimArgs {
@@ -83,35 +85,82 @@ __global__ void k_gate1(double2* __restrict__ psi, int d, int nb, int bit, doubl
   }
 }
 
-struct Mat4 {
-  double2 m[16];
+// Gate fusion: a run of consecutive gates that together touch at most
+// kTileBits of the state's index bits is applied in one pass.  The tile bits
+// are those bits plus the lowest other ones (so a tile's first 8 amplitudes
+// are contiguous in memory); a block owns one tile (one variant, one value
+// of the other bits), loads its 2^L amplitudes into shared memory, applies
+// every gate of the run there (one barrier between gates) and writes them
+// back.  The arithmetic is the per-gate kernels' (complex FP64), in the same
+// order per amplitude, so the states are the same as gate by gate.
+constexpr int kTileBits = 10;
+
+struct FusedGate {
+  int nq;        // 1 or 2
+  int p0, p1;    // positions among the tile bits (p0: the matrix's more significant qubit)
+  int mat;       // first entry of its matrix in the matrix table (4 or 16 entries)
 };
 
-// 4x4 gate on (q0, q1); matrix index = 2 * bit(q0) + bit(q1)
-__global__ void k_gate2(double2* __restrict__ psi, int d, int nb, int b0, int b1, Mat4 U) {
-  const int64_t quarter = int64_t(1) << (d - 2);
-  const int64_t tot = quarter * nb;
-  const int lo_b = b0 < b1 ? b0 : b1, hi_b = b0 < b1 ? b1 : b0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t v = t >> (d - 2);
-    int64_t i = t & (quarter - 1);
-    // insert zero bits at lo_b then hi_b
-    int64_t m = (int64_t(1) << lo_b) - 1;
-    i = ((i & ~m) << 1) | (i & m);
-    m = (int64_t(1) << hi_b) - 1;
-    i = ((i & ~m) << 1) | (i & m);
-    double2* p = psi + (v << d);
-    int64_t idx[4];
-    for (int k = 0; k < 4; ++k)
-      idx[k] = i | ((int64_t)((k >> 1) & 1) << b0) | ((int64_t)(k & 1) << b1);
-    double2 a[4];
-    for (int k = 0; k < 4; ++k) a[k] = p[idx[k]];
-    for (int r = 0; r < 4; ++r) {
-      double2 acc = make_double2(0.0, 0.0);
-      for (int k = 0; k < 4; ++k) acc = cadd(acc, cmul(U.m[4 * r + k], a[k]));
-      p[idx[r]] = acc;
+struct TileBits {
+  int L;
+  int tb[kTileBits];   // index bit of tile position k, ascending
+  int64_t tmask;       // the tile bits as a mask
+};
+
+__global__ __launch_bounds__(256) void k_gates_tile(double2* __restrict__ psi, int d, TileBits t,
+                                                    const FusedGate* __restrict__ gates, int ng,
+                                                    const double2* __restrict__ mats) {
+  __shared__ double2 tile[1 << kTileBits];
+  const int L = t.L, n = 1 << L, tid = threadIdx.x;
+  const int64_t v = (int64_t)blockIdx.x >> (d - L);
+  const int64_t r = (int64_t)blockIdx.x & ((int64_t(1) << (d - L)) - 1);
+  // the other bits of this tile's amplitudes: r deposited into the non-tile bits
+  int64_t base = 0;
+  for (int b = 0, rb = 0; b < d; ++b)
+    if (!((t.tmask >> b) & 1)) base |= ((r >> rb++) & 1) << b;
+  double2* p = psi + (v << d);
+  auto at = [&](int j) {
+    int64_t y = base;
+#pragma unroll
+    for (int k = 0; k < kTileBits; ++k)
+      if (k < L) y |= (int64_t)((j >> k) & 1) << t.tb[k];
+    return y;
+  };
+  for (int j = tid; j < n; j += 256) tile[j] = p[at(j)];
+  __syncthreads();
+  for (int gi = 0; gi < ng; ++gi) {
+    const FusedGate G = gates[gi];
+    if (G.nq == 1) {
+      const double2 u00 = mats[G.mat], u01 = mats[G.mat + 1], u10 = mats[G.mat + 2], u11 = mats[G.mat + 3];
+      const int lo = (1 << G.p0) - 1;
+      for (int q = tid; q < (n >> 1); q += 256) {
+        const int i0 = ((q & ~lo) << 1) | (q & lo), i1 = i0 | (1 << G.p0);
+        const double2 a0 = tile[i0], a1 = tile[i1];
+        tile[i0] = cadd(cmul(u00, a0), cmul(u01, a1));
+        tile[i1] = cadd(cmul(u10, a0), cmul(u11, a1));
+      }
+    } else {
+      const int lo_b = G.p0 < G.p1 ? G.p0 : G.p1, hi_b = G.p0 < G.p1 ? G.p1 : G.p0;
+      for (int q = tid; q < (n >> 2); q += 256) {
+        int i = q;
+        int m = (1 << lo_b) - 1;
+        i = ((i & ~m) << 1) | (i & m);
+        m = (1 << hi_b) - 1;
+        i = ((i & ~m) << 1) | (i & m);
+        int idx[4];
+        for (int k = 0; k < 4; ++k) idx[k] = i | (((k >> 1) & 1) << G.p0) | ((k & 1) << G.p1);
+        double2 a[4];
+        for (int k = 0; k < 4; ++k) a[k] = tile[idx[k]];
+        for (int rr = 0; rr < 4; ++rr) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int k = 0; k < 4; ++k) acc = cadd(acc, cmul(mats[G.mat + 4 * rr + k], a[k]));
+          tile[idx[rr]] = acc;
+        }
+      }
     }
+    __syncthreads();
   }
+  for (int j = tid; j < n; j += 256) p[at(j)] = tile[j];
 }
 
 // Eq. 3 for one combination of measurement bases `mb` (base-3 digits Z=0,
@@ -119,6 +168,12 @@ __global__ void k_gate2(double2* __restrict__ psi, int d, int nb, int b0, int b1
 // s and output x, and every Pauli row b that this basis combination serves
 // (slots measured in Z serve b = I and b = Z, X serves X, Y serves Y),
 // P[s][b][x] = sum_m (prod_j sign(b_j, m_j)) p_s(x, m).
+// ROT: the state is the one before measurement and the kernel applies the
+// basis changes itself (H for X, S^dagger then H for Y on each measured
+// qubit) to the 2^k_out amplitudes of each output it holds, with the
+// arithmetic of the gate kernels (so the result is the same as rotating a
+// copy of the state first); for at most 4 measured qubits.
+template <bool ROT>
 __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, int nb, int mb,
                             double* __restrict__ P) {
   const int64_t nx = int64_t(1) << a.n_eff;
@@ -141,12 +196,39 @@ __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, 
       if ((x >> (a.n_eff - 1 - i)) & 1) ybase |= int64_t(1) << a.out_bit[i];
     const double2* p = phi + ((int64_t)sl << a.d);
     double pr[1 << kMaxMeasSim];
-    for (int m = 0; m < nm; ++m) {
-      int64_t y = ybase;
-      for (int j = 0; j < a.k_out; ++j)
-        if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
-      const double2 v = p[y];
-      pr[m] = v.x * v.x + v.y * v.y;
+    if constexpr (ROT) {
+      constexpr int NM = 1 << kMaxRotSim;
+      double2 amp[NM];
+      for (int m = 0; m < nm; ++m) {
+        int64_t y = ybase;
+        for (int j = 0; j < a.k_out; ++j)
+          if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
+        amp[m] = p[y];
+      }
+      const double r = 0.70710678118654752440;
+      for (int j = 0; j < a.k_out; ++j) {
+        if (basis[j] == 0) continue;
+        // X: (1/sqrt2) [[1, 1], [1, -1]]; Y: (1/sqrt2) [[1, -i], [1, i]]
+        const double2 u00 = make_double2(r, 0.0), u10 = make_double2(r, 0.0);
+        const double2 u01 = basis[j] == 1 ? make_double2(r, 0.0) : make_double2(0.0, -r);
+        const double2 u11 = basis[j] == 1 ? make_double2(-r, 0.0) : make_double2(0.0, r);
+        const int bit = 1 << (a.k_out - 1 - j);
+        for (int m = 0; m < nm; ++m) {
+          if (m & bit) continue;
+          const double2 a0 = amp[m], a1 = amp[m | bit];
+          amp[m] = cadd(cmul(u00, a0), cmul(u01, a1));
+          amp[m | bit] = cadd(cmul(u10, a0), cmul(u11, a1));
+        }
+      }
+      for (int m = 0; m < nm; ++m) pr[m] = amp[m].x * amp[m].x + amp[m].y * amp[m].y;
+    } else {
+      for (int m = 0; m < nm; ++m) {
+        int64_t y = ybase;
+        for (int j = 0; j < a.k_out; ++j)
+          if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
+        const double2 v = p[y];
+        pr[m] = v.x * v.x + v.y * v.y;
+      }
     }
     // enumerate the b rows served: for Z-basis slots choose I or Z
     for (int sub = 0; sub < nm; ++sub) {
@@ -276,7 +358,7 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
   double* P = nullptr;
   CUTQC_CUDA(cudaStreamSynchronize(s));
   CUTQC_CUDA(cudaMalloc(&psi, (size_t)dim * nb * sizeof(double2)));
-  CUTQC_CUDA(cudaMalloc(&phi, (size_t)dim * nb * sizeof(double2)));
+  if (sp.k_out > kMaxRotSim) CUTQC_CUDA(cudaMalloc(&phi, (size_t)dim * nb * sizeof(double2)));
   CUTQC_CUDA(cudaMalloc(&P, (size_t)total * sizeof(double)));
   try {
     std::vector<std::pair<std::vector<double2>, int>> mats;
@@ -286,26 +368,84 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
       gate_matrix(g, m.data(), nq);
       mats.emplace_back(m, nq);
     }
+    // runs of consecutive gates over at most L index bits, each run's tile
+    // bits, its gates by tile position and the matrix table
+    const int L = std::min(sp.d, kTileBits);
+    std::vector<TileBits> runs;
+    std::vector<std::pair<int, int>> run_gates;   // [first, count) into fg
+    std::vector<FusedGate> fg;
+    std::vector<double2> mt;
+    {
+      size_t gi = 0;
+      while (gi < sp.gates.size()) {
+        int64_t used = 0;
+        size_t gj = gi;
+        for (; gj < sp.gates.size(); ++gj) {
+          int64_t m = int64_t(1) << (sp.d - 1 - sp.gates[gj].q0);
+          if (mats[gj].second == 2) m |= int64_t(1) << (sp.d - 1 - sp.gates[gj].q1);
+          if (__builtin_popcountll(used | m) > L) break;
+          used |= m;
+        }
+        for (int b = 0; b < sp.d && __builtin_popcountll(used) < L; ++b) used |= int64_t(1) << b;
+        TileBits t{};
+        t.L = L;
+        t.tmask = used;
+        int pos[64];
+        for (int b = 0, k = 0; b < sp.d; ++b)
+          if ((used >> b) & 1) {
+            pos[b] = k;
+            t.tb[k++] = b;
+          }
+        runs.push_back(t);
+        run_gates.emplace_back((int)fg.size(), (int)(gj - gi));
+        for (size_t g = gi; g < gj; ++g) {
+          FusedGate f{};
+          f.nq = mats[g].second;
+          f.p0 = pos[sp.d - 1 - sp.gates[g].q0];
+          f.p1 = f.nq == 2 ? pos[sp.d - 1 - sp.gates[g].q1] : 0;
+          f.mat = (int)mt.size();
+          mt.insert(mt.end(), mats[g].first.begin(), mats[g].first.begin() + (f.nq == 2 ? 16 : 4));
+          fg.push_back(f);
+        }
+        gi = gj;
+      }
+    }
+    FusedGate* dg = nullptr;
+    double2* dm = nullptr;
+    if (!fg.empty()) {
+      CUTQC_CUDA(cudaMalloc(&dg, fg.size() * sizeof(FusedGate)));
+      CUTQC_CUDA(cudaMalloc(&dm, mt.size() * sizeof(double2)));
+      CUTQC_CUDA(cudaMemcpy(dg, fg.data(), fg.size() * sizeof(FusedGate), cudaMemcpyHostToDevice));
+      CUTQC_CUDA(cudaMemcpy(dm, mt.data(), mt.size() * sizeof(double2), cudaMemcpyHostToDevice));
+    }
+    struct FreeTables {
+      FusedGate* g;
+      double2* m;
+      ~FreeTables() {
+        if (g) cudaFree(g);
+        if (m) cudaFree(m);
+      }
+    } free_tables{dg, dm};
     const double2 hr = make_double2(0.70710678118654752440, 0.0);
     for (int s0 = 0; s0 < nvar; s0 += nb) {
       const int n = std::min(nb, nvar - s0);
       k_sim_init<<<grid_for(dim * n), 256, 0, s>>>(psi, a, s0, n);
       count_launch();
       check_launch("k_sim_init");
-      for (size_t gi = 0; gi < sp.gates.size(); ++gi) {
-        const cutqc_gate& g = sp.gates[gi];
-        const double2* m = mats[gi].first.data();
-        if (mats[gi].second == 1) {
-          k_gate1<<<grid_for(dim / 2 * n), 256, 0, s>>>(psi, sp.d, n, sp.d - 1 - g.q0, m[0], m[1], m[2], m[3]);
-        } else {
-          Mat4 U;
-          for (int k = 0; k < 16; ++k) U.m[k] = m[k];
-          k_gate2<<<grid_for(dim / 4 * n), 256, 0, s>>>(psi, sp.d, n, sp.d - 1 - g.q0, sp.d - 1 - g.q1, U);
-        }
+      for (size_t r = 0; r < runs.size(); ++r) {
+        const unsigned blocks = (unsigned)(((int64_t)n) << (sp.d - L));
+        k_gates_tile<<<blocks, 256, 0, s>>>(psi, sp.d, runs[r], dg + run_gates[r].first, run_gates[r].second, dm);
         count_launch();
-        check_launch("k_gate");
+        check_launch("k_gates_tile");
       }
       for (int mb = 0; mb < nmb; ++mb) {
+        if (sp.k_out <= kMaxRotSim) {
+          // the basis changes inside the attribution: no copy of the state
+          k_attr_meas<true><<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(psi, a, s0, n, mb, P);
+          count_launch();
+          check_launch("k_attr_meas");
+          continue;
+        }
         CUTQC_CUDA(cudaMemcpyAsync(phi, psi, (size_t)dim * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         int t = mb;
         std::vector<int> bases(sp.k_out);
@@ -324,7 +464,7 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
             count_launch();
           }
         }
-        k_attr_meas<<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(phi, a, s0, n, mb, P);
+        k_attr_meas<false><<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(phi, a, s0, n, mb, P);
         count_launch();
         check_launch("k_attr_meas");
       }
