@@ -1824,6 +1824,7 @@ void cutqc_release(void) {
   }
   g_dev.clear();
   cudaSetDevice(cur);
+  release_sim_scratch();
 }
 
 int64_t cutqc_launch_count(void) { return g_launches.load(); }

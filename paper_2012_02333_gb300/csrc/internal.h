@@ -293,5 +293,6 @@ struct SimPlan {
   std::vector<cutqc_gate> gates;
 };
 void run_subcircuit_sim(const SimPlan& p, int dtype, void* tensor, cudaStream_t s);
+void release_sim_scratch();   // frees the simulator's cached scratch on every device
 
 }  // namespace cutqc

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -91,12 +92,27 @@ __global__ void k_gate1(double2* __restrict__ psi, int d, int nb, int bit, doubl
 // are contiguous in memory); a block owns one tile (one variant, one value
 // of the other bits), loads its 2^L amplitudes into shared memory, applies
 // every gate of the run there (one barrier between gates) and writes them
-// back.  The arithmetic is the per-gate kernels' (complex FP64), in the same
-// order per amplitude, so the states are the same as gate by gate.
+// back.
+//
+// Inside a pass the amplitudes are double-float numbers (an unevaluated sum
+// hi + lo of two FP32 values, about 48 significant bits) and the gates are
+// evaluated with error-free transformations on the FP32 pipes: Knuth's
+// TwoSum for additions, the FMA form of Dekker's product for
+// multiplications (the pair renormalised with Dekker's fast two-sum after
+// each operation).  FP64 runs at 1/64 of the FP32 rate on this part, and
+// the gates were FP64-bound (53 % of the FP64 peak in the fused kernel).
+// Between passes the state is stored in FP64.  Each operation's relative
+// error is about 2^-48 (against 2^-53 in FP64), so amplitudes of a
+// 100-gate circuit carry relative errors of order 1e-13 and the attributed
+// tensor entries (sums of probabilities of magnitude at most 2) absolute
+// errors of order 1e-13: entries that vanish exactly stay far below the
+// 2^-40 (9.1e-13) zero threshold only if the accumulation stays below it,
+// which the simulator tests check against the FP64 oracle at 1e-12.
 constexpr int kTileBits = 10;
 
 struct FusedGate {
   int nq;        // 1 or 2
+  int diag;      // the matrix is diagonal (entries 0, 3 or 0, 5, 10, 15 of the table)
   int p0, p1;    // positions among the tile bits (p0: the matrix's more significant qubit)
   int mat;       // first entry of its matrix in the matrix table (4 or 16 entries)
 };
@@ -107,10 +123,58 @@ struct TileBits {
   int64_t tmask;       // the tile bits as a mask
 };
 
-__global__ __launch_bounds__(256) void k_gates_tile(double2* __restrict__ psi, int d, TileBits t,
+struct DF {
+  float hi, lo;
+};
+// (the _rn intrinsics are never contracted into an FMA, which would break
+// the error-free transformations)
+// Dekker's fast two-sum (|a| >= |b| or a == 0)
+__device__ __forceinline__ DF df_fast(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// Knuth's TwoSum
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = df_two_sum(a.hi, b.hi);
+  const DF t = df_two_sum(a.lo, b.lo);
+  s = df_fast(s.hi, __fadd_rn(s.lo, t.hi));
+  return df_fast(s.hi, __fadd_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);   // exact rounding error of the product
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast(p, e);
+}
+__device__ __forceinline__ DF df_of(double x) {
+  const float hi = (float)x;
+  return {hi, (float)(x - (double)hi)};
+}
+__device__ __forceinline__ double df_val(DF a) { return (double)a.hi + (double)a.lo; }
+
+struct CDF {
+  DF re, im;
+};
+__device__ __forceinline__ CDF cdf_of(double2 z) { return {df_of(z.x), df_of(z.y)}; }
+__device__ __forceinline__ double2 cdf_val(CDF z) { return make_double2(df_val(z.re), df_val(z.im)); }
+__device__ __forceinline__ CDF cdf_mul(CDF u, CDF a) {
+  return {df_add(df_mul(u.re, a.re), df_neg(df_mul(u.im, a.im))), df_add(df_mul(u.re, a.im), df_mul(u.im, a.re))};
+}
+__device__ __forceinline__ CDF cdf_add(CDF a, CDF b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ float4 cdf_pack(CDF z) { return make_float4(z.re.hi, z.re.lo, z.im.hi, z.im.lo); }
+__device__ __forceinline__ CDF cdf_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+__global__ __launch_bounds__(256, 3) void k_gates_tile(double2* __restrict__ psi, int d, TileBits t,
                                                     const FusedGate* __restrict__ gates, int ng,
-                                                    const double2* __restrict__ mats) {
-  __shared__ double2 tile[1 << kTileBits];
+                                                    const float4* __restrict__ mats) {
+  __shared__ float4 tile[1 << kTileBits];
   const int L = t.L, n = 1 << L, tid = threadIdx.x;
   const int64_t v = (int64_t)blockIdx.x >> (d - L);
   const int64_t r = (int64_t)blockIdx.x & ((int64_t(1) << (d - L)) - 1);
@@ -126,18 +190,28 @@ __global__ __launch_bounds__(256) void k_gates_tile(double2* __restrict__ psi, i
       if (k < L) y |= (int64_t)((j >> k) & 1) << t.tb[k];
     return y;
   };
-  for (int j = tid; j < n; j += 256) tile[j] = p[at(j)];
+  for (int j = tid; j < n; j += 256) tile[j] = cdf_pack(cdf_of(p[at(j)]));
   __syncthreads();
   for (int gi = 0; gi < ng; ++gi) {
     const FusedGate G = gates[gi];
     if (G.nq == 1) {
-      const double2 u00 = mats[G.mat], u01 = mats[G.mat + 1], u10 = mats[G.mat + 2], u11 = mats[G.mat + 3];
       const int lo = (1 << G.p0) - 1;
-      for (int q = tid; q < (n >> 1); q += 256) {
-        const int i0 = ((q & ~lo) << 1) | (q & lo), i1 = i0 | (1 << G.p0);
-        const double2 a0 = tile[i0], a1 = tile[i1];
-        tile[i0] = cadd(cmul(u00, a0), cmul(u01, a1));
-        tile[i1] = cadd(cmul(u10, a0), cmul(u11, a1));
+      if (G.diag) {
+        const CDF u00 = cdf_unpack(mats[G.mat]), u11 = cdf_unpack(mats[G.mat + 3]);
+        for (int q = tid; q < (n >> 1); q += 256) {
+          const int i0 = ((q & ~lo) << 1) | (q & lo), i1 = i0 | (1 << G.p0);
+          tile[i0] = cdf_pack(cdf_mul(u00, cdf_unpack(tile[i0])));
+          tile[i1] = cdf_pack(cdf_mul(u11, cdf_unpack(tile[i1])));
+        }
+      } else {
+        const CDF u00 = cdf_unpack(mats[G.mat]), u01 = cdf_unpack(mats[G.mat + 1]);
+        const CDF u10 = cdf_unpack(mats[G.mat + 2]), u11 = cdf_unpack(mats[G.mat + 3]);
+        for (int q = tid; q < (n >> 1); q += 256) {
+          const int i0 = ((q & ~lo) << 1) | (q & lo), i1 = i0 | (1 << G.p0);
+          const CDF a0 = cdf_unpack(tile[i0]), a1 = cdf_unpack(tile[i1]);
+          tile[i0] = cdf_pack(cdf_add(cdf_mul(u00, a0), cdf_mul(u01, a1)));
+          tile[i1] = cdf_pack(cdf_add(cdf_mul(u10, a0), cdf_mul(u11, a1)));
+        }
       }
     } else {
       const int lo_b = G.p0 < G.p1 ? G.p0 : G.p1, hi_b = G.p0 < G.p1 ? G.p1 : G.p0;
@@ -148,32 +222,33 @@ __global__ __launch_bounds__(256) void k_gates_tile(double2* __restrict__ psi, i
         m = (1 << hi_b) - 1;
         i = ((i & ~m) << 1) | (i & m);
         int idx[4];
+#pragma unroll
         for (int k = 0; k < 4; ++k) idx[k] = i | (((k >> 1) & 1) << G.p0) | ((k & 1) << G.p1);
-        double2 a[4];
-        for (int k = 0; k < 4; ++k) a[k] = tile[idx[k]];
-        for (int rr = 0; rr < 4; ++rr) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int k = 0; k < 4; ++k) acc = cadd(acc, cmul(mats[G.mat + 4 * rr + k], a[k]));
-          tile[idx[rr]] = acc;
+        if (G.diag) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            tile[idx[k]] = cdf_pack(cdf_mul(cdf_unpack(mats[G.mat + 5 * k]), cdf_unpack(tile[idx[k]])));
+        } else {
+          CDF a[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) a[k] = cdf_unpack(tile[idx[k]]);
+#pragma unroll 1
+          for (int rr = 0; rr < 4; ++rr) {
+            CDF acc = cdf_mul(cdf_unpack(mats[G.mat + 4 * rr]), a[0]);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) acc = cdf_add(acc, cdf_mul(cdf_unpack(mats[G.mat + 4 * rr + k]), a[k]));
+            tile[idx[rr]] = cdf_pack(acc);
+          }
         }
       }
     }
     __syncthreads();
   }
-  for (int j = tid; j < n; j += 256) p[at(j)] = tile[j];
+  for (int j = tid; j < n; j += 256) p[at(j)] = cdf_val(cdf_unpack(tile[j]));
 }
 
-// Eq. 3 for one combination of measurement bases `mb` (base-3 digits Z=0,
-// X=1, Y=2 per measurement slot, slot 0 most significant): for every variant
-// s and output x, and every Pauli row b that this basis combination serves
-// (slots measured in Z serve b = I and b = Z, X serves X, Y serves Y),
-// P[s][b][x] = sum_m (prod_j sign(b_j, m_j)) p_s(x, m).
-// ROT: the state is the one before measurement and the kernel applies the
-// basis changes itself (H for X, S^dagger then H for Y on each measured
-// qubit) to the 2^k_out amplitudes of each output it holds, with the
-// arithmetic of the gate kernels (so the result is the same as rotating a
-// copy of the state first); for at most 4 measured qubits.
-template <bool ROT>
+// Generic form (any number of measured qubits up to 8): phi is a copy of
+// the state already rotated into the measurement bases of combination mb.
 __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, int nb, int mb,
                             double* __restrict__ P) {
   const int64_t nx = int64_t(1) << a.n_eff;
@@ -196,39 +271,12 @@ __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, 
       if ((x >> (a.n_eff - 1 - i)) & 1) ybase |= int64_t(1) << a.out_bit[i];
     const double2* p = phi + ((int64_t)sl << a.d);
     double pr[1 << kMaxMeasSim];
-    if constexpr (ROT) {
-      constexpr int NM = 1 << kMaxRotSim;
-      double2 amp[NM];
-      for (int m = 0; m < nm; ++m) {
-        int64_t y = ybase;
-        for (int j = 0; j < a.k_out; ++j)
-          if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
-        amp[m] = p[y];
-      }
-      const double r = 0.70710678118654752440;
-      for (int j = 0; j < a.k_out; ++j) {
-        if (basis[j] == 0) continue;
-        // X: (1/sqrt2) [[1, 1], [1, -1]]; Y: (1/sqrt2) [[1, -i], [1, i]]
-        const double2 u00 = make_double2(r, 0.0), u10 = make_double2(r, 0.0);
-        const double2 u01 = basis[j] == 1 ? make_double2(r, 0.0) : make_double2(0.0, -r);
-        const double2 u11 = basis[j] == 1 ? make_double2(-r, 0.0) : make_double2(0.0, r);
-        const int bit = 1 << (a.k_out - 1 - j);
-        for (int m = 0; m < nm; ++m) {
-          if (m & bit) continue;
-          const double2 a0 = amp[m], a1 = amp[m | bit];
-          amp[m] = cadd(cmul(u00, a0), cmul(u01, a1));
-          amp[m | bit] = cadd(cmul(u10, a0), cmul(u11, a1));
-        }
-      }
-      for (int m = 0; m < nm; ++m) pr[m] = amp[m].x * amp[m].x + amp[m].y * amp[m].y;
-    } else {
-      for (int m = 0; m < nm; ++m) {
-        int64_t y = ybase;
-        for (int j = 0; j < a.k_out; ++j)
-          if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
-        const double2 v = p[y];
-        pr[m] = v.x * v.x + v.y * v.y;
-      }
+    for (int m = 0; m < nm; ++m) {
+      int64_t y = ybase;
+      for (int j = 0; j < a.k_out; ++j)
+        if ((m >> (a.k_out - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
+      const double2 v = p[y];
+      pr[m] = v.x * v.x + v.y * v.y;
     }
     // enumerate the b rows served: for Z-basis slots choose I or Z
     for (int sub = 0; sub < nm; ++sub) {
@@ -244,6 +292,87 @@ __global__ void k_attr_meas(const double2* __restrict__ phi, SimArgs a, int s0, 
       }
       double val = 0.0;
       for (int m = 0; m < nm; ++m) val += (__popc(m & sign_mask) & 1) ? -pr[m] : pr[m];
+      P[((int64_t)(s0 + sl) * rows_b + b) * nx + x] = val;
+    }
+  }
+}
+
+// KO <= 4 measured qubits: the state is the one before measurement and the
+// kernel applies the basis changes itself (H for X, S^dagger then H for Y)
+// to the 2^KO amplitudes of each output it holds, with the arithmetic of the
+// gate kernels, for every basis combination mb = blockIdx.y in one launch
+// (no rotated copy of the state per combination); the sizes are compile-time
+// so the amplitudes and probabilities stay in registers.  Same results as
+// the generic form on a rotated copy.
+template <int KO>
+__global__ void k_attr_meas_rot(const double2* __restrict__ psi, SimArgs a, int s0, int nb,
+                                double* __restrict__ P) {
+  constexpr int NM = 1 << KO;
+  const int mb = (int)blockIdx.y;
+  const int64_t nx = int64_t(1) << a.n_eff;
+  const int64_t tot = nx * nb;
+  constexpr int64_t rows_b = int64_t(1) << (2 * KO);
+  int basis[KO > 0 ? KO : 1];
+  int zmask = 0;
+#pragma unroll
+  for (int j = 0; j < KO; ++j) {
+    int t = mb;
+    for (int r = 0; r < KO - 1 - j; ++r) t /= 3;
+    basis[j] = t % 3;
+    if (basis[j] == 0) zmask |= 1 << j;
+  }
+  const double r = 0.70710678118654752440;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < tot; t += (int64_t)gridDim.x * blockDim.x) {
+    const int sl = (int)(t >> a.n_eff);
+    const int64_t x = t & (nx - 1);
+    int64_t ybase = 0;
+    for (int i = 0; i < a.n_eff; ++i)
+      if ((x >> (a.n_eff - 1 - i)) & 1) ybase |= int64_t(1) << a.out_bit[i];
+    const double2* p = psi + ((int64_t)sl << a.d);
+    double2 amp[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      int64_t y = ybase;
+#pragma unroll
+      for (int j = 0; j < KO; ++j)
+        if ((m >> (KO - 1 - j)) & 1) y |= int64_t(1) << a.meas_bit[j];
+      amp[m] = p[y];
+    }
+#pragma unroll
+    for (int j = 0; j < KO; ++j) {
+      if (basis[j] == 0) continue;
+      // X: (1/sqrt2) [[1, 1], [1, -1]]; Y: (1/sqrt2) [[1, -i], [1, i]]
+      const double2 u00 = make_double2(r, 0.0), u10 = make_double2(r, 0.0);
+      const double2 u01 = basis[j] == 1 ? make_double2(r, 0.0) : make_double2(0.0, -r);
+      const double2 u11 = basis[j] == 1 ? make_double2(-r, 0.0) : make_double2(0.0, r);
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const int bit = 1 << (KO - 1 - j);
+        if (m & bit) continue;
+        const double2 a0 = amp[m], a1 = amp[m | bit];
+        amp[m] = cadd(cmul(u00, a0), cmul(u01, a1));
+        amp[m | bit] = cadd(cmul(u10, a0), cmul(u11, a1));
+      }
+    }
+    double pr[NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) pr[m] = amp[m].x * amp[m].x + amp[m].y * amp[m].y;
+#pragma unroll
+    for (int sub = 0; sub < NM; ++sub) {
+      if (sub & ~zmask) continue;
+      int64_t b = 0;
+      int sign_mask = 0;
+#pragma unroll
+      for (int j = 0; j < KO; ++j) {
+        int digit;
+        if (basis[j] == 0) digit = ((sub >> j) & 1) ? 3 : 0;
+        else digit = basis[j];
+        b = 4 * b + digit;
+        if (digit != 0) sign_mask |= 1 << (KO - 1 - j);
+      }
+      double val = 0.0;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) val += (__popc(m & sign_mask) & 1) ? -pr[m] : pr[m];
       P[((int64_t)(s0 + sl) * rows_b + b) * nx + x] = val;
     }
   }
@@ -333,6 +462,27 @@ void gate_matrix(const cutqc_gate& g, double2* m, int& nq) {
   }
 }
 
+// the per-device scratch block of the simulator (grow-only, at most 256 MiB)
+struct SimScratch {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+std::map<int, SimScratch> g_sim_scratch;
+
+char* sim_scratch(size_t bytes) {
+  int dev = 0;
+  CUTQC_CUDA(cudaGetDevice(&dev));
+  SimScratch& sc = g_sim_scratch[dev];
+  if (bytes > sc.bytes) {
+    if (sc.p) CUTQC_CUDA(cudaFree(sc.p));
+    sc.p = nullptr;
+    sc.bytes = 0;
+    CUTQC_CUDA(cudaMalloc(&sc.p, bytes));
+    sc.bytes = bytes;
+  }
+  return static_cast<char*>(sc.p);
+}
+
 }  // namespace
 
 void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t s) {
@@ -354,78 +504,94 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
   // state chunk: psi and phi for nb variants within ~8 GiB
   const int64_t budget = int64_t(8) << 30;
   int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nvar, budget / (dim * 32)));
-  double2 *psi = nullptr, *phi = nullptr;
-  double* P = nullptr;
-  CUTQC_CUDA(cudaStreamSynchronize(s));
-  CUTQC_CUDA(cudaMalloc(&psi, (size_t)dim * nb * sizeof(double2)));
-  if (sp.k_out > kMaxRotSim) CUTQC_CUDA(cudaMalloc(&phi, (size_t)dim * nb * sizeof(double2)));
-  CUTQC_CUDA(cudaMalloc(&P, (size_t)total * sizeof(double)));
-  try {
-    std::vector<std::pair<std::vector<double2>, int>> mats;
-    for (const cutqc_gate& g : sp.gates) {
-      std::vector<double2> m(16);
-      int nq = 1;
-      gate_matrix(g, m.data(), nq);
-      mats.emplace_back(m, nq);
-    }
-    // runs of consecutive gates over at most L index bits, each run's tile
-    // bits, its gates by tile position and the matrix table
-    const int L = std::min(sp.d, kTileBits);
-    std::vector<TileBits> runs;
-    std::vector<std::pair<int, int>> run_gates;   // [first, count) into fg
-    std::vector<FusedGate> fg;
-    std::vector<double2> mt;
-    {
-      size_t gi = 0;
-      while (gi < sp.gates.size()) {
-        int64_t used = 0;
-        size_t gj = gi;
-        for (; gj < sp.gates.size(); ++gj) {
-          int64_t m = int64_t(1) << (sp.d - 1 - sp.gates[gj].q0);
-          if (mats[gj].second == 2) m |= int64_t(1) << (sp.d - 1 - sp.gates[gj].q1);
-          if (__builtin_popcountll(used | m) > L) break;
-          used |= m;
+  std::vector<std::pair<std::vector<double2>, int>> mats;
+  for (const cutqc_gate& g : sp.gates) {
+    std::vector<double2> m(16);
+    int nq = 1;
+    gate_matrix(g, m.data(), nq);
+    mats.emplace_back(m, nq);
+  }
+  // runs of consecutive gates over at most L index bits, each run's tile
+  // bits, its gates by tile position and the matrix table
+  const int L = std::min(sp.d, kTileBits);
+  std::vector<TileBits> runs;
+  std::vector<std::pair<int, int>> run_gates;   // [first, count) into fg
+  std::vector<FusedGate> fg;
+  std::vector<float4> mt;   // matrix entries as double-float (re.hi, re.lo, im.hi, im.lo)
+  {
+    size_t gi = 0;
+    while (gi < sp.gates.size()) {
+      int64_t used = 0;
+      size_t gj = gi;
+      for (; gj < sp.gates.size(); ++gj) {
+        int64_t m = int64_t(1) << (sp.d - 1 - sp.gates[gj].q0);
+        if (mats[gj].second == 2) m |= int64_t(1) << (sp.d - 1 - sp.gates[gj].q1);
+        if (__builtin_popcountll(used | m) > L) break;
+        used |= m;
+      }
+      for (int b = 0; b < sp.d && __builtin_popcountll(used) < L; ++b) used |= int64_t(1) << b;
+      TileBits t{};
+      t.L = L;
+      t.tmask = used;
+      int pos[64];
+      for (int b = 0, k = 0; b < sp.d; ++b)
+        if ((used >> b) & 1) {
+          pos[b] = k;
+          t.tb[k++] = b;
         }
-        for (int b = 0; b < sp.d && __builtin_popcountll(used) < L; ++b) used |= int64_t(1) << b;
-        TileBits t{};
-        t.L = L;
-        t.tmask = used;
-        int pos[64];
-        for (int b = 0, k = 0; b < sp.d; ++b)
-          if ((used >> b) & 1) {
-            pos[b] = k;
-            t.tb[k++] = b;
+      runs.push_back(t);
+      run_gates.emplace_back((int)fg.size(), (int)(gj - gi));
+      for (size_t g = gi; g < gj; ++g) {
+        FusedGate f{};
+        f.nq = mats[g].second;
+        f.diag = 1;
+        for (int rr = 0; rr < 2 * f.nq; ++rr)
+          for (int k = 0; k < 2 * f.nq; ++k) {
+            const double2 e = mats[g].first[(size_t)(2 * f.nq) * rr + k];
+            if (rr != k && (e.x != 0.0 || e.y != 0.0)) f.diag = 0;
           }
-        runs.push_back(t);
-        run_gates.emplace_back((int)fg.size(), (int)(gj - gi));
-        for (size_t g = gi; g < gj; ++g) {
-          FusedGate f{};
-          f.nq = mats[g].second;
-          f.p0 = pos[sp.d - 1 - sp.gates[g].q0];
-          f.p1 = f.nq == 2 ? pos[sp.d - 1 - sp.gates[g].q1] : 0;
-          f.mat = (int)mt.size();
-          mt.insert(mt.end(), mats[g].first.begin(), mats[g].first.begin() + (f.nq == 2 ? 16 : 4));
-          fg.push_back(f);
+        f.p0 = pos[sp.d - 1 - sp.gates[g].q0];
+        f.p1 = f.nq == 2 ? pos[sp.d - 1 - sp.gates[g].q1] : 0;
+        f.mat = (int)mt.size();
+        for (int e = 0; e < (f.nq == 2 ? 16 : 4); ++e) {
+          const double2 z = mats[g].first[e];
+          const float rh = (float)z.x, ih = (float)z.y;
+          mt.push_back(make_float4(rh, (float)(z.x - (double)rh), ih, (float)(z.y - (double)ih)));
         }
-        gi = gj;
+        fg.push_back(f);
       }
+      gi = gj;
     }
-    FusedGate* dg = nullptr;
-    double2* dm = nullptr;
+  }
+  // one scratch block: state, rotated copy (more than 4 measured qubits),
+  // attributed rows, gate and matrix tables.  Up to 256 MiB it is kept per
+  // device between calls (calls are serialised and end with a stream
+  // synchronisation, so the next call may reuse it); larger blocks are
+  // allocated and freed per call.
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t o_phi = up((size_t)dim * nb * sizeof(double2));
+  const size_t o_P = o_phi + (sp.k_out > kMaxRotSim ? up((size_t)dim * nb * sizeof(double2)) : 0);
+  const size_t o_g = o_P + up((size_t)total * sizeof(double));
+  const size_t o_m = o_g + up(fg.size() * sizeof(FusedGate));
+  const size_t bytes = o_m + up(mt.size() * sizeof(float4));
+  char* block = nullptr;
+  const bool cached = bytes <= (size_t(256) << 20);
+  if (cached) {
+    block = sim_scratch(bytes);
+  } else {
+    CUTQC_CUDA(cudaStreamSynchronize(s));
+    CUTQC_CUDA(cudaMalloc(&block, bytes));
+  }
+  double2* psi = reinterpret_cast<double2*>(block);
+  double2* phi = reinterpret_cast<double2*>(block + o_phi);
+  double* P = reinterpret_cast<double*>(block + o_P);
+  FusedGate* dg = reinterpret_cast<FusedGate*>(block + o_g);
+  float4* dm = reinterpret_cast<float4*>(block + o_m);
+  try {
     if (!fg.empty()) {
-      CUTQC_CUDA(cudaMalloc(&dg, fg.size() * sizeof(FusedGate)));
-      CUTQC_CUDA(cudaMalloc(&dm, mt.size() * sizeof(double2)));
-      CUTQC_CUDA(cudaMemcpy(dg, fg.data(), fg.size() * sizeof(FusedGate), cudaMemcpyHostToDevice));
-      CUTQC_CUDA(cudaMemcpy(dm, mt.data(), mt.size() * sizeof(double2), cudaMemcpyHostToDevice));
+      CUTQC_CUDA(cudaMemcpyAsync(dg, fg.data(), fg.size() * sizeof(FusedGate), cudaMemcpyHostToDevice, s));
+      CUTQC_CUDA(cudaMemcpyAsync(dm, mt.data(), mt.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
     }
-    struct FreeTables {
-      FusedGate* g;
-      double2* m;
-      ~FreeTables() {
-        if (g) cudaFree(g);
-        if (m) cudaFree(m);
-      }
-    } free_tables{dg, dm};
     const double2 hr = make_double2(0.70710678118654752440, 0.0);
     for (int s0 = 0; s0 < nvar; s0 += nb) {
       const int n = std::min(nb, nvar - s0);
@@ -438,14 +604,21 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
         count_launch();
         check_launch("k_gates_tile");
       }
-      for (int mb = 0; mb < nmb; ++mb) {
-        if (sp.k_out <= kMaxRotSim) {
-          // the basis changes inside the attribution: no copy of the state
-          k_attr_meas<true><<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(psi, a, s0, n, mb, P);
-          count_launch();
-          check_launch("k_attr_meas");
-          continue;
+      if (sp.k_out <= kMaxRotSim) {
+        // the basis changes inside the attribution (no copy of the state),
+        // every basis combination in one launch
+        const dim3 grid(std::max(1u, grid_for((int64_t(1) << sp.n_eff) * n) / (unsigned)nmb), (unsigned)nmb);
+        switch (sp.k_out) {
+          case 0: k_attr_meas_rot<0><<<grid, 256, 0, s>>>(psi, a, s0, n, P); break;
+          case 1: k_attr_meas_rot<1><<<grid, 256, 0, s>>>(psi, a, s0, n, P); break;
+          case 2: k_attr_meas_rot<2><<<grid, 256, 0, s>>>(psi, a, s0, n, P); break;
+          case 3: k_attr_meas_rot<3><<<grid, 256, 0, s>>>(psi, a, s0, n, P); break;
+          default: k_attr_meas_rot<4><<<grid, 256, 0, s>>>(psi, a, s0, n, P); break;
         }
+        count_launch();
+        check_launch("k_attr_meas");
+      }
+      for (int mb = 0; mb < nmb && sp.k_out > kMaxRotSim; ++mb) {
         CUTQC_CUDA(cudaMemcpyAsync(phi, psi, (size_t)dim * n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
         int t = mb;
         std::vector<int> bases(sp.k_out);
@@ -464,7 +637,7 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
             count_launch();
           }
         }
-        k_attr_meas<false><<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(phi, a, s0, n, mb, P);
+        k_attr_meas<<<grid_for((int64_t(1) << sp.n_eff) * n), 256, 0, s>>>(phi, a, s0, n, mb, P);
         count_launch();
         check_launch("k_attr_meas");
       }
@@ -483,14 +656,21 @@ void run_subcircuit_sim(const SimPlan& sp, int dtype, void* tensor, cudaStream_t
     check_launch("k_sim_finish");
     CUTQC_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
-    cudaFree(psi);
-    cudaFree(phi);
-    cudaFree(P);
+    if (!cached) cudaFree(block);
     throw;
   }
-  CUTQC_CUDA(cudaFree(psi));
-  CUTQC_CUDA(cudaFree(phi));
-  CUTQC_CUDA(cudaFree(P));
+  if (!cached) CUTQC_CUDA(cudaFree(block));
+}
+
+void release_sim_scratch() {
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_sim_scratch) {
+    cudaSetDevice(kv.first);
+    if (kv.second.p) cudaFree(kv.second.p);
+  }
+  g_sim_scratch.clear();
+  cudaSetDevice(cur);
 }
 
 }  // namespace cutqc
