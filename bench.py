@@ -717,12 +717,13 @@ def run_other(args):
                               "frac": flops / (ms / 1e3) / 1e12 / LIBRARY_PEAKS["fp64_tflops"],
                               "traffic": None, "algorithmic_flops": flops,
                               "peak_file": "measured FP64 (torch.matmul, LIBRARY_PEAKS)",
-                              "note": "complex FP64 arithmetic of the dense gate matrices as applied; the "
-                                      "states (2 and 0.5 MB) stay in L2"}}
+                              "note": "FP64-equivalent flops of the dense gate matrices as applied (the gates "
+                                      "run in double-float on the FP32 pipes, so this is the fraction of the "
+                                      "FP64 peak the FP64 form would need); the states (2 and 8 MB) stay in L2"}}
         cfg = {"workload": "sim_supremacy4x6_fp64_state", "subcircuits": [[s.d, s.k_in, s.k_out, s.n_eff]
                                                                           for s in cc.subs],
                "step": "simulate every variant of both subcircuits and attribute (input preparation; each call "
-                       "allocates and frees its state buffers)"}
+                       "ends with a stream synchronisation; its scratch is kept per device)"}
     elif w == "metrics_qaoa30":
         # Eq. 16 chi^2 and total variation between the split-precision and the
         # FP32 CUDA-core reconstructions of QAOA-30 (2^30 entries each), and

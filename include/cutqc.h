@@ -310,7 +310,9 @@ CUTQC_API int cutqc_attribute_merged(const void* variant_probs, int32_t d, int32
                                      void* stream);
 
 /* Produce one subcircuit's attributed tensor on the GPU (Fig. 3, Eq. 2-3):
- * simulates, in complex FP64, every variant (each init slot in |0>, |1>,
+ * simulates every variant (state stored in complex FP64, gates evaluated in
+ * double-float arithmetic of about 48 significant bits, attribution in FP64;
+ * each init slot in |0>, |1>,
  * |+>, |+i>; each measurement slot measured in the Z, X, Y basis) of a
  * d-qubit subcircuit whose other qubits start in |0>, attributes the measured
  * cut qubits' outcomes with +-1 (Eq. 3) and combines the init variants into
@@ -318,7 +320,9 @@ CUTQC_API int cutqc_attribute_merged(const void* variant_probs, int32_t d, int32
  * init_qubit[k_in], meas_qubit[k_out], out_local[n_eff]: host arrays of local
  * qubits (local qubit 0 = most significant).  tensor: device
  * [4^k_in][4^k_out][2^n_eff] of `dtype`.  d <= 30.  Synchronises the stream
- * (it allocates and frees temporary state buffers). */
+ * before it returns; its scratch (state, attributed rows, gate tables) is kept
+ * per device between calls up to 256 MiB (freed by cutqc_release), larger
+ * scratch is allocated and freed per call. */
 CUTQC_API int cutqc_simulate_subcircuit(const cutqc_gate* gates, int32_t n_gates,
                               int32_t d, const int32_t* init_qubit,
                               int32_t k_in, const int32_t* meas_qubit,

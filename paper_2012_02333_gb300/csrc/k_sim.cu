@@ -1,6 +1,7 @@
 // GPU subcircuit simulator: input preparation for the reconstruction.
 //
-// For one subcircuit it simulates, in complex FP64, every physical variant
+// For one subcircuit it simulates every physical variant (state stored in
+// complex FP64, gates evaluated in double-float arithmetic, see below)
 // (Fig. 3: each init slot prepared in |0>, |1>, |+>, |+i>; each measured cut
 // qubit measured in the Z, X or Y basis), attributes the measured cut qubits'
 // outcomes with the +-1 factors of Eq. 3 (basis I: both outcomes +1; X, Y, Z:
