@@ -3,9 +3,11 @@ let the library call cudaMalloc: device memory reserved up front by another
 allocator, or no device allocation allowed after start-up).
 
 Its outputs are compared with the FP64 oracle's plain sum on the same tensors
-(oracle-simulated, rounded to FP32 for the FP32 cases), within the tolerances
-of the other parity tests (1e-6 for FP32, 1e-12 for FP64), on two calls in a
-row that share its static scratch array - different problems and dtypes, so
+(oracle-simulated, rounded to FP32 for the FP32 cases) and with the
+allocating entry point's (cutqc_reconstruct_fd, CUDA-core form) on the same
+problem, within the tolerances of the other parity tests (1e-6 for FP32,
+1e-12 for FP64), on two calls in a row that share its static scratch
+array - different problems and dtypes, so
 the second call cannot lean on what the first left behind - including a
 K = 8 problem near the array's limit.  The same calls also run in a fresh
 process that never touches the library's allocating entry points, where the
@@ -65,15 +67,26 @@ def test_noalloc_matches_oracle_on_calls_in_a_row(env):
         dt = getattr(torch, dtn)
         ts = [torch.tensor(t.reshape(-1), dtype=dt, device="cuda") for t in T]
         prepared.append((cutqc.Problem.from_cut(cc, ts), ts, dt, ref, tol, cc))
+    # the allocating entry point's results on the same problems
+    alloc = []
+    for problem, ts, dt, ref, tol, cc in prepared:
+        o = torch.full((2 ** cc.n,), float("nan"), dtype=dt, device="cuda")
+        sp = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+        cutqc.cutqc_reconstruct_fd([problem], [o], "cc", sp)
+        torch.cuda.synchronize()
+        alloc.append((o.double().cpu().numpy(), sp.item()))
     for _ in range(2):   # every problem twice, interleaved
-        for problem, ts, dt, ref, tol, cc in prepared:
+        for (problem, ts, dt, ref, tol, cc), (a_out, a_sum) in zip(prepared, alloc):
             got = torch.full((2 ** cc.n,), float("nan"), dtype=dt, device="cuda")
             got_sum = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
             cutqc.cutqc_reconstruct_fd_noalloc(problem, got, got_sum)
             torch.cuda.synchronize()
-            err = np.abs(got.double().cpu().numpy() - ref).max()
+            g = got.double().cpu().numpy()
+            err = np.abs(g - ref).max()
             assert err <= tol, f"{cc.n} qubits, K={cc.n_cuts}: max abs error {err:.3e}"
             assert abs(got_sum.item() - ref.sum()) <= max(tol, 1e-9)
+            assert np.abs(g - a_out).max() <= tol, f"{cc.n} qubits: differs from cutqc_reconstruct_fd"
+            assert abs(got_sum.item() - a_sum) <= max(tol, 1e-9)
 
 
 _FRESH = r"""
